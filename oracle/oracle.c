@@ -1,0 +1,629 @@
+/*
+ * oracle.c -- plain, slow FP64 CPU oracle of the PHAST multicanonical sweep.
+ *
+ * TEST INFRASTRUCTURE ONLY: used by tests/, the package smoke check and the
+ * benchmark's CPU-baseline leg; never by the product path.  Independent of the
+ * CUDA library: no shared headers, helpers, tables or constants.
+ *
+ * Every routine is written for a reader holding the paper: loops run in the
+ * order of the sums as printed, nothing is blocked, fused or reordered.  Where
+ * the paper is silent, the reading taken is stated at the routine.
+ * Parity pins (tests/test_oracle_*.py): closed-form energies of hand-built
+ * conformations, rigid-motion / periodic-shift / relabelling invariances,
+ * E_after - E_before = dE, the trimer's exact density of states, the reduction
+ * of Berg's recursion to the paper's naive recursion, and finite-difference
+ * exactness on quadratic entropies.
+ */
+#include "oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10, Salmon et al., "Parallel random numbers: as easy as 1, 2, 3", */
+/* SC'11.  Round: two 32x32->64 products of counter words 0 and 2 with the     */
+/* published multipliers, words recombined with the key, key bumped by the     */
+/* published Weyl constants between rounds.  Stands in for the cuRAND vectors  */
+/* of Sec. 3.2 (RANDOM.f / cudaRandom.cu).                                     */
+/* ------------------------------------------------------------------------- */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]) {
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Stream layout: key = (seed low, seed high); block b of move t uses counter
+ * (t low, t high, b, 0x4D554341).  Blocks: 0 selection, 1 and 2 uniforms,
+ * 3 + j Marsaglia attempt j (j < 64). */
+#define ORC_STREAM_TAG 0x4D554341u
+
+static void orc_block(uint64_t seed, uint64_t t, uint32_t b, uint32_t out[4]) {
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), b, ORC_STREAM_TAG};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+/* Uniform in (0,1) from 52 random bits, exact in FP64: ((a>>6) 2^26 + (b>>6) + 1/2) 2^-52. */
+static double orc_u52(uint32_t a, uint32_t b) {
+    double n = (double)(a >> 6) * 67108864.0 + (double)(b >> 6);
+    return (n + 0.5) * (1.0 / 4503599627370496.0);
+}
+
+/* ------------------------------------------------------------------------- */
+/* Move geometry (Sec. 3.2, UPDATE_ENGINE: pivots, Galilean updates; plus the  */
+/* crankshaft).  sin and cos by their Taylor series (|a| <= 1), coefficients   */
+/* (-1)^i/(2i+1)! and (-1)^i/(2i)! as correctly rounded quotients of exact     */
+/* factorials; evaluated by Horner in a^2 with separately rounded operations.  */
+/* ------------------------------------------------------------------------- */
+static double orc_factorial(int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f = f * (double)i;   /* exact for n <= 18 */
+    return f;
+}
+
+static void orc_sincos(double a, double* s, double* c) {
+    double x2 = a * a;
+    double ps = 0.0, pc = 0.0;
+    /* sin a = a * sum_{i=0..8} (-1)^i a^{2i}/(2i+1)! */
+    for (int i = 8; i >= 0; --i) {
+        double coef = (i % 2 ? -1.0 : 1.0) / orc_factorial(2 * i + 1);
+        ps = (i == 8) ? coef : ps * x2 + coef;
+    }
+    /* cos a = sum_{i=0..9} (-1)^i a^{2i}/(2i)! */
+    for (int i = 9; i >= 0; --i) {
+        double coef = (i % 2 ? -1.0 : 1.0) / orc_factorial(2 * i);
+        pc = (i == 9) ? coef : pc * x2 + coef;
+    }
+    *s = a * ps;
+    *c = pc;
+}
+
+/* Rodrigues' rotation matrix about unit axis k by the angle with sine s and cosine c. */
+static void orc_rotation(const double k[3], double s, double c, double R[3][3]) {
+    double t = 1.0 - c;
+    R[0][0] = (t * k[0]) * k[0] + c;
+    R[0][1] = (t * k[0]) * k[1] - s * k[2];
+    R[0][2] = (t * k[0]) * k[2] + s * k[1];
+    R[1][0] = (t * k[1]) * k[0] + s * k[2];
+    R[1][1] = (t * k[1]) * k[1] + c;
+    R[1][2] = (t * k[1]) * k[2] - s * k[0];
+    R[2][0] = (t * k[2]) * k[0] - s * k[1];
+    R[2][1] = (t * k[2]) * k[1] + s * k[0];
+    R[2][2] = (t * k[2]) * k[2] + c;
+}
+
+/* x' = p + R (x - p). */
+static void orc_rotate_about(const double R[3][3], const double p[3], const double x[3], double out[3]) {
+    double v[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
+    for (int i = 0; i < 3; ++i) {
+        double w = (R[i][0] * v[0] + R[i][1] * v[1]) + R[i][2] * v[2];
+        out[i] = p[i] + w;
+    }
+}
+
+/* Isotropic unit axis by Marsaglia (1972): (v1, v2) uniform in the unit disc,
+ * axis = (2 v1 sqrt(1-s), 2 v2 sqrt(1-s), 1 - 2 s), s = v1^2 + v2^2. */
+static void orc_axis(uint64_t seed, uint64_t t, double axis[3]) {
+    for (uint32_t j = 0; j < 64; ++j) {
+        uint32_t r[4];
+        orc_block(seed, t, 3u + j, r);
+        double v1 = 2.0 * orc_u52(r[0], r[1]) - 1.0;
+        double v2 = 2.0 * orc_u52(r[2], r[3]) - 1.0;
+        double s = v1 * v1 + v2 * v2;
+        if (s < 1.0 && s > 0.0) {
+            double q = sqrt(1.0 - s);
+            axis[0] = 2.0 * v1 * q;
+            axis[1] = 2.0 * v2 * q;
+            axis[2] = 1.0 - 2.0 * s;
+            return;
+        }
+    }
+    axis[0] = 0.0; axis[1] = 0.0; axis[2] = 1.0;   /* probability (1 - pi/4)^64 */
+}
+
+static int orc_chain_offset(const orc_model* m, int c) {
+    int o = 0;
+    for (int i = 0; i < c; ++i) o += m->chain_len[i];
+    return o;
+}
+
+static int orc_total(const orc_model* m) { return orc_chain_offset(m, m->n_chains); }
+
+/* Draw move t of a walker.  Readings: the move type is chosen by comparing one
+ * uniform with the running sum of the type probabilities; the chain is uniform;
+ * pivot and crankshaft act on an interior monomer 1..n-2; angles and steps are
+ * uniform in [-max, max]; the axis is isotropic. */
+void orc_propose(const orc_model* m, const orc_muca* mu, uint64_t seed, uint64_t t,
+                 orc_move* mv, double* u_acc) {
+    uint32_t b0[4], b1[4], b2[4];
+    orc_block(seed, t, 0u, b0);
+    orc_block(seed, t, 1u, b1);
+    orc_block(seed, t, 2u, b2);
+    double u_type = orc_u52(b0[0], b0[1]);
+    double u_a = orc_u52(b1[0], b1[1]);
+    double u_b = orc_u52(b1[2], b1[3]);
+    double u_c = orc_u52(b2[0], b2[1]);
+    *u_acc = orc_u52(b2[2], b2[3]);
+
+    int type = -1, last = 0;
+    double cum = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        cum = cum + mu->p[i];
+        if (mu->p[i] > 0.0) {
+            last = i;
+            if (type < 0 && u_type < cum) type = i;
+        }
+    }
+    if (type < 0) type = last;
+
+    memset(mv, 0, sizeof(*mv));
+    mv->type = type;
+    mv->chain = (int32_t)(((uint64_t)b0[2] * (uint64_t)m->n_chains) >> 32);
+    int n = m->chain_len[mv->chain];
+    if (type == ORC_PIVOT || type == ORC_CRANK)
+        mv->index = 1 + (int32_t)(((uint64_t)b0[3] * (uint64_t)(n - 2)) >> 32);
+    if (type == ORC_TRANS) {
+        mv->disp[0] = (2.0 * u_a - 1.0) * mu->amax[ORC_TRANS];
+        mv->disp[1] = (2.0 * u_b - 1.0) * mu->amax[ORC_TRANS];
+        mv->disp[2] = (2.0 * u_c - 1.0) * mu->amax[ORC_TRANS];
+    } else {
+        mv->angle = (2.0 * u_a - 1.0) * mu->amax[type];
+        if (type == ORC_PIVOT || type == ORC_ROT) orc_axis(seed, t, mv->axis);
+    }
+}
+
+/* Apply a move.  Pivot (Sec. 3.2 "pivotings"): rotate the shorter side of the
+ * chain about an axis through the pivot monomer k; on a tie the tail j > k.
+ * Translation / rotation (Sec. 3.2 "Galilean-group updates"): the whole chain,
+ * rotation about its centroid (running sum j = 0..n-1, then divided by n).
+ * Crankshaft: monomer i about the axis through monomers i-1 and i+1. */
+int orc_apply_move(const orc_model* m, const orc_move* mv, const double* xyz, double* xyz_new) {
+    int N = orc_total(m);
+    memcpy(xyz_new, xyz, sizeof(double) * 3 * (size_t)N);
+    int o = orc_chain_offset(m, mv->chain);
+    int n = m->chain_len[mv->chain];
+    int lo, hi;
+    double center[3], axis[3], R[3][3], s, c;
+
+    if (mv->type == ORC_TRANS) {
+        for (int j = o; j < o + n; ++j)
+            for (int d = 0; d < 3; ++d) xyz_new[3 * j + d] = xyz[3 * j + d] + mv->disp[d];
+        return n;
+    }
+    if (mv->type == ORC_PIVOT) {
+        int k = mv->index;
+        if (k < n - 1 - k) { lo = o; hi = o + k - 1; }
+        else { lo = o + k + 1; hi = o + n - 1; }
+        for (int d = 0; d < 3; ++d) { center[d] = xyz[3 * (o + k) + d]; axis[d] = mv->axis[d]; }
+    } else if (mv->type == ORC_ROT) {
+        lo = o; hi = o + n - 1;
+        for (int d = 0; d < 3; ++d) {
+            double sum = 0.0;
+            for (int j = o; j < o + n; ++j) sum = sum + xyz[3 * j + d];
+            center[d] = sum / (double)n;
+            axis[d] = mv->axis[d];
+        }
+    } else {   /* crankshaft */
+        int i = o + mv->index;
+        double e[3];
+        for (int d = 0; d < 3; ++d) e[d] = xyz[3 * (i + 1) + d] - xyz[3 * (i - 1) + d];
+        double len = sqrt((e[0] * e[0] + e[1] * e[1]) + e[2] * e[2]);
+        if (!(len > 1e-12)) return 0;
+        for (int d = 0; d < 3; ++d) { axis[d] = e[d] / len; center[d] = xyz[3 * (i - 1) + d]; }
+        lo = hi = i;
+    }
+    orc_sincos(mv->angle, &s, &c);
+    orc_rotation(axis, s, c, R);
+    for (int j = lo; j <= hi; ++j) orc_rotate_about(R, center, &xyz[3 * j], &xyz_new[3 * j]);
+    return hi - lo + 1;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Energy, Eq. 2 (kappa_F = 0) per chain and the inter-chain term of Eq. 3.    */
+/* ------------------------------------------------------------------------- */
+
+/* Lennard-Jones term of Eq. 2/3 without its coupling: r^-12 - C r^-6. */
+static double orc_lj(double r2, double C) {
+    double r6 = r2 * r2 * r2;
+    return 1.0 / (r6 * r6) - C / r6;
+}
+
+/* Squared distance; between different chains of a periodic system the minimum
+ * image d - L rint(d / L) per component (reading: the paper's spherical
+ * container is replaced by a periodic cube; chains are never wrapped, so
+ * intra-chain distances are direct). */
+static double orc_dist2(const orc_model* m, const double* a, const double* b, int periodic) {
+    double r2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        double x = a[d] - b[d];
+        if (periodic && m->box_L > 0.0) x = x - m->box_L * rint(x / m->box_L);
+        r2 = r2 + x * x;
+    }
+    return r2;
+}
+
+/* Bending (kappa_C sum_k (1 - cos theta_k), theta_k the angle between bonds
+ * k-1 and k, so a straight chain costs 0) and torsion (-kappa sum cos tau_j,
+ * tau_j the dihedral of monomers j..j+3 from the normals b_j x b_{j+1} and
+ * b_{j+1} x b_{j+2}; a dihedral whose normals have |n1|^2 |n2|^2 < 1e-20
+ * contributes 0) of one chain starting at monomer o with n monomers. */
+static void orc_chain_local(const orc_model* m, const double* xyz, int o, int n,
+                            double* e_bend, double* e_tors) {
+    double bend = 0.0, tors = 0.0;
+    for (int k = 1; k <= n - 2; ++k) {
+        const double* x0 = &xyz[3 * (o + k - 1)];
+        const double* x1 = &xyz[3 * (o + k)];
+        const double* x2 = &xyz[3 * (o + k + 1)];
+        double a[3], b[3];
+        for (int d = 0; d < 3; ++d) { a[d] = x1[d] - x0[d]; b[d] = x2[d] - x1[d]; }
+        double ab = a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+        double aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+        double bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+        double cos_theta = ab / (sqrt(aa) * sqrt(bb));
+        bend = bend + (1.0 - cos_theta);
+    }
+    for (int j = 0; j <= n - 4; ++j) {
+        double b[3][3];
+        for (int q = 0; q < 3; ++q)
+            for (int d = 0; d < 3; ++d)
+                b[q][d] = xyz[3 * (o + j + q + 1) + d] - xyz[3 * (o + j + q) + d];
+        double n1[3] = {b[0][1] * b[1][2] - b[0][2] * b[1][1],
+                        b[0][2] * b[1][0] - b[0][0] * b[1][2],
+                        b[0][0] * b[1][1] - b[0][1] * b[1][0]};
+        double n2[3] = {b[1][1] * b[2][2] - b[1][2] * b[2][1],
+                        b[1][2] * b[2][0] - b[1][0] * b[2][2],
+                        b[1][0] * b[2][1] - b[1][1] * b[2][0]};
+        double n12 = n1[0] * n2[0] + n1[1] * n2[1] + n1[2] * n2[2];
+        double n11 = n1[0] * n1[0] + n1[1] * n1[1] + n1[2] * n1[2];
+        double n22 = n2[0] * n2[0] + n2[1] * n2[1] + n2[2] * n2[2];
+        if (n11 * n22 < 1e-20) continue;
+        tors = tors + n12 / (sqrt(n11) * sqrt(n22));
+    }
+    *e_bend = m->k_bend * bend;
+    *e_tors = -m->k_tors * tors;
+}
+
+static int orc_chain_of(const orc_model* m, int j) {
+    int o = 0;
+    for (int c = 0; c < m->n_chains; ++c) {
+        if (j < o + m->chain_len[c]) return c;
+        o += m->chain_len[c];
+    }
+    return -1;
+}
+
+double orc_energy(const orc_model* m, const double* xyz, double* terms) {
+    int N = orc_total(m);
+    double bend = 0.0, tors = 0.0, intra = 0.0, inter = 0.0;
+    for (int c = 0, o = 0; c < m->n_chains; o += m->chain_len[c], ++c) {
+        double eb, et;
+        orc_chain_local(m, xyz, o, m->chain_len[c], &eb, &et);
+        bend = bend + eb;
+        tors = tors + et;
+    }
+    /* Eq. 2: pairs i < j - 1 of one chain.  Eq. 3: all pairs of different chains. */
+    for (int i = 0; i < N; ++i) {
+        int ci = orc_chain_of(m, i);
+        for (int j = i + 1; j < N; ++j) {
+            int cj = orc_chain_of(m, j);
+            double C = m->C[2 * m->seq[i] + m->seq[j]];
+            if (ci == cj) {
+                if (j < i + 2) continue;
+                intra = intra + orc_lj(orc_dist2(m, &xyz[3 * i], &xyz[3 * j], 0), C);
+            } else {
+                inter = inter + orc_lj(orc_dist2(m, &xyz[3 * i], &xyz[3 * j], 1), C);
+            }
+        }
+    }
+    intra = m->k_lj_intra * intra;
+    inter = m->k_lj_inter * inter;
+    if (terms) { terms[0] = bend; terms[1] = tors; terms[2] = intra; terms[3] = inter; }
+    return ((bend + tors) + intra) + inter;
+}
+
+/* Moved monomer range of a move, [lo, hi] (global indices). */
+static void orc_moved_range(const orc_model* m, const orc_move* mv, int* lo, int* hi) {
+    int o = orc_chain_offset(m, mv->chain);
+    int n = m->chain_len[mv->chain];
+    if (mv->type == ORC_TRANS || mv->type == ORC_ROT) { *lo = o; *hi = o + n - 1; return; }
+    if (mv->type == ORC_CRANK) { *lo = *hi = o + mv->index; return; }
+    int k = mv->index;
+    if (k < n - 1 - k) { *lo = o; *hi = o + k - 1; }
+    else { *lo = o + k + 1; *hi = o + n - 1; }
+}
+
+/* dE of a move: the bending and torsion of the moved chain before and after,
+ * plus every Lennard-Jones pair (moved monomer, unmoved monomer) before and
+ * after.  Pairs of two moved monomers keep their distance (the moved set moves
+ * rigidly) and are left out.  Returns NaN for a degenerate move. */
+double orc_delta_energy(const orc_model* m, const double* xyz, const orc_move* mv, double* xyz_new) {
+    int N = orc_total(m);
+    double* xn = xyz_new ? xyz_new : (double*)malloc(sizeof(double) * 3 * (size_t)N);
+    int moved = orc_apply_move(m, mv, xyz, xn);
+    double dE;
+    if (moved == 0) {
+        dE = NAN;
+    } else {
+        int o = orc_chain_offset(m, mv->chain);
+        int n = m->chain_len[mv->chain];
+        double eb0, et0, eb1, et1;
+        orc_chain_local(m, xyz, o, n, &eb0, &et0);
+        orc_chain_local(m, xn, o, n, &eb1, &et1);
+        dE = (eb1 + et1) - (eb0 + et0);
+        int lo, hi;
+        orc_moved_range(m, mv, &lo, &hi);
+        for (int i = lo; i <= hi; ++i) {
+            int ci = orc_chain_of(m, i);
+            for (int j = 0; j < N; ++j) {
+                if (j >= lo && j <= hi) continue;
+                int cj = orc_chain_of(m, j);
+                double C = m->C[2 * m->seq[i] + m->seq[j]];
+                double e_old, e_new;
+                if (ci == cj) {
+                    if (abs(i - j) < 2) continue;
+                    e_old = m->k_lj_intra * orc_lj(orc_dist2(m, &xyz[3 * i], &xyz[3 * j], 0), C);
+                    e_new = m->k_lj_intra * orc_lj(orc_dist2(m, &xn[3 * i], &xn[3 * j], 0), C);
+                } else {
+                    e_old = m->k_lj_inter * orc_lj(orc_dist2(m, &xyz[3 * i], &xyz[3 * j], 1), C);
+                    e_new = m->k_lj_inter * orc_lj(orc_dist2(m, &xn[3 * i], &xn[3 * j], 1), C);
+                }
+                dE = dE + (e_new - e_old);
+            }
+        }
+    }
+    if (!xyz_new) free(xn);
+    return dE;
+}
+
+/* Pair evaluations of a move: 2 (before and after) for every Lennard-Jones pair
+ * (moved i, unmoved j) whose distance the move can change -- the pivot monomer
+ * keeps its distance to the rotated side and is not counted. */
+int64_t orc_pair_evals(const orc_model* m, const orc_move* mv) {
+    int N = orc_total(m);
+    int lo, hi;
+    orc_moved_range(m, mv, &lo, &hi);
+    int pivot = (mv->type == ORC_PIVOT) ? orc_chain_offset(m, mv->chain) + mv->index : -1;
+    int64_t count = 0;
+    for (int i = lo; i <= hi; ++i) {
+        int ci = orc_chain_of(m, i);
+        for (int j = 0; j < N; ++j) {
+            if ((j >= lo && j <= hi) || j == pivot) continue;
+            if (orc_chain_of(m, j) == ci && abs(i - j) < 2) continue;
+            count += 2;
+        }
+    }
+    return count;
+}
+
+/* Energy bin: floor((E - e_min) / width) on [e_min, e_min + K width); -1 outside
+ * or for a non-finite E.  (Reading of Sec. 2.2: E_k in [E_0, E_max], half-open bins.) */
+int32_t orc_bin(const orc_muca* mu, double E) {
+    if (!isfinite(E)) return -1;
+    double q = (E - mu->e_min) / mu->bin_width;
+    if (!(q >= 0.0 && q < (double)mu->n_bins)) return -1;
+    return (int32_t)floor(q);
+}
+
+/* ------------------------------------------------------------------------- */
+/* The multicanonical Metropolis sweep of one walker (Sec. 2.2 and Sec. 3.2,   */
+/* MONTE_CARLO.f): accept with min(1, W(E')/W(E)), W = exp(lnW[bin]) piecewise  */
+/* constant per bin (Eq. 8 tabulated), and count the current bin into the      */
+/* histogram after every attempt, accepted or not.  Readings: one sweep is      */
+/* N_tot attempts; a proposal out of the bin range or with non-finite dE is     */
+/* rejected; every recompute_every sweeps the running energy is replaced by a   */
+/* full FP64 energy (if that lands in range) and the drift recorded.            */
+/* ------------------------------------------------------------------------- */
+int orc_sweep_walker(const orc_model* m, const orc_muca* mu, const double* lnW,
+                     uint64_t seed, int64_t n_moves,
+                     double* xyz, double* E, int32_t* bin, uint64_t* t,
+                     uint64_t* hist, const int8_t* force, orc_record* rec, double* stats) {
+    int N = orc_total(m);
+    if (orc_bin(mu, *E) != *bin || *bin < 0) return -1;
+    double* xn = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+    uint64_t attempts[4] = {0, 0, 0, 0}, accepts[4] = {0, 0, 0, 0};
+    int64_t pair_evals = 0, n_recompute = 0, mismatches = 0;
+    double drift_max = 0.0;
+    uint64_t period = (uint64_t)N * (uint64_t)(mu->recompute_every > 0 ? mu->recompute_every : 0);
+
+    for (int64_t it = 0; it < n_moves; ++it) {
+        orc_move mv;
+        double u_acc;
+        orc_propose(m, mu, seed, *t, &mv, &u_acc);
+        double dE = orc_delta_energy(m, xyz, &mv, xn);
+        double E_new = *E + dE;
+        int32_t b_new = orc_bin(mu, E_new);
+        int own = 0;
+        if (b_new >= 0) {
+            double dlnW = lnW[b_new] - lnW[*bin];
+            own = (dlnW >= 0.0) || (u_acc < exp(dlnW));
+        }
+        int acc = own;
+        if (force && force[it] >= 0) {
+            acc = force[it];
+            if (acc != own) mismatches++;
+            if (acc && b_new < 0)   /* imposed acceptance at a range-edge near-tie */
+                b_new = (E_new < mu->e_min) ? 0 : mu->n_bins - 1;
+        }
+        attempts[mv.type]++;
+        pair_evals += orc_pair_evals(m, &mv);
+        if (acc) {
+            memcpy(xyz, xn, sizeof(double) * 3 * (size_t)N);
+            *E = E_new;
+            *bin = b_new;
+            accepts[mv.type]++;
+        }
+        hist[*bin] += 1;
+        if (rec) {
+            rec[it].dE = dE;
+            rec[it].E_after = *E;
+            rec[it].bin_after = *bin;
+            rec[it].accepted = acc;
+        }
+        *t += 1;
+        if (period > 0 && (*t % period) == 0) {
+            double Ef = orc_energy(m, xyz, NULL);
+            double drift = fabs(*E - Ef);
+            if (drift > drift_max) drift_max = drift;
+            int32_t bf = orc_bin(mu, Ef);
+            if (bf >= 0) { *E = Ef; *bin = bf; }
+            n_recompute++;
+        }
+    }
+    free(xn);
+    if (stats) {
+        for (int i = 0; i < 4; ++i) { stats[i] = (double)attempts[i]; stats[4 + i] = (double)accepts[i]; }
+        stats[8] = (double)pair_evals;
+        stats[9] = (double)n_recompute;
+        stats[10] = drift_max;
+        stats[11] = (double)mismatches;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Berg's multicanonical recursion with accumulated error weights (Sec. 2.2,    */
+/* cited there to Berg).  With beta_k = (lnW_k - lnW_{k+1}) / eps (so that       */
+/* S = -lnW and beta = dS/dE):                                                   */
+/*   g0_k  = H_k H_{k+1} / (H_k + H_{k+1})   (0 unless both bins are visited)    */
+/*   ghat  = g0_k / (g_acc_k + g0_k),  g_acc_k += g0_k                           */
+/*   beta_k += ghat (ln H_{k+1} - ln H_k) / eps                                  */
+/* and lnW re-integrated from lnW_0 = 0.  With g_acc = 0 this is the naive       */
+/* recursion W^{n+1} = W^n / H^n on every pair of visited bins.                  */
+/* Flatness (Sec. 4.1): c_Var = sigma_H / mu_H and the largest |H - mu_H| / mu_H */
+/* over visited bins.                                                            */
+/* ------------------------------------------------------------------------- */
+void orc_berg_update(int32_t K, double bin_width, const double* H, double* lnW,
+                     double* g_acc, double* flat_out) {
+    (void)bin_width;   /* beta_k eps is carried as a difference; eps cancels */
+    double* d = (double*)malloc(sizeof(double) * (size_t)(K > 1 ? K - 1 : 1));
+    for (int k = 0; k + 1 < K; ++k) {
+        double g0 = 0.0;
+        if (H[k] > 0.0 && H[k + 1] > 0.0) g0 = H[k] * H[k + 1] / (H[k] + H[k + 1]);
+        double den = g_acc[k] + g0;
+        double ghat = den > 0.0 ? g0 / den : 0.0;
+        g_acc[k] = den;
+        d[k] = lnW[k] - lnW[k + 1];
+        if (g0 > 0.0) d[k] = d[k] + ghat * (log(H[k + 1]) - log(H[k]));
+    }
+    if (K > 0) lnW[0] = 0.0;
+    for (int k = 0; k + 1 < K; ++k) lnW[k + 1] = lnW[k] - d[k];
+    free(d);
+    if (flat_out) {
+        double n = 0.0, sum = 0.0;
+        for (int k = 0; k < K; ++k) if (H[k] > 0.0) { n = n + 1.0; sum = sum + H[k]; }
+        double mean = n > 0.0 ? sum / n : 0.0;
+        double var = 0.0, maxdev = 0.0;
+        for (int k = 0; k < K; ++k) {
+            if (!(H[k] > 0.0)) continue;
+            var = var + (H[k] - mean) * (H[k] - mean);
+            double dev = fabs(H[k] - mean) / mean;
+            if (dev > maxdev) maxdev = dev;
+        }
+        var = n > 0.0 ? var / n : 0.0;
+        flat_out[0] = n;
+        flat_out[1] = mean;
+        flat_out[2] = mean > 0.0 ? sqrt(var) / mean : 0.0;
+        flat_out[3] = maxdev;
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Microcanonical analysis (Sec. 2.2 Eq. 4-6, Sec. 3.3 ANALYST).               */
+/* S_k = -lnW_k + ln H_k on visited bins (the multicanonical reweighting; with */
+/* H omitted S = -lnW, i.e. S_muca of Eq. 8), shifted so max S = 0.            */
+/* beta_k = (S_{k+h} - S_{k-h}) / (2 h eps)            (Eq. 5, central)        */
+/* S''_k  = (S_{k+h} - 2 S_k + S_{k-h}) / (h eps)^2                            */
+/* C_V,k  = -beta_k^2 / S''_k                          (Eq. 6)                 */
+/* Canonical: p_k(T) ~ exp(S_k - E_k / T), E_k the bin centre; <E>_T and       */
+/* c_V(T) = var_T(E) / (N T^2); peak by a parabola through the grid maximum     */
+/* and its neighbours.                                                          */
+/* ------------------------------------------------------------------------- */
+void orc_micro_analysis(int32_t K, double e_min, double bin_width, const double* lnW,
+                        const double* H, int32_t h, int32_t n_monomers,
+                        int32_t n_T, const double* T,
+                        double* S, double* beta, double* CV,
+                        double* E_T, double* cV_T, double* peak) {
+    double smax = -INFINITY;
+    for (int k = 0; k < K; ++k) {
+        if (H && !(H[k] > 0.0)) { S[k] = NAN; continue; }
+        S[k] = -lnW[k] + (H ? log(H[k]) : 0.0);
+        if (S[k] > smax) smax = S[k];
+    }
+    for (int k = 0; k < K; ++k) if (!isnan(S[k])) S[k] = S[k] - smax;
+
+    double he = (double)h * bin_width;
+    for (int k = 0; k < K; ++k) {
+        beta[k] = NAN;
+        CV[k] = NAN;
+        if (k - h < 0 || k + h >= K) continue;
+        if (isnan(S[k - h]) || isnan(S[k + h])) continue;
+        beta[k] = (S[k + h] - S[k - h]) / (2.0 * he);
+        if (isnan(S[k])) continue;
+        double s2 = (S[k + h] - 2.0 * S[k] + S[k - h]) / (he * he);
+        CV[k] = -(beta[k] * beta[k]) / s2;
+    }
+
+    for (int i = 0; i < n_T; ++i) {
+        double lmax = -INFINITY;
+        for (int k = 0; k < K; ++k) {
+            if (isnan(S[k])) continue;
+            double Ek = e_min + ((double)k + 0.5) * bin_width;
+            double lp = S[k] - Ek / T[i];
+            if (lp > lmax) lmax = lp;
+        }
+        double Z = 0.0, sE = 0.0;
+        for (int k = 0; k < K; ++k) {
+            if (isnan(S[k])) continue;
+            double Ek = e_min + ((double)k + 0.5) * bin_width;
+            double w = exp(S[k] - Ek / T[i] - lmax);
+            Z = Z + w;
+            sE = sE + w * Ek;
+        }
+        double mean = sE / Z, var = 0.0;
+        for (int k = 0; k < K; ++k) {
+            if (isnan(S[k])) continue;
+            double Ek = e_min + ((double)k + 0.5) * bin_width;
+            double w = exp(S[k] - Ek / T[i] - lmax);
+            var = var + w * (Ek - mean) * (Ek - mean);
+        }
+        var = var / Z;
+        E_T[i] = mean;
+        cV_T[i] = var / ((double)n_monomers * T[i] * T[i]);
+    }
+
+    if (n_T > 0) {
+        int im = 0;
+        for (int i = 1; i < n_T; ++i) if (cV_T[i] > cV_T[im]) im = i;
+        peak[0] = T[im];
+        peak[1] = cV_T[im];
+        if (im > 0 && im < n_T - 1) {
+            double x0 = T[im - 1], x1 = T[im], x2 = T[im + 1];
+            double y0 = cV_T[im - 1], y1 = cV_T[im], y2 = cV_T[im + 1];
+            double num = (x1 - x0) * (x1 - x0) * (y1 - y2) - (x1 - x2) * (x1 - x2) * (y1 - y0);
+            double den = (x1 - x0) * (y1 - y2) - (x1 - x2) * (y1 - y0);
+            if (den != 0.0) {
+                double xs = x1 - 0.5 * num / den;
+                /* value of the interpolating parabola at xs (Lagrange form) */
+                double ys = y0 * (xs - x1) * (xs - x2) / ((x0 - x1) * (x0 - x2))
+                          + y1 * (xs - x0) * (xs - x2) / ((x1 - x0) * (x1 - x2))
+                          + y2 * (xs - x0) * (xs - x1) / ((x2 - x0) * (x2 - x1));
+                peak[0] = xs;
+                peak[1] = ys;
+            }
+        }
+    }
+}
