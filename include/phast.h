@@ -1,0 +1,257 @@
+/*
+ * phast.h -- C ABI of libphast.so, the GB300 (sm_103a) multicanonical sweep of
+ * off-lattice AB heteropolymers (PHAST, arXiv 1702.01770).
+ *
+ * Conventions for every entry point:
+ *  - Return 0 (PHAST_OK) or a negative PHAST_E* code; phast_last_error() gives
+ *    a message for the calling thread's last failure.
+ *  - "dev" pointers are CUDA device pointers on the current device; "host"
+ *    pointers are ordinary host memory.  The library never frees or keeps a
+ *    caller pointer beyond the call, except the phast_ctx object, which the
+ *    caller creates and destroys.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Work is enqueued asynchronously on it; device-side failures surface at the
+ *    next synchronising call (PHAST_ECUDA).
+ *  - Coordinates are unwrapped Cartesian positions in units of the bond length
+ *    r0 = 1 (Sec. 4: kappa_F = 0 fixes every bond at r0); energies are in units
+ *    of the Lennard-Jones well depth with k_B = 1.  xyz arrays are [.][N][3]
+ *    doubles, monomers of chain 0 first, then chain 1, and so on.
+ *  - Sequences are uint8, 0 = A (hydrophobic), 1 = B (hydrophilic), Eq. 1.
+ *
+ * Equations are numbered in order of appearance in the paper: Eq. 1 C_LJ,
+ * Eq. 2 H_single, Eq. 3 H_multi (Sec. 2.1); Eq. 4 S = k_B ln Omega, Eq. 5
+ * beta(E), Eq. 6 C_V(E), Eq. 7 F(E), Eq. 8 S_muca (Sec. 2.2).
+ */
+#ifndef PHAST_H
+#define PHAST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PHAST_VERSION 1
+
+/* Hard limits of this build. */
+#define PHAST_MAX_SYSTEMS 8      /* system types in one context */
+#define PHAST_MAX_CHAINS 16      /* chains per system */
+#define PHAST_MAX_MONOMERS 512   /* monomers per system (all chains) */
+#define PHAST_MAX_BINS 16384     /* energy bins per system */
+#define PHAST_MAX_ANGLE 1.0      /* largest rotation amplitude (rad) */
+
+enum {
+    PHAST_OK = 0,
+    PHAST_EINVAL = -1,     /* bad argument (message says which) */
+    PHAST_ERANGE = -2,     /* a walker energy outside its bin range */
+    PHAST_ENOMEM = -3,     /* device or host allocation failed */
+    PHAST_ECUDA = -4,      /* a CUDA runtime call failed */
+    PHAST_ETIMEOUT = -5,   /* a bounded device wait ran out */
+    PHAST_EDEVICE = -6,    /* a kernel reported an error word */
+    PHAST_ENONFINITE = -7  /* non-finite coordinates or energy */
+};
+
+enum { PHAST_PIVOT = 0, PHAST_TRANS = 1, PHAST_ROT = 2, PHAST_CRANK = 3 };
+
+/* A system type: M chains (each >= 3 monomers), their AB sequence and the box.
+ * box_L > 0: periodic cube of side box_L with the minimum image between
+ * different chains (chains are never wrapped, so distances within a chain are
+ * direct); box_L = 0: open space.  All pointers are host pointers. */
+typedef struct {
+    int32_t n_chains;
+    const int32_t* chain_len;   /* host [n_chains] */
+    const uint8_t* seq;         /* host [N], N = sum chain_len */
+    double box_L;
+} phast_system;
+
+/* Force field, Eq. 2/3 in the AB limit (kappa_F = 0) plus torsion:
+ * E = k_bend sum_k (1 - cos theta_k) - k_tors sum_j cos tau_j
+ *   + k_lj_intra sum_{i < j-1} (r^-12 - C r^-6) + k_lj_inter sum_{inter} (...).
+ * C[2*s_i + s_j] is C_LJ of Eq. 1 (AA = 1, AB = BA = -1/2, BB = 1/2). */
+typedef struct {
+    double k_bend, k_tors, k_lj_intra, k_lj_inter;
+    double C[4];
+} phast_ff;
+
+/* Multicanonical set-up of one system type (Sec. 2.2, Eq. 8): bins
+ * [e_min + k w, e_min + (k+1) w), k < n_bins; move mix p[] over pivot,
+ * translation, rotation, crankshaft (sums to 1); amplitudes amax[] (angles in
+ * rad <= PHAST_MAX_ANGLE, translation step per component); an FP64 full-energy
+ * recompute every `recompute_every` sweeps (0 = never); pair arithmetic of the
+ * batched sweep in FP32 (32) or FP64 (64). */
+typedef struct {
+    double e_min, bin_width;
+    int32_t n_bins;
+    int32_t recompute_every;
+    double p[4];
+    double amax[4];
+    int32_t pair_precision;
+    int32_t pad;
+} phast_muca_params;
+
+/* An explicit move (64 bytes): pivot about monomer `index` of `chain` by
+ * `angle` around unit `axis`; translation by `disp`; rotation of the chain
+ * about its centroid; crankshaft of monomer `index` about its neighbours' axis
+ * (axis ignored). */
+typedef struct {
+    int32_t type, chain, index, pad;
+    double axis[3];
+    double angle;
+    double disp[3];
+} phast_move;
+
+/* Per-walker counters, accumulated over sweeps (dev arrays of these). */
+typedef struct {
+    uint64_t attempts[4];
+    uint64_t accepts[4];
+    uint64_t pair_evals;   /* 2 per (moved, unmoved) Lennard-Jones pair whose distance can change */
+    uint64_t recomputes;
+    double drift_max;      /* largest |E_running - E_full| seen at a recompute */
+    double pad;
+} phast_walker_stats;
+
+/* One traced move (16 bytes). */
+typedef struct {
+    double dE;           /* energy change computed for the proposal (NaN: degenerate) */
+    int32_t bin_after;   /* bin counted for this attempt */
+    int32_t accepted;
+} phast_trace;
+
+typedef struct phast_ctx phast_ctx;
+
+/* ---- energy (Sec. 2.1, Eq. 2 and Eq. 3) --------------------------------- */
+
+/* Total energy of B configurations of one system.  xyz: dev [B][N][3] FP64;
+ * pair_precision 32 or 64 selects the Lennard-Jones pair arithmetic (local
+ * terms and sums are FP64).  E_out: dev [B].  B = 0 is a no-op. */
+int phast_energy(const phast_system* sys, const phast_ff* ff, int32_t B, const double* xyz,
+                 int32_t pair_precision, double* E_out, void* stream);
+
+/* Energy change of move b applied to configuration b (Sec. 3.2 move set):
+ * bending/torsion terms that the move changes plus every Lennard-Jones pair
+ * (moved, unmoved) before and after.  moves: dev [B]; dE_out: dev [B];
+ * xyz_new_out: dev [B][N][3] or NULL (receives the moved configurations).
+ * A degenerate crankshaft (coincident neighbours) gives NaN. */
+int phast_delta_energy(const phast_system* sys, const phast_ff* ff, int32_t B, const double* xyz,
+                       const phast_move* moves, int32_t pair_precision, double* dE_out,
+                       double* xyz_new_out, void* stream);
+
+/* ---- walker context ---------------------------------------------------- */
+
+/* Create the walker state of n_systems system types on the current device:
+ * walkers[s] walkers of type s (walker indices run over type 0 first), host
+ * seeds[W] (each walker's Philox4x32-10 key; walker streams are
+ * counter-based: block b of move t uses counter (t_lo, t_hi, b, 0x4D554341)),
+ * host xyz0 concatenated per type [walkers[s]][N_s][3].  Computes every
+ * walker's FP64 energy and bin; PHAST_ERANGE if one is outside its range.
+ * Allocates the device state (the caller destroys the context). */
+int phast_ctx_create(phast_ctx** out, int32_t n_systems, const phast_system* sys,
+                     const phast_ff* ff, const phast_muca_params* mp, const int32_t* walkers,
+                     const uint64_t* seeds, const double* xyz0, void* stream);
+void phast_ctx_destroy(phast_ctx* ctx);
+
+/* Sizes: total walkers, and for system type s its N, n_bins, walker offset,
+ * xyz offset (doubles) and lnW offset (the concatenated per-type layouts). */
+int phast_ctx_info(const phast_ctx* ctx, int32_t s, int64_t* info8);
+
+/* Copy walker state between the context and caller buffers (dev or host:
+ * cudaMemcpyAsync with cudaMemcpyDefault).  Any pointer may be NULL. xyz:
+ * concatenated per type; E [W] FP64; bin [W] int32; move index t [W] uint64;
+ * stats [W]. set_state recomputes nothing: E and bin must match xyz. */
+int phast_ctx_get_state(const phast_ctx* ctx, double* xyz, double* E, int32_t* bin, uint64_t* t,
+                        phast_walker_stats* stats, void* stream);
+int phast_ctx_set_state(phast_ctx* ctx, const double* xyz, const double* E, const int32_t* bin,
+                        const uint64_t* t, const phast_walker_stats* stats, void* stream);
+
+/* Tile shape of the batched sweep: threads per walker (4, 8, 16 or 32) and
+ * walkers per CTA; 0 picks the default.  phast_ctx_autotune times the
+ * candidates on a scratch copy of the state and keeps the fastest. */
+int phast_ctx_set_tile(phast_ctx* ctx, int32_t threads_per_walker, int32_t walkers_per_cta);
+int phast_ctx_get_tile(const phast_ctx* ctx, int32_t* threads_per_walker, int32_t* walkers_per_cta);
+int phast_ctx_autotune(phast_ctx* ctx, const double* lnW, int32_t sweeps, void* stream);
+
+/* ---- the multicanonical sweep (Sec. 2.2; MONTE_CARLO.f of Sec. 3.2) ------ */
+
+enum { PHAST_FORM_BATCHED = 0, PHAST_FORM_PLAIN = 1 };
+
+/* n_sweeps sweeps (a sweep = N_s move attempts) of every walker with the
+ * tabulated log-weights lnW (dev, concatenated per type [n_bins_s]): propose
+ * (Philox stream), dE from the changed terms, accept with min(1, W(E')/W(E)),
+ * count the current bin after every attempt.  Proposals out of range or with
+ * non-finite dE are rejected.  Every recompute_every sweeps (by each walker's
+ * own move index) the running energy is replaced by an FP64 full energy.
+ *  form: PHAST_FORM_BATCHED (shared-memory tiles, FP32 or FP64 pairs per
+ *        mp.pair_precision) or PHAST_FORM_PLAIN (one walker per CTA, all FP64,
+ *        global-memory histogram atomics; the comparison form).
+ *  hist_sum: dev uint64 [sum_s n_jk * n_bins_s] or NULL; += counts summed over
+ *        the walkers of jackknife block b of type s, block b holding walkers
+ *        [b W_s / n_jk, (b+1) W_s / n_jk) (integer division).
+ *  hist_walker: dev uint32 [sum_s W_s * n_bins_s] or NULL; += per-walker counts.
+ *  trace: dev [trace_walkers][n_sweeps * N] or NULL; per-move record of the
+ *        first trace_walkers walkers of type 0 (walker-major).
+ * Histograms are added to, never cleared. */
+int phast_muca_sweep(phast_ctx* ctx, int64_t n_sweeps, const double* lnW, int32_t form,
+                     int32_t n_jk, uint64_t* hist_sum, uint32_t* hist_walker,
+                     phast_trace* trace, int32_t trace_walkers, void* stream);
+
+/* ---- Berg's weight recursion (Sec. 2.2) ------------------------------- */
+
+/* One step of the multicanonical recursion with accumulated error weights:
+ * H_k = sum over n_blocks rows of hist (dev uint64 [n_blocks][K]);
+ * g0_k = H_k H_{k+1} / (H_k + H_{k+1}) (0 unless both are visited),
+ * ghat_k = g0_k / (g_acc_k + g0_k), g_acc_k += g0_k,
+ * beta_k += ghat_k (ln H_{k+1} - ln H_k) / w with beta_k = (lnW_k - lnW_{k+1}) / w,
+ * then lnW re-integrated from lnW_0 = 0.  From g_acc = 0 this is the naive
+ * recursion W^{n+1} = W^n / H^n.  lnW dev [K] in/out, g_acc dev [K-1] in/out,
+ * beta_out dev [K-1] or NULL, flat_out dev [4] or NULL: visited bins, mean,
+ * c_Var = sigma_H / mu_H, max |H - mu_H| / mu_H (Sec. 4.1 flatness). */
+int phast_weight_update(int32_t K, double bin_width, const uint64_t* hist, int32_t n_blocks,
+                        double* lnW, double* g_acc, double* beta_out, double* flat_out,
+                        void* stream);
+
+/* ---- microcanonical analysis (Eq. 4-6, Sec. 3.3) ------------------------ */
+
+/* Outputs of phast_micro_analysis (all dev pointers; any may be NULL).
+ * Values from all blocks; *_err the jackknife errors over leave-one-block-out
+ * replicates (n_blocks >= 2), NaN where undefined. */
+typedef struct {
+    double *S, *beta, *CV;               /* [K] */
+    double *E_T, *cV_T;                  /* [n_T] */
+    double *peak;                        /* [2]: T_peak, c_V peak */
+    double *S_err, *beta_err, *CV_err;   /* [K] */
+    double *E_T_err, *cV_T_err;          /* [n_T] */
+    double *peak_err;                    /* [2] */
+} phast_micro_out;
+
+/* S_k = -lnW_k + ln H_k on visited bins (H from hist summed over blocks; with
+ * hist = NULL, S = -lnW, the S_muca of Eq. 8), shifted to max S = 0 (Eq. 4);
+ * beta_k = (S_{k+h} - S_{k-h}) / (2 h w) (Eq. 5); C_V,k = -beta_k^2 / S''_k
+ * with S'' the central second difference of step h (Eq. 6); canonical
+ * <E>_T and c_V(T) = var_T(E) / (n_monomers T^2) with p_k ~ exp(S_k - E_k/T),
+ * E_k the bin centre; peak by a parabola through the largest c_V(T) on the
+ * T grid.  T: dev [n_T].  workspace: dev, phast_micro_workspace_size() bytes. */
+size_t phast_micro_workspace_size(int32_t K, int32_t n_T, int32_t n_blocks);
+int phast_micro_analysis(int32_t K, double e_min, double bin_width, const double* lnW,
+                         const uint64_t* hist, int32_t n_blocks, int32_t fd_half_width,
+                         int32_t n_monomers, int32_t n_T, const double* T,
+                         const phast_micro_out* out, void* workspace, size_t workspace_bytes,
+                         void* stream);
+
+/* ---- checkpoint --------------------------------------------------------- */
+
+/* Serialise the walker state (coordinates, energies, bins, move indices,
+ * counters) with a CRC-32 into a host buffer.  With buf = NULL, *len receives
+ * the size needed.  Restore checks sizes and the CRC (PHAST_EINVAL on a
+ * mismatch) and synchronises `stream`. */
+int phast_ctx_checkpoint(phast_ctx* ctx, void* buf, size_t* len, void* stream);
+int phast_ctx_restore(phast_ctx* ctx, const void* buf, size_t len, void* stream);
+
+/* ---- misc --------------------------------------------------------------- */
+const char* phast_last_error(void);
+int phast_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

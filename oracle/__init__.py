@@ -1,9 +1,8 @@
 """Plain FP64 CPU oracle of the PHAST multicanonical sweep (ctypes wrapper).
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
-benchmark's CPU-baseline / reference leg may import this package.  The product
-path (``paper_1702_01770_gb300``) never imports it, and it never imports the
-product path.  The C source (``oracle.c``) is the oracle; this file only moves
+benchmark's CPU-baseline / reference leg may import this package.  The CUDA
+product path never imports it, and it never imports the product path.  The C source (``oracle.c``) is the oracle; this file only moves
 numpy arrays across the C boundary.
 
 Paper: arXiv 1702.01770 (PHAST).  Eq. 2/3 energy, Sec. 2.2 multicanonical

@@ -1,0 +1,98 @@
+// abi.cu -- host-side pieces of the C ABI: thread-local error messages,
+// validation of the system / force-field / MUCA structs and their flattening
+// into device descriptors, version.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "common.cuh"
+
+static thread_local char g_err[512] = "";
+
+int phast_set_error(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+extern "C" const char* phast_last_error(void) { return g_err; }
+extern "C" int phast_version(void) { return PHAST_VERSION; }
+
+int phast_build_desc(const phast_system* sys, const phast_ff* ff, const phast_muca_params* mp,
+                     SysDesc* d, const char* what) {
+    memset(d, 0, sizeof(*d));
+    if (!sys || !ff) return phast_set_error(PHAST_EINVAL, "%s: NULL system or force field", what);
+    if (sys->n_chains < 1 || sys->n_chains > PHAST_MAX_CHAINS)
+        return phast_set_error(PHAST_EINVAL, "%s: n_chains %d outside [1, %d]", what, sys->n_chains,
+                               PHAST_MAX_CHAINS);
+    if (!sys->chain_len || !sys->seq)
+        return phast_set_error(PHAST_EINVAL, "%s: NULL chain_len or seq", what);
+    int N = 0, maxc = 0;
+    for (int c = 0; c < sys->n_chains; ++c) {
+        int n = sys->chain_len[c];
+        if (n < 3) return phast_set_error(PHAST_EINVAL, "%s: chain %d has %d < 3 monomers", what, c, n);
+        if (N + n > PHAST_MAX_MONOMERS)
+            return phast_set_error(PHAST_EINVAL, "%s: more than %d monomers", what, PHAST_MAX_MONOMERS);
+        d->chain_off[c] = N;
+        for (int j = 0; j < n; ++j) {
+            uint8_t s = sys->seq[N + j];
+            if (s > 1) return phast_set_error(PHAST_EINVAL, "%s: sequence value %d not 0 (A) or 1 (B)", what, s);
+            d->seq[N + j] = s;
+            d->chain_of[N + j] = (uint8_t)c;
+        }
+        N += n;
+        if (n > maxc) maxc = n;
+    }
+    d->chain_off[sys->n_chains] = N;
+    d->n_chains = sys->n_chains;
+    d->N = N;
+    d->max_chain = maxc;
+    if (!(sys->box_L >= 0.0) || !isfinite(sys->box_L))
+        return phast_set_error(PHAST_EINVAL, "%s: box_L must be finite and >= 0", what);
+    d->box_L = sys->box_L;
+    d->inv_L = sys->box_L > 0.0 ? 1.0 / sys->box_L : 0.0;
+    d->k_bend = ff->k_bend;
+    d->k_tors = ff->k_tors;
+    d->k_lj_intra = ff->k_lj_intra;
+    d->k_lj_inter = ff->k_lj_inter;
+    for (int i = 0; i < 4; ++i) d->C[i] = ff->C[i];
+    for (int i = 0; i < 4; ++i)
+        if (!isfinite(d->C[i])) return phast_set_error(PHAST_EINVAL, "%s: non-finite coupling", what);
+    if (!isfinite(d->k_bend) || !isfinite(d->k_tors) || !isfinite(d->k_lj_intra) || !isfinite(d->k_lj_inter))
+        return phast_set_error(PHAST_EINVAL, "%s: non-finite force-field weight", what);
+    d->pair_precision = 64;
+    if (mp) {
+        if (!(mp->bin_width > 0.0) || !isfinite(mp->e_min) || !isfinite(mp->bin_width))
+            return phast_set_error(PHAST_EINVAL, "%s: bins need finite e_min and bin_width > 0", what);
+        if (mp->n_bins < 1 || mp->n_bins > PHAST_MAX_BINS)
+            return phast_set_error(PHAST_EINVAL, "%s: n_bins %d outside [1, %d]", what, mp->n_bins,
+                                   PHAST_MAX_BINS);
+        if (mp->recompute_every < 0)
+            return phast_set_error(PHAST_EINVAL, "%s: recompute_every < 0", what);
+        if (mp->pair_precision != 32 && mp->pair_precision != 64)
+            return phast_set_error(PHAST_EINVAL, "%s: pair_precision must be 32 or 64", what);
+        double sum = 0.0;
+        for (int i = 0; i < 4; ++i) {
+            if (!(mp->p[i] >= 0.0)) return phast_set_error(PHAST_EINVAL, "%s: negative move probability", what);
+            sum += mp->p[i];
+        }
+        if (fabs(sum - 1.0) > 1e-9) return phast_set_error(PHAST_EINVAL, "%s: move probabilities sum to %.17g", what, sum);
+        for (int i = 0; i < 4; ++i) {
+            if (!(mp->amax[i] >= 0.0) || !isfinite(mp->amax[i]))
+                return phast_set_error(PHAST_EINVAL, "%s: amplitude %d must be finite and >= 0", what, i);
+            if (i != PHAST_TRANS && mp->amax[i] > PHAST_MAX_ANGLE)
+                return phast_set_error(PHAST_EINVAL, "%s: rotation amplitude %g > %g rad", what, mp->amax[i],
+                                       PHAST_MAX_ANGLE);
+        }
+        d->e_min = mp->e_min;
+        d->bin_width = mp->bin_width;
+        d->n_bins = mp->n_bins;
+        d->recompute_every = mp->recompute_every;
+        for (int i = 0; i < 4; ++i) { d->p[i] = mp->p[i]; d->amax[i] = mp->amax[i]; }
+        d->pair_precision = mp->pair_precision;
+    }
+    return PHAST_OK;
+}

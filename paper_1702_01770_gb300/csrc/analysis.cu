@@ -1,0 +1,221 @@
+// analysis.cu -- microcanonical analysis (Eq. 4-6; ANALYST of Sec. 3.3) with
+// canonical reweighting and jackknife errors over histogram blocks.
+// Replicate 0 uses every block; replicate r >= 1 leaves block r-1 out.
+//   kernel 1 (one CTA per replicate): S_k, beta_k, C_V,k;
+//   kernel 2 (one CTA per replicate and temperature): <E>_T and c_V(T);
+//   kernel 3 (one CTA): c_V peak per replicate, values and jackknife errors.
+#include "common.cuh"
+
+namespace {
+
+constexpr int kThreads = 512;
+
+struct Work {
+    double *S, *beta, *CV, *ET, *cVT, *peak;   // [R][K] x3, [R][n_T] x2, [R][2]
+};
+
+__host__ __device__ inline size_t work_doubles(int K, int n_T, int R) {
+    return (size_t)R * (3 * (size_t)K + 2 * (size_t)n_T + 2);
+}
+
+__host__ __device__ inline Work carve(double* base, int K, int n_T, int R) {
+    Work w;
+    w.S = base;
+    w.beta = w.S + (size_t)R * K;
+    w.CV = w.beta + (size_t)R * K;
+    w.ET = w.CV + (size_t)R * K;
+    w.cVT = w.ET + (size_t)R * n_T;
+    w.peak = w.cVT + (size_t)R * n_T;
+    return w;
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (l < nw) ? red[l] : -INFINITY;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+        if (l == 0) red[0] = v;
+    }
+    __syncthreads();
+    double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+// H_k of replicate r (block r-1 left out for r >= 1); -1 when no histogram.
+__device__ __forceinline__ double rep_hist(const unsigned long long* hist, int n_blocks, int K, int r, int k) {
+    if (!hist) return -1.0;
+    unsigned long long s = 0;
+    for (int b = 0; b < n_blocks; ++b)
+        if (b != r - 1) s += hist[(int64_t)b * K + k];
+    return (double)s;
+}
+
+__global__ void __launch_bounds__(kThreads)
+entropy_kernel(int K, double w, const double* __restrict__ lnW, const unsigned long long* __restrict__ hist,
+               int n_blocks, int h, Work wk) {
+    __shared__ double red[32];
+    const int r = blockIdx.x;
+    double* S = wk.S + (size_t)r * K;
+    double* beta = wk.beta + (size_t)r * K;
+    double* CV = wk.CV + (size_t)r * K;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    double mx = -INFINITY;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double H = rep_hist(hist, n_blocks, K, r, k);
+        double s = nan;
+        if (H < 0.0) s = -lnW[k];
+        else if (H > 0.0) s = -lnW[k] + log(H);
+        S[k] = s;
+        if (!isnan(s)) mx = fmax(mx, s);
+    }
+    mx = block_max(mx, red);
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+        if (!isnan(S[k])) S[k] -= mx;
+    __syncthreads();
+    const double he = (double)h * w;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        double b = nan, cv = nan;
+        if (k - h >= 0 && k + h < K && !isnan(S[k - h]) && !isnan(S[k + h])) {
+            b = (S[k + h] - S[k - h]) / (2.0 * he);
+            if (!isnan(S[k])) {
+                double s2 = (S[k + h] - 2.0 * S[k] + S[k - h]) / (he * he);
+                cv = -(b * b) / s2;
+            }
+        }
+        beta[k] = b;
+        CV[k] = cv;
+    }
+}
+
+__global__ void __launch_bounds__(256)
+canonical_kernel(int K, double e_min, double w, const double* __restrict__ T, int n_T, int n_monomers, Work wk) {
+    __shared__ double red[32];
+    const int i = blockIdx.x, r = blockIdx.y;
+    const double* S = wk.S + (size_t)r * K;
+    const double Ti = T[i];
+    double lmax = -INFINITY;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        if (isnan(S[k])) continue;
+        double Ek = e_min + ((double)k + 0.5) * w;
+        lmax = fmax(lmax, S[k] - Ek / Ti);
+    }
+    lmax = block_max(lmax, red);
+    double Z = 0.0, sE = 0.0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        if (isnan(S[k])) continue;
+        double Ek = e_min + ((double)k + 0.5) * w;
+        double p = exp(S[k] - Ek / Ti - lmax);
+        Z += p;
+        sE += p * Ek;
+    }
+    Z = block_sum(Z, red);
+    sE = block_sum(sE, red);
+    const double mean = sE / Z;
+    double var = 0.0;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        if (isnan(S[k])) continue;
+        double Ek = e_min + ((double)k + 0.5) * w;
+        double p = exp(S[k] - Ek / Ti - lmax);
+        var += p * (Ek - mean) * (Ek - mean);
+    }
+    var = block_sum(var, red) / Z;
+    if (threadIdx.x == 0) {
+        wk.ET[(size_t)r * n_T + i] = mean;
+        wk.cVT[(size_t)r * n_T + i] = var / ((double)n_monomers * Ti * Ti);
+    }
+}
+
+__device__ __forceinline__ void jackknife(const double* v, size_t stride, int n, double* val, double* err,
+                                          size_t idx) {
+    // v[0] full estimate, v[r * stride] leave-block-(r-1)-out replicates
+    if (val) val[idx] = v[0];
+    if (!err) return;
+    if (n < 2) { err[idx] = __longlong_as_double(0x7ff8000000000000ll); return; }
+    double m = 0.0;
+    for (int r = 1; r <= n; ++r) m += v[r * stride];
+    m /= n;
+    double s = 0.0;
+    for (int r = 1; r <= n; ++r) s += (v[r * stride] - m) * (v[r * stride] - m);
+    err[idx] = sqrt((double)(n - 1) / n * s);
+}
+
+__global__ void __launch_bounds__(kThreads)
+finish_kernel(int K, const double* __restrict__ T, int n_T, int R, int n_jk, Work wk, phast_micro_out o) {
+    // c_V peak of each replicate: grid maximum, refined by a parabola through it and its neighbours
+    for (int r = threadIdx.x; r < R; r += blockDim.x) {
+        const double* c = wk.cVT + (size_t)r * n_T;
+        double* pk = wk.peak + 2 * (size_t)r;
+        if (n_T < 1) { pk[0] = pk[1] = __longlong_as_double(0x7ff8000000000000ll); continue; }
+        int im = 0;
+        for (int i = 1; i < n_T; ++i) if (c[i] > c[im]) im = i;
+        pk[0] = T[im];
+        pk[1] = c[im];
+        if (im > 0 && im < n_T - 1) {
+            double x0 = T[im - 1], x1 = T[im], x2 = T[im + 1], y0 = c[im - 1], y1 = c[im], y2 = c[im + 1];
+            double num = (x1 - x0) * (x1 - x0) * (y1 - y2) - (x1 - x2) * (x1 - x2) * (y1 - y0);
+            double den = (x1 - x0) * (y1 - y2) - (x1 - x2) * (y1 - y0);
+            if (den != 0.0) {
+                double xs = x1 - 0.5 * num / den;
+                pk[0] = xs;
+                pk[1] = y0 * (xs - x1) * (xs - x2) / ((x0 - x1) * (x0 - x2)) +
+                        y1 * (xs - x0) * (xs - x2) / ((x1 - x0) * (x1 - x2)) +
+                        y2 * (xs - x0) * (xs - x1) / ((x2 - x0) * (x2 - x1));
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        jackknife(wk.S + k, (size_t)K, n_jk, o.S, o.S_err, k);
+        jackknife(wk.beta + k, (size_t)K, n_jk, o.beta, o.beta_err, k);
+        jackknife(wk.CV + k, (size_t)K, n_jk, o.CV, o.CV_err, k);
+    }
+    for (int i = threadIdx.x; i < n_T; i += blockDim.x) {
+        jackknife(wk.ET + i, (size_t)n_T, n_jk, o.E_T, o.E_T_err, i);
+        jackknife(wk.cVT + i, (size_t)n_T, n_jk, o.cV_T, o.cV_T_err, i);
+    }
+    if (threadIdx.x < 2) jackknife(wk.peak + threadIdx.x, 2, n_jk, o.peak, o.peak_err, threadIdx.x);
+}
+
+}  // namespace
+
+extern "C" size_t phast_micro_workspace_size(int32_t K, int32_t n_T, int32_t n_blocks) {
+    if (K < 1 || n_T < 0 || n_blocks < 0) return 0;
+    int R = 1 + (n_blocks >= 2 ? n_blocks : 0);
+    return sizeof(double) * work_doubles(K, n_T, R);
+}
+
+extern "C" int phast_micro_analysis(int32_t K, double e_min, double bin_width, const double* lnW, const uint64_t* hist,
+                                    int32_t n_blocks, int32_t h, int32_t n_monomers, int32_t n_T, const double* T,
+                                    const phast_micro_out* out, void* workspace, size_t workspace_bytes,
+                                    void* stream) {
+    if (K < 1 || K > PHAST_MAX_BINS) return phast_set_error(PHAST_EINVAL, "phast_micro_analysis: K %d outside [1, %d]", K, PHAST_MAX_BINS);
+    if (!(bin_width > 0.0) || !isfinite(e_min)) return phast_set_error(PHAST_EINVAL, "phast_micro_analysis: bad bins");
+    if (h < 1 || 2 * h >= K) return phast_set_error(PHAST_EINVAL, "phast_micro_analysis: fd_half_width %d outside [1, K/2)", h);
+    if (n_monomers < 1) return phast_set_error(PHAST_EINVAL, "phast_micro_analysis: n_monomers < 1");
+    if (n_T < 0 || (n_T > 0 && !T)) return phast_set_error(PHAST_EINVAL, "phast_micro_analysis: bad temperature grid");
+    if (!lnW || !out) return phast_set_error(PHAST_EINVAL, "phast_micro_analysis: NULL argument");
+    if (hist && n_blocks < 1) return phast_set_error(PHAST_EINVAL, "phast_micro_analysis: n_blocks < 1");
+    if (!hist) n_blocks = 0;
+    const int R = 1 + (n_blocks >= 2 ? n_blocks : 0);
+    const size_t need = sizeof(double) * work_doubles(K, n_T, R);
+    if (!workspace || workspace_bytes < need)
+        return phast_set_error(PHAST_EINVAL, "phast_micro_analysis: workspace of %zu bytes < %zu", workspace_bytes, need);
+    cudaStream_t st = (cudaStream_t)stream;
+    Work wk = carve((double*)workspace, K, n_T, R);
+    const int njk = n_blocks >= 2 ? n_blocks : 0;
+    entropy_kernel<<<R, kThreads, 0, st>>>(K, bin_width, lnW, reinterpret_cast<const unsigned long long*>(hist),
+                                           n_blocks, h, wk);
+    PHAST_CUDA_TRY(cudaGetLastError());
+    if (n_T > 0) {
+        canonical_kernel<<<dim3(n_T, R), 256, 0, st>>>(K, e_min, bin_width, T, n_T, n_monomers, wk);
+        PHAST_CUDA_TRY(cudaGetLastError());
+    }
+    finish_kernel<<<1, kThreads, 0, st>>>(K, T, n_T, R, njk, wk, *out);
+    PHAST_CUDA_TRY(cudaGetLastError());
+    return PHAST_OK;
+}

@@ -1,0 +1,291 @@
+// common.cuh -- device building blocks shared by the PHAST kernels (sm_103a):
+// system descriptors, the Philox4x32-10 walker stream, FP64 move geometry with
+// explicitly rounded operations, FP64 bending/torsion terms, the bin map, and
+// host-side error reporting.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "phast.h"
+
+#define PHAST_STREAM_TAG 0x4D554341u   // counter word 3 of every walker-stream block
+#define PHAST_MARSAGLIA_TRIES 64
+
+// ---------------------------------------------------------------------------
+// Host-side errors (thread-local message; every entry point returns a code).
+// ---------------------------------------------------------------------------
+int phast_set_error(int code, const char* fmt, ...);
+#define PHAST_CUDA_TRY(call)                                                            \
+    do {                                                                                \
+        cudaError_t err_ = (call);                                                      \
+        if (err_ != cudaSuccess)                                                        \
+            return phast_set_error(PHAST_ECUDA, "%s: %s (%s:%d)", #call,               \
+                                   cudaGetErrorString(err_), __FILE__, __LINE__);       \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// System descriptor: one system type with its force field and MUCA set-up,
+// flattened for the device.  Built once on the host from the ABI structs.
+// ---------------------------------------------------------------------------
+struct SysDesc {
+    int32_t n_chains, N, n_bins, recompute_every;
+    int32_t walker_off, n_walkers, lnw_off, max_chain;
+    int32_t pair_precision, n_tiles, tile_off, pad0;
+    int64_t xyz_off;      // offset of walker 0's coordinates in the concatenated xyz (doubles)
+    int64_t hw_off;       // offset of walker 0's histogram in hist_walker (bins)
+    double box_L, inv_L;  // inv_L = 0 for open systems
+    double k_bend, k_tors, k_lj_intra, k_lj_inter;
+    double C[4];
+    double e_min, bin_width;
+    double p[4], amax[4];
+    int32_t chain_off[PHAST_MAX_CHAINS + 1];
+    int32_t pad1[3];
+    uint8_t seq[PHAST_MAX_MONOMERS];
+    uint8_t chain_of[PHAST_MAX_MONOMERS];
+};
+static_assert(sizeof(SysDesc) % 16 == 0, "SysDesc must be 16-byte sized for vector copies");
+
+// Validates the ABI structs and fills a descriptor (offsets left at 0).
+int phast_build_desc(const phast_system* sys, const phast_ff* ff, const phast_muca_params* mp,
+                     SysDesc* d, const char* what);
+
+// ---------------------------------------------------------------------------
+// Explicitly rounded FP64 arithmetic: the geometry below must round exactly
+// as the specification states (no contraction into FMA), so that coordinates
+// are reproducible bit for bit by any IEEE-754 implementation of it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double xadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double xsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double xdiv(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double xsqrt(double a) { return __dsqrt_rn(a); }
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Block b of move t of the walker keyed by `seed`.
+__device__ __forceinline__ uint4 stream_block(uint64_t seed, uint64_t t, uint32_t b) {
+    return philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), b, PHAST_STREAM_TAG),
+                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// Uniform in (0,1) from 52 bits, exact: ((a>>6) 2^26 + (b>>6) + 1/2) 2^-52.
+__device__ __forceinline__ double u52(uint32_t a, uint32_t b) {
+    double n = xadd(xmul((double)(a >> 6), 67108864.0), (double)(b >> 6));
+    return xmul(xadd(n, 0.5), 2.220446049250313080847263336181640625e-16);
+}
+
+// sin and cos of |a| <= 1 by their Taylor series, Horner in a^2 with separately
+// rounded operations; coefficients are the correctly rounded (-1)^i/(2i+1)! and
+// (-1)^i/(2i)!.
+__device__ __forceinline__ void taylor_sincos(double a, double* s, double* c) {
+    const double S[9] = {1.0, -1.0 / 6.0, 1.0 / 120.0, -1.0 / 5040.0, 1.0 / 362880.0,
+                         -1.0 / 39916800.0, 1.0 / 6227020800.0, -1.0 / 1307674368000.0,
+                         1.0 / 355687428096000.0};
+    const double Cc[10] = {1.0, -1.0 / 2.0, 1.0 / 24.0, -1.0 / 720.0, 1.0 / 40320.0,
+                           -1.0 / 3628800.0, 1.0 / 479001600.0, -1.0 / 87178291200.0,
+                           1.0 / 20922789888000.0, -1.0 / 6402373705728000.0};
+    double x2 = xmul(a, a);
+    double ps = S[8];
+#pragma unroll
+    for (int i = 7; i >= 0; --i) ps = xadd(xmul(ps, x2), S[i]);
+    double pc = Cc[9];
+#pragma unroll
+    for (int i = 8; i >= 0; --i) pc = xadd(xmul(pc, x2), Cc[i]);
+    *s = xmul(a, ps);
+    *c = pc;
+}
+
+// Rodrigues' matrix about unit axis k, angle with sine s and cosine c.
+struct Rot3 { double m[9]; };
+__device__ __forceinline__ Rot3 rodrigues(double kx, double ky, double kz, double s, double c) {
+    double t = xsub(1.0, c);
+    double tx = xmul(t, kx), ty = xmul(t, ky), tz = xmul(t, kz);
+    Rot3 R;
+    R.m[0] = xadd(xmul(tx, kx), c);
+    R.m[1] = xsub(xmul(tx, ky), xmul(s, kz));
+    R.m[2] = xadd(xmul(tx, kz), xmul(s, ky));
+    R.m[3] = xadd(xmul(ty, kx), xmul(s, kz));
+    R.m[4] = xadd(xmul(ty, ky), c);
+    R.m[5] = xsub(xmul(ty, kz), xmul(s, kx));
+    R.m[6] = xsub(xmul(tz, kx), xmul(s, ky));
+    R.m[7] = xadd(xmul(tz, ky), xmul(s, kx));
+    R.m[8] = xadd(xmul(tz, kz), c);
+    return R;
+}
+
+// x' = p + R (x - p), rows summed left to right.
+__device__ __forceinline__ double3 rotate_about(const Rot3& R, double3 p, double3 x) {
+    double v0 = xsub(x.x, p.x), v1 = xsub(x.y, p.y), v2 = xsub(x.z, p.z);
+    double w0 = xadd(xadd(xmul(R.m[0], v0), xmul(R.m[1], v1)), xmul(R.m[2], v2));
+    double w1 = xadd(xadd(xmul(R.m[3], v0), xmul(R.m[4], v1)), xmul(R.m[5], v2));
+    double w2 = xadd(xadd(xmul(R.m[6], v0), xmul(R.m[7], v1)), xmul(R.m[8], v2));
+    return make_double3(xadd(p.x, w0), xadd(p.y, w1), xadd(p.z, w2));
+}
+
+// One Marsaglia (1972) attempt from block (a, b, c, d): returns true and the
+// isotropic unit axis if (v1, v2) falls inside the unit disc.
+__device__ __forceinline__ bool marsaglia_try(uint4 r, double3* axis) {
+    double v1 = xsub(xmul(2.0, u52(r.x, r.y)), 1.0);
+    double v2 = xsub(xmul(2.0, u52(r.z, r.w)), 1.0);
+    double s = xadd(xmul(v1, v1), xmul(v2, v2));
+    if (s < 1.0 && s > 0.0) {
+        double q = xsqrt(xsub(1.0, s));
+        *axis = make_double3(xmul(xmul(2.0, v1), q), xmul(xmul(2.0, v2), q), xsub(1.0, xmul(2.0, s)));
+        return true;
+    }
+    return false;
+}
+
+// A proposed move, drawn from the walker stream.
+struct Proposal {
+    int type, chain, index;
+    double angle, u_acc;
+    double3 axis, disp;
+};
+
+// Selection part of move t (blocks 0-2): type by comparing a uniform with the
+// running sum of the type probabilities (the last type with p > 0 catches the
+// rounding remainder), uniform chain, interior monomer 1..n-2 for pivot and
+// crankshaft, amplitude uniform in [-amax, amax].  The axis is set separately.
+__device__ __forceinline__ void propose_select(const SysDesc& d, uint4 b0, uint4 b1, uint4 b2,
+                                               Proposal* P) {
+    double u_type = u52(b0.x, b0.y);
+    double u_a = u52(b1.x, b1.y), u_b = u52(b1.z, b1.w), u_c = u52(b2.x, b2.y);
+    P->u_acc = u52(b2.z, b2.w);
+    int type = -1, last = 0;
+    double cum = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        cum = xadd(cum, d.p[i]);
+        if (d.p[i] > 0.0) {
+            last = i;
+            if (type < 0 && u_type < cum) type = i;
+        }
+    }
+    if (type < 0) type = last;
+    P->type = type;
+    P->chain = (int)(((uint64_t)b0.z * (uint64_t)d.n_chains) >> 32);
+    int n = d.chain_off[P->chain + 1] - d.chain_off[P->chain];
+    P->index = (type == PHAST_PIVOT || type == PHAST_CRANK)
+                   ? 1 + (int)(((uint64_t)b0.w * (uint64_t)(n - 2)) >> 32) : 0;
+    P->angle = 0.0;
+    P->disp = make_double3(0.0, 0.0, 0.0);
+    P->axis = make_double3(0.0, 0.0, 1.0);
+    if (type == PHAST_TRANS) {
+        double a = d.amax[PHAST_TRANS];
+        P->disp = make_double3(xmul(xsub(xmul(2.0, u_a), 1.0), a), xmul(xsub(xmul(2.0, u_b), 1.0), a),
+                               xmul(xsub(xmul(2.0, u_c), 1.0), a));
+    } else {
+        P->angle = xmul(xsub(xmul(2.0, u_a), 1.0), d.amax[type]);
+    }
+}
+
+// Moved monomer range [lo, hi] (system indices) and the fixed point excluded
+// from the pair set (the pivot; -1 otherwise) of a move.
+__device__ __forceinline__ void moved_range(const SysDesc& d, int type, int chain, int index,
+                                            int* lo, int* hi, int* fixed) {
+    int o = d.chain_off[chain], n = d.chain_off[chain + 1] - o;
+    *fixed = -1;
+    if (type == PHAST_TRANS || type == PHAST_ROT) { *lo = o; *hi = o + n - 1; return; }
+    if (type == PHAST_CRANK) { *lo = *hi = o + index; return; }
+    *fixed = o + index;
+    if (index < n - 1 - index) { *lo = o; *hi = o + index - 1; }
+    else { *lo = o + index + 1; *hi = o + n - 1; }
+}
+
+// Energy bin of E: floor((E - e_min) / w) or -1 (out of range / non-finite).
+__device__ __forceinline__ int bin_of(const SysDesc& d, double E) {
+    if (!isfinite(E)) return -1;
+    double q = xdiv(xsub(E, d.e_min), d.bin_width);
+    if (!(q >= 0.0 && q < (double)d.n_bins)) return -1;
+    return (int)floor(q);
+}
+
+// ---------------------------------------------------------------------------
+// FP64 local terms.  Positions come from a functor pos(j) -> double3.
+// ---------------------------------------------------------------------------
+template <class Pos>
+__device__ __forceinline__ double bend_term(const Pos& pos, int o, int k) {
+    // 1 - cos(theta_k), theta_k between bonds (k-1 -> k) and (k -> k+1) of the chain at o
+    double3 x0 = pos(o + k - 1), x1 = pos(o + k), x2 = pos(o + k + 1);
+    double ax = x1.x - x0.x, ay = x1.y - x0.y, az = x1.z - x0.z;
+    double bx = x2.x - x1.x, by = x2.y - x1.y, bz = x2.z - x1.z;
+    double ab = ax * bx + ay * by + az * bz;
+    double aa = ax * ax + ay * ay + az * az, bb = bx * bx + by * by + bz * bz;
+    return 1.0 - ab / (sqrt(aa) * sqrt(bb));
+}
+
+template <class Pos>
+__device__ __forceinline__ double torsion_term(const Pos& pos, int o, int j) {
+    // cos(tau_j) of monomers j..j+3; 0 when a normal degenerates
+    double3 x0 = pos(o + j), x1 = pos(o + j + 1), x2 = pos(o + j + 2), x3 = pos(o + j + 3);
+    double b0x = x1.x - x0.x, b0y = x1.y - x0.y, b0z = x1.z - x0.z;
+    double b1x = x2.x - x1.x, b1y = x2.y - x1.y, b1z = x2.z - x1.z;
+    double b2x = x3.x - x2.x, b2y = x3.y - x2.y, b2z = x3.z - x2.z;
+    double n1x = b0y * b1z - b0z * b1y, n1y = b0z * b1x - b0x * b1z, n1z = b0x * b1y - b0y * b1x;
+    double n2x = b1y * b2z - b1z * b2y, n2y = b1z * b2x - b1x * b2z, n2z = b1x * b2y - b1y * b2x;
+    double n12 = n1x * n2x + n1y * n2y + n1z * n2z;
+    double n11 = n1x * n1x + n1y * n1y + n1z * n1z, n22 = n2x * n2x + n2y * n2y + n2z * n2z;
+    if (n11 * n22 < 1e-20) return 0.0;
+    return n12 / (sqrt(n11) * sqrt(n22));
+}
+
+// Local (bending + torsion) items a move changes.  Items 0..nb-1 are bends at
+// vertices vb0.., items nb.. are dihedrals starting at jt0..; returns the count.
+__device__ __forceinline__ void local_window(const SysDesc& d, int type, int chain, int index,
+                                             int* vb0, int* nb, int* jt0, int* nt) {
+    int n = d.chain_off[chain + 1] - d.chain_off[chain];
+    *nb = 0; *nt = 0; *vb0 = 0; *jt0 = 0;
+    if (type == PHAST_PIVOT) {
+        *vb0 = index; *nb = 1;
+        int a = max(index - 2, 0), b = min(index - 1, n - 4);
+        *jt0 = a; *nt = max(b - a + 1, 0);
+    } else if (type == PHAST_CRANK) {
+        int a = max(index - 1, 1), b = min(index + 1, n - 2);
+        *vb0 = a; *nb = max(b - a + 1, 0);
+        int c = max(index - 3, 0), e = min(index, n - 4);
+        *jt0 = c; *nt = max(e - c + 1, 0);
+    }
+}
+
+// Lennard-Jones pair of Eq. 2/3 without its coupling: r^-12 - C r^-6 (FP64).
+__device__ __forceinline__ double lj64(double r2, double C) {
+    double ir2 = 1.0 / r2;
+    double ir6 = ir2 * ir2 * ir2;
+    return ir6 * (ir6 - C);
+}
+
+// Minimum-image component (FP64); inv_L = 0 leaves d unchanged.
+__device__ __forceinline__ double mimage64(double dx, double L, double inv_L) {
+    return dx - L * rint(dx * inv_L);
+}
+
+// Block-wide FP64 sum; every thread gets the result.  red: >= 32 doubles of shared.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = (l < nw) ? red[l] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (l == 0) red[0] = v;
+    }
+    __syncthreads();
+    double r = red[0];
+    __syncthreads();
+    return r;
+}

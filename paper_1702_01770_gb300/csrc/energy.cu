@@ -1,0 +1,131 @@
+// energy.cu -- phast_energy (Eq. 2/3 total energy of a batch of
+// configurations) and phast_delta_energy (energy change of explicit moves).
+// One warp per configuration or move, using the same group machinery as the
+// sweep, so these entry points exercise the sweep's own arithmetic.
+#include "group.cuh"
+
+namespace {
+
+constexpr int kWarpsPerBlock = 4;
+
+template <typename PT>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+energy_kernel(const SysDesc d, int B, const double* __restrict__ xyz, double* __restrict__ E_out, SlotLayout L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    Group<32> g;
+    const int w = threadIdx.x >> 5;
+    const int b = blockIdx.x * kWarpsPerBlock + w;
+    if (b >= B) return;
+    const double* x64 = xyz + (size_t)b * d.N * 3;
+    double E;
+    if (sizeof(PT) == 8) {
+        E = full_energy64<32>(d, x64, g);
+    } else {
+        Slot<PT> s(smem + (size_t)w * L.bytes, L);
+        build_working<32, PT>(d, x64, s, g);
+        E = full_energy_working<32, PT>(d, x64, s, g);
+    }
+    if (g.lane == 0) E_out[b] = E;
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+delta_kernel(const SysDesc d, int B, const double* __restrict__ xyz, const phast_move* __restrict__ moves,
+             double* __restrict__ dE_out, double* __restrict__ xyz_new, SlotLayout L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    Group<32> g;
+    const int w = threadIdx.x >> 5;
+    const int b = blockIdx.x * kWarpsPerBlock + w;
+    if (b >= B) return;
+    const double* x64 = xyz + (size_t)b * d.N * 3;
+    Slot<PT> s(smem + (size_t)w * L.bytes, L);
+    build_working<32, PT>(d, x64, s, g);
+    const phast_move mv = moves[b];
+    Proposal P;
+    P.type = mv.type; P.chain = mv.chain; P.index = mv.index;
+    P.angle = mv.angle; P.u_acc = 0.0;
+    P.axis = make_double3(mv.axis[0], mv.axis[1], mv.axis[2]);
+    P.disp = make_double3(mv.disp[0], mv.disp[1], mv.disp[2]);
+    // a move outside the system (type, chain, interior index, amplitude) is
+    // reported as NaN instead of being applied
+    bool valid = P.type >= 0 && P.type <= 3 && P.chain >= 0 && P.chain < d.n_chains;
+    if (valid) {
+        const int n = d.chain_off[P.chain + 1] - d.chain_off[P.chain];
+        if (P.type == PHAST_PIVOT || P.type == PHAST_CRANK) valid = P.index >= 1 && P.index <= n - 2;
+        if (P.type != PHAST_TRANS) valid = valid && fabs(P.angle) <= PHAST_MAX_ANGLE;
+        else valid = isfinite(P.disp.x) && isfinite(P.disp.y) && isfinite(P.disp.z);
+        if (P.type == PHAST_PIVOT || P.type == PHAST_ROT)
+            valid = valid && isfinite(P.axis.x) && isfinite(P.axis.y) && isfinite(P.axis.z);
+    }
+    if (!valid) P.type = PHAST_TRANS, P.chain = 0, P.index = 0;
+    const MoveSet M = move_set(d, P.type, P.chain, P.index);
+    double dE = __longlong_as_double(0x7ff8000000000000ll);   // NaN for a degenerate or invalid move
+    const bool ok = valid && make_new_positions<32, PT>(d, x64, P, M, s, g);
+    if (ok) {
+        double part = local_delta<32, PT>(d, x64, P, M, s, g) + pair_delta<32, PT, 4>(d, M, P.chain, s, g);
+        dE = g.sum(part);
+    }
+    if (g.lane == 0) dE_out[b] = dE;
+    if (xyz_new) {
+        double* out = xyz_new + (size_t)b * d.N * 3;
+        for (int k = g.lane; k < 3 * d.N; k += 32) {
+            int j = k / 3;
+            out[k] = (ok && j >= M.lo && j <= M.hi) ? s.new64[k - 3 * M.lo] : x64[k];
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int phast_energy(const phast_system* sys, const phast_ff* ff, int32_t B, const double* xyz,
+                            int32_t pair_precision, double* E_out, void* stream) {
+    SysDesc d;
+    int rc = phast_build_desc(sys, ff, nullptr, &d, "phast_energy");
+    if (rc) return rc;
+    if (B < 0) return phast_set_error(PHAST_EINVAL, "phast_energy: B < 0");
+    if (pair_precision != 32 && pair_precision != 64)
+        return phast_set_error(PHAST_EINVAL, "phast_energy: pair_precision must be 32 or 64");
+    if (B == 0) return PHAST_OK;
+    if (!xyz || !E_out) return phast_set_error(PHAST_EINVAL, "phast_energy: NULL xyz or E_out");
+    cudaStream_t st = (cudaStream_t)stream;
+    dim3 grid((B + kWarpsPerBlock - 1) / kWarpsPerBlock), block(32 * kWarpsPerBlock);
+    if (pair_precision == 64) {
+        SlotLayout L = slot_layout<double>(d.N, d.n_chains, d.max_chain);
+        energy_kernel<double><<<grid, block, 0, st>>>(d, B, xyz, E_out, L);
+    } else {
+        SlotLayout L = slot_layout<float>(d.N, d.n_chains, d.max_chain);
+        size_t sm = (size_t)L.bytes * kWarpsPerBlock;
+        PHAST_CUDA_TRY(cudaFuncSetAttribute(energy_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        energy_kernel<float><<<grid, block, sm, st>>>(d, B, xyz, E_out, L);
+    }
+    PHAST_CUDA_TRY(cudaGetLastError());
+    return PHAST_OK;
+}
+
+extern "C" int phast_delta_energy(const phast_system* sys, const phast_ff* ff, int32_t B, const double* xyz,
+                                  const phast_move* moves, int32_t pair_precision, double* dE_out,
+                                  double* xyz_new_out, void* stream) {
+    SysDesc d;
+    int rc = phast_build_desc(sys, ff, nullptr, &d, "phast_delta_energy");
+    if (rc) return rc;
+    if (B < 0) return phast_set_error(PHAST_EINVAL, "phast_delta_energy: B < 0");
+    if (pair_precision != 32 && pair_precision != 64)
+        return phast_set_error(PHAST_EINVAL, "phast_delta_energy: pair_precision must be 32 or 64");
+    if (B == 0) return PHAST_OK;
+    if (!xyz || !moves || !dE_out) return phast_set_error(PHAST_EINVAL, "phast_delta_energy: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    dim3 grid((B + kWarpsPerBlock - 1) / kWarpsPerBlock), block(32 * kWarpsPerBlock);
+    if (pair_precision == 64) {
+        SlotLayout L = slot_layout<double>(d.N, d.n_chains, d.max_chain);
+        size_t sm = (size_t)L.bytes * kWarpsPerBlock;
+        PHAST_CUDA_TRY(cudaFuncSetAttribute(delta_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        delta_kernel<double><<<grid, block, sm, st>>>(d, B, xyz, moves, dE_out, xyz_new_out, L);
+    } else {
+        SlotLayout L = slot_layout<float>(d.N, d.n_chains, d.max_chain);
+        size_t sm = (size_t)L.bytes * kWarpsPerBlock;
+        PHAST_CUDA_TRY(cudaFuncSetAttribute(delta_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        delta_kernel<float><<<grid, block, sm, st>>>(d, B, xyz, moves, dE_out, xyz_new_out, L);
+    }
+    PHAST_CUDA_TRY(cudaGetLastError());
+    return PHAST_OK;
+}

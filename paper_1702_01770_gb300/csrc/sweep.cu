@@ -1,0 +1,889 @@
+// sweep.cu -- the multicanonical sweep (Sec. 2.2; MONTE_CARLO.f / UPDATE_ENGINE.f
+// of Sec. 3.2) over many independent walkers, and the walker context.
+//
+//  * batched form: a persistent kernel; each CTA takes tiles of walkers of one
+//    system type (one jackknife block) from an atomic work counter, a group of
+//    TPW lanes runs one walker with its coordinates staged in shared memory,
+//    FP32 (or FP64) pair terms and FP64 totals, and all walkers of the CTA
+//    count into one shared-memory histogram flushed once per tile;
+//  * plain form: one CTA per walker, everything in FP64 straight from global
+//    memory, histogram atomics to global memory (the comparison form).
+// Both draw the same Philox stream and apply the same FP64 geometry, so their
+// decisions match the FP64 oracle move for move.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "group.cuh"
+
+struct phast_ctx {
+    int n_sys;
+    int W;
+    int device;
+    SysDesc desc[PHAST_MAX_SYSTEMS];
+    SysDesc* d_desc;
+    int64_t xyz_total;    // doubles
+    int64_t lnw_total;
+    int64_t hw_total;     // bins of a per-walker histogram array
+    int max_N, max_nc, max_chain, max_bins;
+    double* xyz;
+    double* E;
+    int32_t* bin;
+    uint64_t* t;
+    uint64_t* seed;
+    phast_walker_stats* stats;
+    int32_t* tile_counter;
+    double* plain_scratch;   // [W][max_chain][3] new positions of the plain form
+    int tpw, wpc;
+    int order[PHAST_MAX_SYSTEMS];   // tile order: most expensive system types first
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Launch arguments (by value).
+// ---------------------------------------------------------------------------
+struct SweepArgs {
+    const SysDesc* descs;
+    int n_sys, n_jk, wpc, n_tiles;
+    int64_t n_sweeps;
+    int order[PHAST_MAX_SYSTEMS];
+    int tile_start[PHAST_MAX_SYSTEMS + 1];
+    int tpb[PHAST_MAX_SYSTEMS];          // tiles per jackknife block, by enumeration position
+    int64_t hs_off[PHAST_MAX_SYSTEMS];   // hist_sum offset of each system id
+    double* xyz;
+    double* E;
+    int32_t* bin;
+    uint64_t* t;
+    const uint64_t* seed;
+    phast_walker_stats* stats;
+    const double* lnW;
+    unsigned long long* hist_sum;
+    uint32_t* hist_walker;
+    phast_trace* trace;
+    int trace_walkers;
+    int32_t* tile_counter;
+    double* scratch;
+    int scratch_stride;                   // doubles per walker in scratch
+    SlotLayout L;
+    int hist_bins;                        // shared histogram capacity (max n_bins)
+};
+
+__device__ __forceinline__ void copy_desc(SysDesc* dst, const SysDesc* src) {
+    const int4* s = reinterpret_cast<const int4*>(src);
+    int4* d = reinterpret_cast<int4*>(dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(SysDesc) / 16); i += blockDim.x) d[i] = s[i];
+}
+
+// Jackknife block of walker w of a type with W walkers split into n blocks
+// [b W / n, (b+1) W / n).
+__host__ __device__ __forceinline__ int jk_block(int w, int W, int n) {
+    return (int)(((int64_t)(w + 1) * n - 1) / W);
+}
+
+// ---------------------------------------------------------------------------
+// Initial energies: one warp per walker, FP64.
+// ---------------------------------------------------------------------------
+__global__ void init_energy_kernel(const SysDesc* __restrict__ descs, int n_sys, int W, const double* xyz,
+                                   double* E, int32_t* bin) {
+    Group<32> g;
+    const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gw >= W) return;
+    int s = 0;
+    while (s + 1 < n_sys && gw >= descs[s + 1].walker_off) ++s;
+    const SysDesc& d = descs[s];
+    const double* x64 = xyz + d.xyz_off + (int64_t)(gw - d.walker_off) * d.N * 3;
+    double e = full_energy64<32>(d, x64, g);
+    if (g.lane == 0) {
+        E[gw] = e;
+        bin[gw] = bin_of(d, e);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Batched form.
+// ---------------------------------------------------------------------------
+template <int TPW, typename PT>
+__device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int w_local, Slot<PT>& slot,
+                           uint32_t* hist, const Group<TPW>& g) {
+    const int gw = sd.walker_off + w_local;
+    double* x64 = a.xyz + sd.xyz_off + (int64_t)w_local * sd.N * 3;
+    const double* lnW = a.lnW + sd.lnw_off;
+    double E = a.E[gw];
+    int bin = a.bin[gw];
+    uint64_t t = a.t[gw];
+    const uint64_t seed = a.seed[gw];
+    uint64_t att[4] = {0, 0, 0, 0}, acc_n[4] = {0, 0, 0, 0}, pev = 0, nrec = 0;
+    double drift_max = 0.0;
+    uint32_t* hw = a.hist_walker ? a.hist_walker + sd.hw_off + (int64_t)w_local * sd.n_bins : nullptr;
+    const bool tracing = a.trace && s_id == 0 && w_local < a.trace_walkers;
+    const int64_t n_moves = a.n_sweeps * sd.N;
+    const uint64_t period = (uint64_t)sd.recompute_every * (uint64_t)sd.N;
+
+    build_working<TPW, PT>(sd, x64, slot, g);
+    for (int64_t it = 0; it < n_moves; ++it) {
+        const Proposal P = propose_group<TPW>(sd, seed, t, g);
+        const MoveSet M = move_set(sd, P.type, P.chain, P.index);
+        const bool ok = make_new_positions<TPW, PT>(sd, x64, P, M, slot, g);
+        double dE = __longlong_as_double(0x7ff8000000000000ll);
+        if (ok) {
+            double part = local_delta<TPW, PT>(sd, x64, P, M, slot, g) +
+                          pair_delta<TPW, PT, 4>(sd, M, P.chain, slot, g);
+            dE = g.sum(part);
+        }
+        const double E_new = E + dE;
+        const int b_new = bin_of(sd, E_new);
+        bool acc = false;
+        if (b_new >= 0) {
+            const double dl = __ldg(lnW + b_new) - __ldg(lnW + bin);
+            acc = (dl >= 0.0) || (P.u_acc < exp(dl));
+        }
+        if (acc) {
+            const int m = M.hi - M.lo + 1;
+            for (int q = g.lane; q < m; q += TPW) {
+                const int j = M.lo + q;
+                x64[3 * j + 0] = slot.new64[3 * q + 0];
+                x64[3 * j + 1] = slot.new64[3 * q + 1];
+                x64[3 * j + 2] = slot.new64[3 * q + 2];
+                slot.r[j] = slot.newr[q];
+            }
+            E = E_new;
+            bin = b_new;
+        }
+        g.sync();
+        if (g.lane == 0) {
+            atomicAdd(hist + bin, 1u);
+            if (hw) atomicAdd(hw + bin, 1u);
+            att[P.type]++;
+            acc_n[P.type] += acc;
+            pev += move_pair_evals(sd, P.type, M);
+            if (tracing) {
+                phast_trace tr;
+                tr.dE = dE;
+                tr.bin_after = bin;
+                tr.accepted = acc;
+                a.trace[(int64_t)w_local * n_moves + it] = tr;
+            }
+        }
+        ++t;
+        if (period && (t % period) == 0) {   // FP64 full energy kills the drift of the running sum
+            const double Ef = full_energy64<TPW>(sd, x64, g);
+            drift_max = fmax(drift_max, fabs(E - Ef));
+            const int bf = bin_of(sd, Ef);
+            if (bf >= 0) { E = Ef; bin = bf; }
+            ++nrec;
+            g.sync();
+            build_working<TPW, PT>(sd, x64, slot, g);
+        }
+    }
+    if (g.lane == 0) {
+        a.E[gw] = E;
+        a.bin[gw] = bin;
+        a.t[gw] = t;
+        phast_walker_stats* st = a.stats + gw;
+        for (int i = 0; i < 4; ++i) { st->attempts[i] += att[i]; st->accepts[i] += acc_n[i]; }
+        st->pair_evals += pev;
+        st->recomputes += nrec;
+        st->drift_max = fmax(st->drift_max, drift_max);
+    }
+}
+
+constexpr int kMaxTileThreads = 512;
+
+template <int TPW, typename PT>
+__global__ void __launch_bounds__(kMaxTileThreads)
+sweep_batched_kernel(const SweepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_tile;
+    SysDesc& sd = *reinterpret_cast<SysDesc*>(smem);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + sizeof(SysDesc));
+    unsigned char* slots = smem + sizeof(SysDesc) + align16(4 * a.hist_bins);
+    const Group<TPW> g;
+    const int slot_id = threadIdx.x / TPW;
+    Slot<PT> slot(slots + (size_t)slot_id * a.L.bytes, a.L);
+
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= a.n_tiles) break;
+        int pos = 0;
+        while (pos + 1 < a.n_sys && tile >= a.tile_start[pos + 1]) ++pos;
+        const int s_id = a.order[pos];
+        copy_desc(&sd, a.descs + s_id);
+        __syncthreads();
+        for (int k = threadIdx.x; k < sd.n_bins; k += blockDim.x) hist[k] = 0u;
+        const int lt = tile - a.tile_start[pos];
+        const int blk = lt / a.tpb[pos], jt = lt % a.tpb[pos];
+        const int W = sd.n_walkers;
+        const int b_lo = (int)((int64_t)blk * W / a.n_jk), b_hi = (int)((int64_t)(blk + 1) * W / a.n_jk);
+        const int w_local = b_lo + jt * a.wpc + slot_id;
+        __syncthreads();
+        if (w_local < b_hi) run_walker<TPW, PT>(sd, a, s_id, w_local, slot, hist, g);
+        __syncthreads();
+        if (a.hist_sum) {
+            unsigned long long* hs = a.hist_sum + a.hs_off[s_id] + (int64_t)blk * sd.n_bins;
+            for (int k = threadIdx.x; k < sd.n_bins; k += blockDim.x)
+                if (hist[k]) atomicAdd(hs + k, (unsigned long long)hist[k]);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Plain form: one CTA per walker, FP64, global memory.
+// ---------------------------------------------------------------------------
+constexpr int kPlainThreads = 128;
+
+__device__ double block_full_energy64(const SysDesc& d, const double* x64, double* red) {
+    double part = 0.0;
+    auto pos = [&](int j) -> double3 { return ld3(x64 + 3 * j); };
+    for (int c = 0; c < d.n_chains; ++c) {
+        int o = d.chain_off[c], n = d.chain_off[c + 1] - o;
+        for (int k = 1 + threadIdx.x; k <= n - 2; k += blockDim.x) part += d.k_bend * bend_term(pos, o, k);
+        for (int j = threadIdx.x; j <= n - 4; j += blockDim.x) part -= d.k_tors * torsion_term(pos, o, j);
+    }
+    for (int i = 0; i < d.N; ++i) {
+        const double3 xi = pos(i);
+        const int ci = d.chain_of[i];
+        for (int j = i + 1 + threadIdx.x; j < d.N; j += blockDim.x) {
+            const int cj = d.chain_of[j];
+            if (ci == cj && j < i + 2) continue;
+            const double3 xj = pos(j);
+            double dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+            if (ci != cj) {
+                dx = mimage64(dx, d.box_L, d.inv_L);
+                dy = mimage64(dy, d.box_L, d.inv_L);
+                dz = mimage64(dz, d.box_L, d.inv_L);
+            }
+            part += (ci == cj ? d.k_lj_intra : d.k_lj_inter) *
+                    lj64(dx * dx + dy * dy + dz * dz, d.C[2 * d.seq[i] + d.seq[j]]);
+        }
+    }
+    return block_sum(part, red);
+}
+
+__global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepArgs a, int W_total) {
+    __shared__ __align__(16) SysDesc sd;
+    __shared__ double red[32];
+    __shared__ Proposal sP;
+    __shared__ double sR[9], sC[3];
+    __shared__ int s_ok, s_acc;
+    const int gw = blockIdx.x;
+    if (gw >= W_total) return;
+    int s_id = 0;
+    while (s_id + 1 < a.n_sys && gw >= a.descs[s_id + 1].walker_off) ++s_id;
+    copy_desc(&sd, a.descs + s_id);
+    __syncthreads();
+    const int w_local = gw - sd.walker_off;
+    double* x64 = a.xyz + sd.xyz_off + (int64_t)w_local * sd.N * 3;
+    double* nx = a.scratch + (int64_t)gw * a.scratch_stride;
+    const double* lnW = a.lnW + sd.lnw_off;
+    double E = a.E[gw];
+    int bin = a.bin[gw];
+    uint64_t t = a.t[gw];
+    const uint64_t seed = a.seed[gw];
+    uint64_t att[4] = {0, 0, 0, 0}, acc_n[4] = {0, 0, 0, 0}, pev = 0, nrec = 0;
+    double drift_max = 0.0;
+    unsigned long long* hs = a.hist_sum
+        ? a.hist_sum + a.hs_off[s_id] + (int64_t)jk_block(w_local, sd.n_walkers, a.n_jk) * sd.n_bins : nullptr;
+    uint32_t* hw = a.hist_walker ? a.hist_walker + sd.hw_off + (int64_t)w_local * sd.n_bins : nullptr;
+    const bool tracing = a.trace && s_id == 0 && w_local < a.trace_walkers;
+    const int64_t n_moves = a.n_sweeps * sd.N;
+    const uint64_t period = (uint64_t)sd.recompute_every * (uint64_t)sd.N;
+
+    for (int64_t it = 0; it < n_moves; ++it) {
+        if (threadIdx.x == 0) {   // proposal, serial Marsaglia, centre and rotation
+            Proposal P;
+            propose_select(sd, stream_block(seed, t, 0), stream_block(seed, t, 1), stream_block(seed, t, 2), &P);
+            if (P.type == PHAST_PIVOT || P.type == PHAST_ROT) {
+                double3 ax = make_double3(0.0, 0.0, 1.0);
+                for (int j = 0; j < PHAST_MARSAGLIA_TRIES; ++j)
+                    if (marsaglia_try(stream_block(seed, t, 3u + j), &ax)) break;
+                P.axis = ax;
+            }
+            const int o = sd.chain_off[P.chain], n = sd.chain_off[P.chain + 1] - o;
+            int ok = 1;
+            double3 center = make_double3(0, 0, 0), axis = P.axis;
+            if (P.type == PHAST_PIVOT) {
+                center = ld3(x64 + 3 * (o + P.index));
+            } else if (P.type == PHAST_ROT) {
+                double sx = 0.0, sy = 0.0, sz = 0.0;
+                for (int j = o; j < o + n; ++j) {
+                    sx = xadd(sx, x64[3 * j]); sy = xadd(sy, x64[3 * j + 1]); sz = xadd(sz, x64[3 * j + 2]);
+                }
+                center = make_double3(xdiv(sx, (double)n), xdiv(sy, (double)n), xdiv(sz, (double)n));
+            } else if (P.type == PHAST_CRANK) {
+                const int i = o + P.index;
+                double3 p0 = ld3(x64 + 3 * (i - 1)), p1 = ld3(x64 + 3 * (i + 1));
+                double ex = xsub(p1.x, p0.x), ey = xsub(p1.y, p0.y), ez = xsub(p1.z, p0.z);
+                double len = xsqrt(xadd(xadd(xmul(ex, ex), xmul(ey, ey)), xmul(ez, ez)));
+                if (!(len > 1e-12)) ok = 0;
+                else axis = make_double3(xdiv(ex, len), xdiv(ey, len), xdiv(ez, len));
+                center = p0;
+            }
+            if (P.type != PHAST_TRANS && ok) {
+                double sn, cs;
+                taylor_sincos(P.angle, &sn, &cs);
+                Rot3 R = rodrigues(axis.x, axis.y, axis.z, sn, cs);
+                for (int k = 0; k < 9; ++k) sR[k] = R.m[k];
+            }
+            sC[0] = center.x; sC[1] = center.y; sC[2] = center.z;
+            sP = P;
+            s_ok = ok;
+        }
+        __syncthreads();
+        const Proposal P = sP;
+        const MoveSet M = move_set(sd, P.type, P.chain, P.index);
+        const int m = M.hi - M.lo + 1;
+        const bool ok = s_ok;
+        double dE = __longlong_as_double(0x7ff8000000000000ll);
+        if (ok) {
+            Rot3 R;
+            for (int k = 0; k < 9; ++k) R.m[k] = sR[k];
+            const double3 center = make_double3(sC[0], sC[1], sC[2]);
+            for (int q = threadIdx.x; q < m; q += blockDim.x) {
+                const double3 x = ld3(x64 + 3 * (M.lo + q));
+                double3 y = (P.type == PHAST_TRANS)
+                    ? make_double3(xadd(x.x, P.disp.x), xadd(x.y, P.disp.y), xadd(x.z, P.disp.z))
+                    : rotate_about(R, center, x);
+                nx[3 * q] = y.x; nx[3 * q + 1] = y.y; nx[3 * q + 2] = y.z;
+            }
+            __syncthreads();
+            // local terms
+            int vb0, nb, jt0, nt;
+            local_window(sd, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt);
+            const int o = sd.chain_off[P.chain];
+            double part = 0.0;
+            for (int itm = threadIdx.x; itm < 2 * (nb + nt); itm += blockDim.x) {
+                const bool after = itm & 1;
+                const int k = itm >> 1;
+                auto pos = [&](int j) -> double3 {
+                    if (after && j >= M.lo && j <= M.hi) return ld3(nx + 3 * (j - M.lo));
+                    return ld3(x64 + 3 * j);
+                };
+                double term = (k < nb) ? sd.k_bend * bend_term(pos, o, vb0 + k)
+                                       : -sd.k_tors * torsion_term(pos, o, jt0 + (k - nb));
+                part += after ? term : -term;
+            }
+            // pairs (moved i, unmoved j), before and after
+            const int U = sd.N - m;
+            for (int64_t p = threadIdx.x; p < (int64_t)m * U; p += blockDim.x) {
+                const int q = (int)(p / U), tt = (int)(p % U);
+                const int i = M.lo + q, j = tt < M.lo ? tt : tt + m;
+                if (j == M.ex0 || j == M.ex1 || j == M.ex2) continue;
+                const bool inter = sd.chain_of[j] != P.chain;
+                const double C = sd.C[2 * sd.seq[i] + sd.seq[j]];
+                const double kap = inter ? sd.k_lj_inter : sd.k_lj_intra;
+                const double3 xj = ld3(x64 + 3 * j), xo = ld3(x64 + 3 * i), xn = ld3(nx + 3 * q);
+                double dx = xo.x - xj.x, dy = xo.y - xj.y, dz = xo.z - xj.z;
+                double ex = xn.x - xj.x, ey = xn.y - xj.y, ez = xn.z - xj.z;
+                if (inter) {
+                    dx = mimage64(dx, sd.box_L, sd.inv_L); dy = mimage64(dy, sd.box_L, sd.inv_L);
+                    dz = mimage64(dz, sd.box_L, sd.inv_L); ex = mimage64(ex, sd.box_L, sd.inv_L);
+                    ey = mimage64(ey, sd.box_L, sd.inv_L); ez = mimage64(ez, sd.box_L, sd.inv_L);
+                }
+                part += kap * (lj64(ex * ex + ey * ey + ez * ez, C) - lj64(dx * dx + dy * dy + dz * dz, C));
+            }
+            dE = block_sum(part, red);
+        }
+        if (threadIdx.x == 0) {
+            const double E_new = E + dE;
+            const int b_new = bin_of(sd, E_new);
+            int acc = 0;
+            if (b_new >= 0) {
+                const double dl = lnW[b_new] - lnW[bin];
+                acc = (dl >= 0.0) || (P.u_acc < exp(dl));
+            }
+            s_acc = acc;
+            if (acc) { E = E_new; bin = b_new; }
+            if (hs) atomicAdd(hs + bin, 1ull);
+            if (hw) atomicAdd(hw + bin, 1u);
+            att[P.type]++;
+            acc_n[P.type] += acc;
+            pev += move_pair_evals(sd, P.type, M);
+            if (tracing) {
+                phast_trace tr;
+                tr.dE = dE;
+                tr.bin_after = bin;
+                tr.accepted = acc;
+                a.trace[(int64_t)w_local * n_moves + it] = tr;
+            }
+        }
+        __syncthreads();
+        if (s_acc)
+            for (int q = threadIdx.x; q < 3 * m; q += blockDim.x) x64[3 * M.lo + q] = nx[q];
+        ++t;
+        __syncthreads();
+        if (period && (t % period) == 0) {
+            const double Ef = block_full_energy64(sd, x64, red);
+            if (threadIdx.x == 0) {
+                drift_max = fmax(drift_max, fabs(E - Ef));
+                const int bf = bin_of(sd, Ef);
+                if (bf >= 0) { E = Ef; bin = bf; }
+                ++nrec;
+            }
+        }
+    }
+    if (threadIdx.x == 0) {
+        a.E[gw] = E;
+        a.bin[gw] = bin;
+        a.t[gw] = t;
+        phast_walker_stats* st = a.stats + gw;
+        for (int i = 0; i < 4; ++i) { st->attempts[i] += att[i]; st->accepts[i] += acc_n[i]; }
+        st->pair_evals += pev;
+        st->recomputes += nrec;
+        st->drift_max = fmax(st->drift_max, drift_max);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+typedef void (*batched_fn)(const SweepArgs);
+
+batched_fn pick_batched(int tpw, bool fp32) {
+    switch (tpw) {
+        case 4: return fp32 ? sweep_batched_kernel<4, float> : sweep_batched_kernel<4, double>;
+        case 8: return fp32 ? sweep_batched_kernel<8, float> : sweep_batched_kernel<8, double>;
+        case 16: return fp32 ? sweep_batched_kernel<16, float> : sweep_batched_kernel<16, double>;
+        case 32: return fp32 ? sweep_batched_kernel<32, float> : sweep_batched_kernel<32, double>;
+        default: return nullptr;
+    }
+}
+
+size_t batched_smem(const phast_ctx* c, bool fp32, int wpc, SlotLayout* L) {
+    *L = fp32 ? slot_layout<float>(c->max_N, c->max_nc, c->max_chain)
+              : slot_layout<double>(c->max_N, c->max_nc, c->max_chain);
+    return sizeof(SysDesc) + (size_t)align16(4 * c->max_bins) + (size_t)wpc * L->bytes;
+}
+
+double system_cost(const SysDesc& d) {
+    // expected pair evaluations per sweep and walker, for ordering the tiles
+    double pv = 0.0, n = d.N;
+    for (int c = 0; c < d.n_chains; ++c) {
+        double nc = d.chain_off[c + 1] - d.chain_off[c];
+        pv += (d.p[PHAST_PIVOT] * nc / 4.0 * (n - nc / 4.0) + (d.p[PHAST_TRANS] + d.p[PHAST_ROT]) * nc * (n - nc) +
+               d.p[PHAST_CRANK] * n) / d.n_chains;
+    }
+    return pv * n * d.n_walkers + 1.0;
+}
+
+int fill_args(const phast_ctx* c, int64_t n_sweeps, const double* lnW, int n_jk, uint64_t* hist_sum,
+              uint32_t* hist_walker, phast_trace* trace, int trace_walkers, int wpc, SweepArgs* a) {
+    memset(a, 0, sizeof(*a));
+    a->descs = c->d_desc;
+    a->n_sys = c->n_sys;
+    a->n_jk = n_jk;
+    a->wpc = wpc;
+    a->n_sweeps = n_sweeps;
+    int64_t hs = 0;
+    for (int s = 0; s < c->n_sys; ++s) { a->hs_off[s] = hs; hs += (int64_t)n_jk * c->desc[s].n_bins; }
+    int tiles = 0;
+    for (int p = 0; p < c->n_sys; ++p) {
+        const int s = c->order[p];
+        const int W = c->desc[s].n_walkers;
+        const int maxblk = (W + n_jk - 1) / n_jk;
+        a->order[p] = s;
+        a->tile_start[p] = tiles;
+        a->tpb[p] = (maxblk + wpc - 1) / wpc;
+        tiles += a->tpb[p] * n_jk;
+    }
+    a->tile_start[c->n_sys] = tiles;
+    a->n_tiles = tiles;
+    a->xyz = c->xyz;
+    a->E = c->E;
+    a->bin = c->bin;
+    a->t = c->t;
+    a->seed = c->seed;
+    a->stats = c->stats;
+    a->lnW = lnW;
+    a->hist_sum = reinterpret_cast<unsigned long long*>(hist_sum);
+    a->hist_walker = hist_walker;
+    a->trace = trace;
+    a->trace_walkers = trace_walkers;
+    a->tile_counter = c->tile_counter;
+    a->scratch = c->plain_scratch;
+    a->scratch_stride = 3 * c->max_chain;
+    a->hist_bins = c->max_bins;
+    return PHAST_OK;
+}
+
+int launch_batched(phast_ctx* c, const SweepArgs& a0, int tpw, int wpc, bool fp32, cudaStream_t st) {
+    SweepArgs a = a0;
+    SlotLayout L;
+    size_t sm = batched_smem(c, fp32, wpc, &L);
+    a.L = L;
+    batched_fn fn = pick_batched(tpw, fp32);
+    if (!fn) return phast_set_error(PHAST_EINVAL, "threads per walker %d not in {4, 8, 16, 32}", tpw);
+    const int threads = tpw * wpc;
+    if (threads < 32 || threads > kMaxTileThreads || threads % 32)
+        return phast_set_error(PHAST_EINVAL, "tile of %d x %d threads is not a whole number of warps <= %d", tpw, wpc,
+                               kMaxTileThreads);
+    int max_sm = 0;
+    PHAST_CUDA_TRY(cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    if (sm + 64 > (size_t)max_sm)
+        return phast_set_error(PHAST_EINVAL, "tile needs %zu bytes of shared memory (> %d)", sm, max_sm);
+    PHAST_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0, n_sm = 0;
+    PHAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, sm));
+    PHAST_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
+    if (per_sm < 1) return phast_set_error(PHAST_EINVAL, "tile of %d x %d does not fit on an SM", tpw, wpc);
+    int grid = per_sm * n_sm;
+    if (grid > a.n_tiles) grid = a.n_tiles;
+    PHAST_CUDA_TRY(cudaMemsetAsync(c->tile_counter, 0, sizeof(int32_t), st));
+    fn<<<grid, threads, sm, st>>>(a);
+    PHAST_CUDA_TRY(cudaGetLastError());
+    return PHAST_OK;
+}
+
+void default_tile(const phast_ctx* c, int* tpw, int* wpc) {
+    // one warp per walker for large systems, smaller groups for small ones
+    const int N = c->max_N;
+    *tpw = N >= 128 ? 32 : (N >= 48 ? 16 : 8);
+    int w = 512 / *tpw;
+    SlotLayout L;
+    while (w > 1 && batched_smem(c, true, w, &L) > 200 * 1024) w >>= 1;
+    while (w > 1 && batched_smem(c, false, w, &L) > 220 * 1024 && *tpw * w > 32) w >>= 1;
+    if (*tpw * w < 32) w = 32 / *tpw;
+    *wpc = w;
+}
+
+uint32_t crc32(const unsigned char* p, size_t n, uint32_t crc) {
+    crc = ~crc;
+    for (size_t i = 0; i < n; ++i) {
+        crc ^= p[i];
+        for (int k = 0; k < 8; ++k) crc = (crc >> 1) ^ (0xEDB88320u & (0u - (crc & 1u)));
+    }
+    return ~crc;
+}
+
+struct CkptHeader {
+    uint32_t magic, version;
+    int32_t n_sys, W;
+    int64_t xyz_total;
+    int32_t N[PHAST_MAX_SYSTEMS];
+    int32_t walkers[PHAST_MAX_SYSTEMS];
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Entry points.
+// ---------------------------------------------------------------------------
+extern "C" int phast_ctx_create(phast_ctx** out, int32_t n_systems, const phast_system* sys, const phast_ff* ff,
+                                const phast_muca_params* mp, const int32_t* walkers, const uint64_t* seeds,
+                                const double* xyz0, void* stream) {
+    if (!out) return phast_set_error(PHAST_EINVAL, "phast_ctx_create: NULL out");
+    *out = nullptr;
+    if (n_systems < 1 || n_systems > PHAST_MAX_SYSTEMS)
+        return phast_set_error(PHAST_EINVAL, "phast_ctx_create: n_systems %d outside [1, %d]", n_systems, PHAST_MAX_SYSTEMS);
+    if (!sys || !ff || !mp || !walkers || !seeds || !xyz0)
+        return phast_set_error(PHAST_EINVAL, "phast_ctx_create: NULL argument");
+    phast_ctx* c = (phast_ctx*)calloc(1, sizeof(phast_ctx));
+    if (!c) return phast_set_error(PHAST_ENOMEM, "phast_ctx_create: host allocation");
+    c->n_sys = n_systems;
+    int64_t xyz_total = 0, lnw_total = 0, hw_total = 0;
+    int W = 0;
+    for (int s = 0; s < n_systems; ++s) {
+        char what[64];
+        snprintf(what, sizeof(what), "phast_ctx_create (system %d)", s);
+        int rc = phast_build_desc(&sys[s], &ff[s], &mp[s], &c->desc[s], what);
+        if (rc) { free(c); return rc; }
+        if (walkers[s] < 1) { free(c); return phast_set_error(PHAST_EINVAL, "%s: walkers < 1", what); }
+        SysDesc& d = c->desc[s];
+        d.walker_off = W;
+        d.n_walkers = walkers[s];
+        d.xyz_off = xyz_total;
+        d.lnw_off = (int32_t)lnw_total;
+        d.hw_off = hw_total;
+        W += walkers[s];
+        xyz_total += (int64_t)walkers[s] * d.N * 3;
+        lnw_total += d.n_bins;
+        hw_total += (int64_t)walkers[s] * d.n_bins;
+        c->max_N = std::max(c->max_N, d.N);
+        c->max_nc = std::max(c->max_nc, d.n_chains);
+        c->max_chain = std::max(c->max_chain, d.max_chain);
+        c->max_bins = std::max(c->max_bins, d.n_bins);
+    }
+    for (int64_t i = 0; i < xyz_total; ++i)
+        if (!isfinite(xyz0[i])) { free(c); return phast_set_error(PHAST_ENONFINITE, "phast_ctx_create: non-finite xyz0[%lld]", (long long)i); }
+    c->W = W;
+    c->xyz_total = xyz_total;
+    c->lnw_total = lnw_total;
+    c->hw_total = hw_total;
+    // tile order: most expensive system types first
+    std::vector<std::pair<double, int>> cost;
+    for (int s = 0; s < n_systems; ++s) cost.push_back({-system_cost(c->desc[s]), s});
+    std::sort(cost.begin(), cost.end());
+    for (int p = 0; p < n_systems; ++p) c->order[p] = cost[p].second;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaGetDevice(&c->device);
+    size_t bytes_stats = sizeof(phast_walker_stats) * (size_t)W;
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_desc, sizeof(SysDesc) * n_systems);
+    if (e == cudaSuccess) e = cudaMalloc(&c->xyz, sizeof(double) * xyz_total);
+    if (e == cudaSuccess) e = cudaMalloc(&c->E, sizeof(double) * W);
+    if (e == cudaSuccess) e = cudaMalloc(&c->bin, sizeof(int32_t) * W);
+    if (e == cudaSuccess) e = cudaMalloc(&c->t, sizeof(uint64_t) * W);
+    if (e == cudaSuccess) e = cudaMalloc(&c->seed, sizeof(uint64_t) * W);
+    if (e == cudaSuccess) e = cudaMalloc(&c->stats, bytes_stats);
+    if (e == cudaSuccess) e = cudaMalloc(&c->tile_counter, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&c->plain_scratch, sizeof(double) * 3 * (size_t)c->max_chain * W);
+    if (e != cudaSuccess) {
+        phast_ctx_destroy(c);
+        return phast_set_error(e == cudaErrorMemoryAllocation ? PHAST_ENOMEM : PHAST_ECUDA,
+                               "phast_ctx_create: %s", cudaGetErrorString(e));
+    }
+    e = cudaMemcpyAsync(c->d_desc, c->desc, sizeof(SysDesc) * n_systems, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->xyz, xyz0, sizeof(double) * xyz_total, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->seed, seeds, sizeof(uint64_t) * W, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->t, 0, sizeof(uint64_t) * W, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->stats, 0, bytes_stats, st);
+    if (e == cudaSuccess) {
+        init_energy_kernel<<<(W + 3) / 4, 128, 0, st>>>(c->d_desc, n_systems, W, c->xyz, c->E, c->bin);
+        e = cudaGetLastError();
+    }
+    std::vector<int32_t> bins(W);
+    std::vector<double> Es(W);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bins.data(), c->bin, sizeof(int32_t) * W, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Es.data(), c->E, sizeof(double) * W, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        phast_ctx_destroy(c);
+        return phast_set_error(PHAST_ECUDA, "phast_ctx_create: %s", cudaGetErrorString(e));
+    }
+    for (int w = 0; w < W; ++w)
+        if (bins[w] < 0) {
+            phast_ctx_destroy(c);
+            return phast_set_error(PHAST_ERANGE, "phast_ctx_create: walker %d starts at E = %.17g outside its bins", w, Es[w]);
+        }
+    default_tile(c, &c->tpw, &c->wpc);
+    *out = c;
+    return PHAST_OK;
+}
+
+extern "C" void phast_ctx_destroy(phast_ctx* c) {
+    if (!c) return;
+    cudaFree(c->d_desc);
+    cudaFree(c->xyz);
+    cudaFree(c->E);
+    cudaFree(c->bin);
+    cudaFree(c->t);
+    cudaFree(c->seed);
+    cudaFree(c->stats);
+    cudaFree(c->tile_counter);
+    cudaFree(c->plain_scratch);
+    free(c);
+}
+
+extern "C" int phast_ctx_info(const phast_ctx* c, int32_t s, int64_t* info8) {
+    if (!c || !info8) return phast_set_error(PHAST_EINVAL, "phast_ctx_info: NULL argument");
+    if (s < 0 || s >= c->n_sys) return phast_set_error(PHAST_EINVAL, "phast_ctx_info: system %d of %d", s, c->n_sys);
+    const SysDesc& d = c->desc[s];
+    info8[0] = c->W;
+    info8[1] = d.N;
+    info8[2] = d.n_bins;
+    info8[3] = d.walker_off;
+    info8[4] = d.xyz_off;
+    info8[5] = d.lnw_off;
+    info8[6] = c->n_sys;
+    info8[7] = d.n_walkers;
+    return PHAST_OK;
+}
+
+extern "C" int phast_ctx_get_state(const phast_ctx* c, double* xyz, double* E, int32_t* bin, uint64_t* t,
+                                   phast_walker_stats* stats, void* stream) {
+    if (!c) return phast_set_error(PHAST_EINVAL, "phast_ctx_get_state: NULL context");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (xyz) PHAST_CUDA_TRY(cudaMemcpyAsync(xyz, c->xyz, sizeof(double) * c->xyz_total, cudaMemcpyDefault, st));
+    if (E) PHAST_CUDA_TRY(cudaMemcpyAsync(E, c->E, sizeof(double) * c->W, cudaMemcpyDefault, st));
+    if (bin) PHAST_CUDA_TRY(cudaMemcpyAsync(bin, c->bin, sizeof(int32_t) * c->W, cudaMemcpyDefault, st));
+    if (t) PHAST_CUDA_TRY(cudaMemcpyAsync(t, c->t, sizeof(uint64_t) * c->W, cudaMemcpyDefault, st));
+    if (stats) PHAST_CUDA_TRY(cudaMemcpyAsync(stats, c->stats, sizeof(phast_walker_stats) * c->W, cudaMemcpyDefault, st));
+    return PHAST_OK;
+}
+
+extern "C" int phast_ctx_set_state(phast_ctx* c, const double* xyz, const double* E, const int32_t* bin,
+                                   const uint64_t* t, const phast_walker_stats* stats, void* stream) {
+    if (!c) return phast_set_error(PHAST_EINVAL, "phast_ctx_set_state: NULL context");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (xyz) PHAST_CUDA_TRY(cudaMemcpyAsync(c->xyz, xyz, sizeof(double) * c->xyz_total, cudaMemcpyDefault, st));
+    if (E) PHAST_CUDA_TRY(cudaMemcpyAsync(c->E, E, sizeof(double) * c->W, cudaMemcpyDefault, st));
+    if (bin) PHAST_CUDA_TRY(cudaMemcpyAsync(c->bin, bin, sizeof(int32_t) * c->W, cudaMemcpyDefault, st));
+    if (t) PHAST_CUDA_TRY(cudaMemcpyAsync(c->t, t, sizeof(uint64_t) * c->W, cudaMemcpyDefault, st));
+    if (stats) PHAST_CUDA_TRY(cudaMemcpyAsync(c->stats, stats, sizeof(phast_walker_stats) * c->W, cudaMemcpyDefault, st));
+    return PHAST_OK;
+}
+
+extern "C" int phast_ctx_set_tile(phast_ctx* c, int32_t tpw, int32_t wpc) {
+    if (!c) return phast_set_error(PHAST_EINVAL, "phast_ctx_set_tile: NULL context");
+    int dt, dw;
+    default_tile(c, &dt, &dw);
+    if (tpw == 0) tpw = dt;
+    if (wpc == 0) wpc = dw;
+    if (tpw != 4 && tpw != 8 && tpw != 16 && tpw != 32)
+        return phast_set_error(PHAST_EINVAL, "phast_ctx_set_tile: threads per walker %d not in {4, 8, 16, 32}", tpw);
+    if (wpc < 1 || tpw * wpc > kMaxTileThreads || (tpw * wpc) % 32)
+        return phast_set_error(PHAST_EINVAL, "phast_ctx_set_tile: %d walkers of %d threads is not a whole number of warps <= %d",
+                               wpc, tpw, kMaxTileThreads);
+    c->tpw = tpw;
+    c->wpc = wpc;
+    return PHAST_OK;
+}
+
+extern "C" int phast_ctx_get_tile(const phast_ctx* c, int32_t* tpw, int32_t* wpc) {
+    if (!c || !tpw || !wpc) return phast_set_error(PHAST_EINVAL, "phast_ctx_get_tile: NULL argument");
+    *tpw = c->tpw;
+    *wpc = c->wpc;
+    return PHAST_OK;
+}
+
+extern "C" int phast_muca_sweep(phast_ctx* c, int64_t n_sweeps, const double* lnW, int32_t form, int32_t n_jk,
+                                uint64_t* hist_sum, uint32_t* hist_walker, phast_trace* trace,
+                                int32_t trace_walkers, void* stream) {
+    if (!c) return phast_set_error(PHAST_EINVAL, "phast_muca_sweep: NULL context");
+    if (n_sweeps < 0) return phast_set_error(PHAST_EINVAL, "phast_muca_sweep: n_sweeps < 0");
+    if (!lnW) return phast_set_error(PHAST_EINVAL, "phast_muca_sweep: NULL lnW");
+    if (form != PHAST_FORM_BATCHED && form != PHAST_FORM_PLAIN)
+        return phast_set_error(PHAST_EINVAL, "phast_muca_sweep: unknown form %d", form);
+    if (!hist_sum) n_jk = 1;
+    if (n_jk < 1) return phast_set_error(PHAST_EINVAL, "phast_muca_sweep: n_jk < 1");
+    for (int s = 0; s < c->n_sys; ++s)
+        if (n_jk > c->desc[s].n_walkers)
+            return phast_set_error(PHAST_EINVAL, "phast_muca_sweep: n_jk %d > walkers of system %d", n_jk, s);
+    if (trace && (trace_walkers < 0 || trace_walkers > c->desc[0].n_walkers))
+        return phast_set_error(PHAST_EINVAL, "phast_muca_sweep: trace_walkers outside [0, walkers of system 0]");
+    if (n_sweeps == 0) return PHAST_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    SweepArgs a;
+    if (form == PHAST_FORM_PLAIN) {
+        fill_args(c, n_sweeps, lnW, n_jk, hist_sum, hist_walker, trace, trace_walkers, 1, &a);
+        sweep_plain_kernel<<<c->W, kPlainThreads, 0, st>>>(a, c->W);
+        PHAST_CUDA_TRY(cudaGetLastError());
+        return PHAST_OK;
+    }
+    bool fp32 = c->desc[0].pair_precision == 32;
+    for (int s = 1; s < c->n_sys; ++s)
+        if ((c->desc[s].pair_precision == 32) != fp32)
+            return phast_set_error(PHAST_EINVAL, "phast_muca_sweep: system types mix pair precisions");
+    fill_args(c, n_sweeps, lnW, n_jk, hist_sum, hist_walker, trace, trace_walkers, c->wpc, &a);
+    return launch_batched(c, a, c->tpw, c->wpc, fp32, st);
+}
+
+extern "C" int phast_ctx_autotune(phast_ctx* c, const double* lnW, int32_t sweeps, void* stream) {
+    if (!c || !lnW) return phast_set_error(PHAST_EINVAL, "phast_ctx_autotune: NULL argument");
+    if (sweeps < 1) sweeps = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool fp32 = c->desc[0].pair_precision == 32;
+    // run the candidates on a scratch copy so the walkers' trajectories are untouched
+    phast_ctx tmp = *c;
+    cudaError_t e = cudaMalloc(&tmp.xyz, sizeof(double) * c->xyz_total);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp.E, sizeof(double) * c->W);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp.bin, sizeof(int32_t) * c->W);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp.t, sizeof(uint64_t) * c->W);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp.stats, sizeof(phast_walker_stats) * c->W);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    int best_t = c->tpw, best_w = c->wpc;
+    float best = 1e30f;
+    const int cands[][2] = {{32, 4}, {32, 8}, {32, 16}, {16, 4}, {16, 8}, {16, 16}, {16, 32}, {8, 8}, {8, 16},
+                            {8, 32}, {8, 64}, {4, 16}, {4, 32}, {4, 64}, {4, 128}};
+    for (const auto& cd : cands) {
+        if (e != cudaSuccess) break;
+        SlotLayout L;
+        if (batched_smem(c, fp32, cd[1], &L) > 220 * 1024) continue;
+        e = cudaMemcpyAsync(tmp.xyz, c->xyz, sizeof(double) * c->xyz_total, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp.E, c->E, sizeof(double) * c->W, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp.bin, c->bin, sizeof(int32_t) * c->W, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(tmp.t, c->t, sizeof(uint64_t) * c->W, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) break;
+        SweepArgs a;
+        fill_args(&tmp, sweeps, lnW, 1, nullptr, nullptr, nullptr, 0, cd[1], &a);
+        cudaEventRecord(e0, st);
+        if (launch_batched(&tmp, a, cd[0], cd[1], fp32, st) != PHAST_OK) continue;
+        cudaEventRecord(e1, st);
+        e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) { best = ms; best_t = cd[0]; best_w = cd[1]; }
+    }
+    cudaFree(tmp.xyz);
+    cudaFree(tmp.E);
+    cudaFree(tmp.bin);
+    cudaFree(tmp.t);
+    cudaFree(tmp.stats);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (e != cudaSuccess) return phast_set_error(PHAST_ECUDA, "phast_ctx_autotune: %s", cudaGetErrorString(e));
+    c->tpw = best_t;
+    c->wpc = best_w;
+    return PHAST_OK;
+}
+
+extern "C" int phast_ctx_checkpoint(phast_ctx* c, void* buf, size_t* len, void* stream) {
+    if (!c || !len) return phast_set_error(PHAST_EINVAL, "phast_ctx_checkpoint: NULL argument");
+    const size_t W = c->W;
+    const size_t need = sizeof(CkptHeader) + sizeof(double) * c->xyz_total + W * (sizeof(double) + sizeof(int32_t) +
+                        sizeof(uint64_t) + sizeof(phast_walker_stats)) + sizeof(uint32_t);
+    if (!buf) { *len = need; return PHAST_OK; }
+    if (*len < need) return phast_set_error(PHAST_EINVAL, "phast_ctx_checkpoint: buffer of %zu < %zu bytes", *len, need);
+    unsigned char* p = (unsigned char*)buf;
+    CkptHeader h;
+    memset(&h, 0, sizeof(h));
+    h.magic = 0x4B434850u;   // "PHCK"
+    h.version = PHAST_VERSION;
+    h.n_sys = c->n_sys;
+    h.W = c->W;
+    h.xyz_total = c->xyz_total;
+    for (int s = 0; s < c->n_sys; ++s) { h.N[s] = c->desc[s].N; h.walkers[s] = c->desc[s].n_walkers; }
+    memcpy(p, &h, sizeof(h));
+    unsigned char* q = p + sizeof(h);
+    cudaStream_t st = (cudaStream_t)stream;
+    double* xyz = (double*)q;                   q += sizeof(double) * c->xyz_total;
+    double* E = (double*)q;                     q += sizeof(double) * W;
+    int32_t* bin = (int32_t*)q;                 q += sizeof(int32_t) * W;
+    uint64_t* t = (uint64_t*)q;                 q += sizeof(uint64_t) * W;
+    phast_walker_stats* stt = (phast_walker_stats*)q; q += sizeof(phast_walker_stats) * W;
+    int rc = phast_ctx_get_state(c, xyz, E, bin, t, stt, stream);
+    if (rc) return rc;
+    PHAST_CUDA_TRY(cudaStreamSynchronize(st));
+    uint32_t crc = crc32(p, (size_t)(q - p), 0);
+    memcpy(q, &crc, sizeof(crc));
+    *len = need;
+    return PHAST_OK;
+}
+
+extern "C" int phast_ctx_restore(phast_ctx* c, const void* buf, size_t len, void* stream) {
+    if (!c || !buf) return phast_set_error(PHAST_EINVAL, "phast_ctx_restore: NULL argument");
+    size_t need = 0;
+    phast_ctx_checkpoint(c, nullptr, &need, stream);
+    if (len != need) return phast_set_error(PHAST_EINVAL, "phast_ctx_restore: %zu bytes, expected %zu", len, need);
+    const unsigned char* p = (const unsigned char*)buf;
+    CkptHeader h;
+    memcpy(&h, p, sizeof(h));
+    if (h.magic != 0x4B434850u || h.n_sys != c->n_sys || h.W != c->W || h.xyz_total != c->xyz_total)
+        return phast_set_error(PHAST_EINVAL, "phast_ctx_restore: checkpoint of a different context");
+    for (int s = 0; s < c->n_sys; ++s)
+        if (h.N[s] != c->desc[s].N || h.walkers[s] != c->desc[s].n_walkers)
+            return phast_set_error(PHAST_EINVAL, "phast_ctx_restore: system %d differs", s);
+    uint32_t crc;
+    memcpy(&crc, p + need - sizeof(uint32_t), sizeof(crc));
+    if (crc != crc32(p, need - sizeof(uint32_t), 0))
+        return phast_set_error(PHAST_EINVAL, "phast_ctx_restore: CRC mismatch (corrupt checkpoint)");
+    const size_t W = c->W;
+    const unsigned char* q = p + sizeof(h);
+    const double* xyz = (const double*)q;       q += sizeof(double) * c->xyz_total;
+    const double* E = (const double*)q;         q += sizeof(double) * W;
+    const int32_t* bin = (const int32_t*)q;     q += sizeof(int32_t) * W;
+    const uint64_t* t = (const uint64_t*)q;     q += sizeof(uint64_t) * W;
+    const phast_walker_stats* stt = (const phast_walker_stats*)q;
+    int rc = phast_ctx_set_state(c, xyz, E, bin, t, stt, stream);
+    if (rc) return rc;
+    PHAST_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return PHAST_OK;
+}

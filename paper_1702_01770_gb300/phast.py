@@ -1,0 +1,363 @@
+"""Python binding of libphast.so (include/phast.h), argument marshalling only.
+
+Every computation happens in the CUDA library; torch tensors provide device
+memory and the stream.  The functions keep the C names.  The library must be
+built (``__graft_entry__.build()``); there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libphast.so")
+
+PIVOT, TRANS, ROT, CRANK = 0, 1, 2, 3
+FORM_BATCHED, FORM_PLAIN = 0, 1
+MAX_SYSTEMS, MAX_CHAINS, MAX_MONOMERS, MAX_BINS = 8, 16, 512, 16384
+ERRORS = {0: "PHAST_OK", -1: "PHAST_EINVAL", -2: "PHAST_ERANGE", -3: "PHAST_ENOMEM", -4: "PHAST_ECUDA",
+          -5: "PHAST_ETIMEOUT", -6: "PHAST_EDEVICE", -7: "PHAST_ENONFINITE"}
+SYMBOLS = ["phast_energy", "phast_delta_energy", "phast_ctx_create", "phast_ctx_destroy", "phast_ctx_info",
+           "phast_ctx_get_state", "phast_ctx_set_state", "phast_ctx_set_tile", "phast_ctx_get_tile",
+           "phast_ctx_autotune", "phast_muca_sweep", "phast_weight_update", "phast_micro_workspace_size",
+           "phast_micro_analysis", "phast_ctx_checkpoint", "phast_ctx_restore", "phast_last_error",
+           "phast_version"]
+
+
+class PhastError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _System(C.Structure):
+    _fields_ = [("n_chains", C.c_int32), ("chain_len", C.POINTER(C.c_int32)),
+                ("seq", C.POINTER(C.c_uint8)), ("box_L", C.c_double)]
+
+
+class _FF(C.Structure):
+    _fields_ = [("k_bend", C.c_double), ("k_tors", C.c_double), ("k_lj_intra", C.c_double),
+                ("k_lj_inter", C.c_double), ("C", C.c_double * 4)]
+
+
+class _Muca(C.Structure):
+    _fields_ = [("e_min", C.c_double), ("bin_width", C.c_double), ("n_bins", C.c_int32),
+                ("recompute_every", C.c_int32), ("p", C.c_double * 4), ("amax", C.c_double * 4),
+                ("pair_precision", C.c_int32), ("pad", C.c_int32)]
+
+
+class _MicroOut(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("S", "beta", "CV", "E_T", "cV_T", "peak", "S_err", "beta_err",
+                                            "CV_err", "E_T_err", "cV_T_err", "peak_err")]
+
+
+MOVE_DTYPE = np.dtype([("type", "<i4"), ("chain", "<i4"), ("index", "<i4"), ("pad", "<i4"),
+                       ("axis", "<f8", 3), ("angle", "<f8"), ("disp", "<f8", 3)])
+STATS_DTYPE = np.dtype([("attempts", "<u8", 4), ("accepts", "<u8", 4), ("pair_evals", "<u8"),
+                        ("recomputes", "<u8"), ("drift_max", "<f8"), ("pad", "<f8")])
+TRACE_DTYPE = np.dtype([("dE", "<f8"), ("bin_after", "<i4"), ("accepted", "<i4")])
+
+_lib = None
+
+
+def lib():
+    """Load libphast.so (raises if it is not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, dbl, P = C.c_void_p, C.c_int32, C.c_int64, C.c_double, C.POINTER
+        L.phast_energy.argtypes = [P(_System), P(_FF), i32, vp, i32, vp, vp]
+        L.phast_delta_energy.argtypes = [P(_System), P(_FF), i32, vp, vp, i32, vp, vp, vp]
+        L.phast_ctx_create.argtypes = [P(vp), i32, P(_System), P(_FF), P(_Muca), vp, vp, vp, vp]
+        L.phast_ctx_destroy.argtypes = [vp]
+        L.phast_ctx_destroy.restype = None
+        L.phast_ctx_info.argtypes = [vp, i32, vp]
+        L.phast_ctx_get_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.phast_ctx_set_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.phast_ctx_set_tile.argtypes = [vp, i32, i32]
+        L.phast_ctx_get_tile.argtypes = [vp, P(i32), P(i32)]
+        L.phast_ctx_autotune.argtypes = [vp, vp, i32, vp]
+        L.phast_muca_sweep.argtypes = [vp, i64, vp, i32, i32, vp, vp, vp, i32, vp]
+        L.phast_weight_update.argtypes = [i32, dbl, vp, i32, vp, vp, vp, vp, vp]
+        L.phast_micro_workspace_size.argtypes = [i32, i32, i32]
+        L.phast_micro_workspace_size.restype = C.c_size_t
+        L.phast_micro_analysis.argtypes = [i32, dbl, dbl, vp, vp, i32, i32, i32, i32, vp, P(_MicroOut), vp,
+                                           C.c_size_t, vp]
+        L.phast_ctx_checkpoint.argtypes = [vp, vp, P(C.c_size_t), vp]
+        L.phast_ctx_restore.argtypes = [vp, vp, C.c_size_t, vp]
+        L.phast_last_error.restype = C.c_char_p
+        L.phast_last_error.argtypes = []
+        L.phast_version.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise PhastError(rc, lib().phast_last_error().decode())
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        assert t.is_contiguous(), "tensors crossing the C ABI must be contiguous"
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    raise TypeError(type(t))
+
+
+class _Structs:
+    """ABI structs of a list of systems, with the host arrays they point to kept alive."""
+
+    def __init__(self, systems, pair_precision: int | None = None):
+        n = len(systems)
+        self.keep = []
+        self.sys = (_System * n)()
+        self.ff = (_FF * n)()
+        self.mp = (_Muca * n)()
+        for i, s in enumerate(systems):
+            cl = np.ascontiguousarray(s.chain_len, dtype=np.int32)
+            sq = np.ascontiguousarray(s.seq, dtype=np.uint8)
+            self.keep += [cl, sq]
+            self.sys[i].n_chains = cl.size
+            self.sys[i].chain_len = cl.ctypes.data_as(C.POINTER(C.c_int32))
+            self.sys[i].seq = sq.ctypes.data_as(C.POINTER(C.c_uint8))
+            self.sys[i].box_L = float(s.box_L)
+            self.ff[i].k_bend, self.ff[i].k_tors = float(s.k_bend), float(s.k_tors)
+            self.ff[i].k_lj_intra, self.ff[i].k_lj_inter = float(s.k_lj_intra), float(s.k_lj_inter)
+            self.ff[i].C = (C.c_double * 4)(*[float(c) for c in s.C])
+            self.mp[i].e_min, self.mp[i].bin_width = float(s.e_min), float(s.bin_width)
+            self.mp[i].n_bins, self.mp[i].recompute_every = int(s.n_bins), int(s.recompute_every)
+            self.mp[i].p = (C.c_double * 4)(*[float(x) for x in s.p])
+            self.mp[i].amax = (C.c_double * 4)(*[float(x) for x in s.amax])
+            self.mp[i].pair_precision = int(pair_precision or 64)
+
+
+def phast_energy(system, xyz: torch.Tensor, pair_precision: int = 64, stream=None) -> torch.Tensor:
+    """Energies (FP64, device) of xyz [B, N, 3] FP64 on the device."""
+    st = _Structs([system])
+    xyz = xyz.contiguous()
+    B = xyz.shape[0] if xyz.numel() else 0
+    E = torch.empty(B, dtype=torch.float64, device=xyz.device)
+    _check(lib().phast_energy(st.sys, st.ff, B, _ptr(xyz), pair_precision, _ptr(E), _stream(stream)))
+    return E
+
+
+def moves_tensor(moves, device) -> torch.Tensor:
+    """Pack moves (a MOVE_DTYPE array or a list of dicts) into device bytes."""
+    if not isinstance(moves, np.ndarray):
+        arr = np.zeros(len(moves), MOVE_DTYPE)
+        for i, m in enumerate(moves):
+            for k, v in m.items():
+                arr[i][k] = v
+        moves = arr
+    raw = np.ascontiguousarray(moves.astype(MOVE_DTYPE)).view(np.uint8)
+    return torch.from_numpy(raw.copy()).to(device)
+
+
+def phast_delta_energy(system, xyz: torch.Tensor, moves, pair_precision: int = 64, want_xyz: bool = False,
+                       stream=None):
+    st = _Structs([system])
+    xyz = xyz.contiguous()
+    B = xyz.shape[0]
+    mv = moves if isinstance(moves, torch.Tensor) else moves_tensor(moves, xyz.device)
+    dE = torch.empty(B, dtype=torch.float64, device=xyz.device)
+    xn = torch.empty_like(xyz) if want_xyz else None
+    _check(lib().phast_delta_energy(st.sys, st.ff, B, _ptr(xyz), _ptr(mv), pair_precision, _ptr(dE), _ptr(xn),
+                                    _stream(stream)))
+    return (dE, xn) if want_xyz else dE
+
+
+class Context:
+    """Walker state of one or more system types on the current device (phast_ctx)."""
+
+    def __init__(self, systems, pair_precision: int = 32, xyz0=None, seeds=None, stream=None):
+        if isinstance(systems, inputs.System):
+            systems = [systems]
+        self.systems = list(systems)
+        self._st = _Structs(self.systems, pair_precision)
+        walkers = np.array([s.walkers for s in self.systems], dtype=np.int32)
+        if seeds is None:
+            seeds = np.concatenate([s.seeds() for s in self.systems]).astype(np.uint64)
+        if xyz0 is None:
+            xyz0 = np.concatenate([s.walker_xyz().reshape(-1) for s in self.systems])
+        seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+        xyz0 = np.ascontiguousarray(xyz0, dtype=np.float64).reshape(-1)
+        self._keep = [walkers, seeds, xyz0]
+        h = C.c_void_p()
+        _check(lib().phast_ctx_create(C.byref(h), len(self.systems), self._st.sys, self._st.ff, self._st.mp,
+                                      walkers.ctypes.data, seeds.ctypes.data, xyz0.ctypes.data, _stream(stream)))
+        self.h = h
+        self.W = int(walkers.sum())
+        self.pair_precision = pair_precision
+        info = [self.info(s) for s in range(len(self.systems))]
+        self.N = [i[1] for i in info]
+        self.n_bins = [i[2] for i in info]
+        self.walker_off = [i[3] for i in info]
+        self.xyz_off = [i[4] for i in info]
+        self.lnw_off = [i[5] for i in info]
+        self.xyz_total = sum(s.walkers * n * 3 for s, n in zip(self.systems, self.N))
+
+    def info(self, s: int):
+        out = np.zeros(8, np.int64)
+        _check(lib().phast_ctx_info(self.h, s, out.ctypes.data))
+        return [int(x) for x in out]
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().phast_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # state ------------------------------------------------------------------
+    def get_state(self, device="cuda", stream=None) -> dict:
+        dev = torch.device(device)
+        xyz = torch.empty(self.xyz_total, dtype=torch.float64, device=dev)
+        E = torch.empty(self.W, dtype=torch.float64, device=dev)
+        b = torch.empty(self.W, dtype=torch.int32, device=dev)
+        t = torch.empty(self.W, dtype=torch.int64, device=dev)
+        stats = torch.empty(self.W * STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+        _check(lib().phast_ctx_get_state(self.h, _ptr(xyz), _ptr(E), _ptr(b), _ptr(t), _ptr(stats),
+                                         _stream(stream)))
+        return dict(xyz=xyz, E=E, bin=b, t=t, stats=stats)
+
+    def set_state(self, xyz=None, E=None, bin=None, t=None, stats=None, stream=None):
+        _check(lib().phast_ctx_set_state(self.h, _ptr(xyz), _ptr(E), _ptr(bin), _ptr(t), _ptr(stats),
+                                         _stream(stream)))
+
+    def stats(self) -> np.ndarray:
+        st = self.get_state()
+        torch.cuda.synchronize()
+        return st["stats"].cpu().numpy().view(STATS_DTYPE)
+
+    def xyz_of(self, state: dict, s: int) -> torch.Tensor:
+        """Coordinates of system type s as [walkers, N, 3]."""
+        n = self.systems[s].walkers * self.N[s] * 3
+        return state["xyz"][self.xyz_off[s]: self.xyz_off[s] + n].view(self.systems[s].walkers, self.N[s], 3)
+
+    # tiles ------------------------------------------------------------------
+    def set_tile(self, threads_per_walker: int = 0, walkers_per_cta: int = 0):
+        _check(lib().phast_ctx_set_tile(self.h, threads_per_walker, walkers_per_cta))
+
+    def get_tile(self):
+        a, b = C.c_int32(), C.c_int32()
+        _check(lib().phast_ctx_get_tile(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def autotune(self, lnW: torch.Tensor, sweeps: int = 1, stream=None):
+        _check(lib().phast_ctx_autotune(self.h, _ptr(lnW), sweeps, _stream(stream)))
+        return self.get_tile()
+
+    # the sweep --------------------------------------------------------------
+    def lnW_zeros(self, device="cuda") -> torch.Tensor:
+        return torch.zeros(sum(self.n_bins), dtype=torch.float64, device=device)
+
+    def hist_sum_zeros(self, n_jk: int = 1, device="cuda") -> torch.Tensor:
+        return torch.zeros(n_jk * sum(self.n_bins), dtype=torch.int64, device=device)
+
+    def hist_walker_zeros(self, device="cuda") -> torch.Tensor:
+        return torch.zeros(sum(s.walkers * k for s, k in zip(self.systems, self.n_bins)), dtype=torch.int32,
+                           device=device)
+
+    def sweep(self, n_sweeps: int, lnW: torch.Tensor, form: int = FORM_BATCHED, n_jk: int = 1,
+              hist_sum: torch.Tensor | None = None, hist_walker: torch.Tensor | None = None,
+              trace: torch.Tensor | None = None, trace_walkers: int = 0, stream=None):
+        _check(lib().phast_muca_sweep(self.h, int(n_sweeps), _ptr(lnW), form, n_jk, _ptr(hist_sum),
+                                      _ptr(hist_walker), _ptr(trace), trace_walkers, _stream(stream)))
+
+    def trace_buffer(self, n_sweeps: int, walkers: int, device="cuda") -> torch.Tensor:
+        n = walkers * n_sweeps * self.N[0]
+        return torch.zeros(n * TRACE_DTYPE.itemsize, dtype=torch.uint8, device=device)
+
+    # checkpoint -------------------------------------------------------------
+    def checkpoint(self, stream=None) -> bytes:
+        n = C.c_size_t()
+        _check(lib().phast_ctx_checkpoint(self.h, None, C.byref(n), _stream(stream)))
+        buf = C.create_string_buffer(n.value)
+        _check(lib().phast_ctx_checkpoint(self.h, buf, C.byref(n), _stream(stream)))
+        return buf.raw
+
+    def restore(self, blob: bytes, stream=None):
+        buf = C.create_string_buffer(blob, len(blob))
+        _check(lib().phast_ctx_restore(self.h, buf, len(blob), _stream(stream)))
+
+
+def phast_weight_update(hist: torch.Tensor, lnW: torch.Tensor, g_acc: torch.Tensor, bin_width: float,
+                        beta_out: torch.Tensor | None = None, flat_out: torch.Tensor | None = None, stream=None):
+    """One Berg step in place on lnW [K] and g_acc [K-1]; hist int64 [n_blocks, K] (or [K])."""
+    K = lnW.numel()
+    n_blocks = hist.numel() // K
+    _check(lib().phast_weight_update(K, float(bin_width), _ptr(hist), n_blocks, _ptr(lnW), _ptr(g_acc),
+                                     _ptr(beta_out), _ptr(flat_out), _stream(stream)))
+
+
+@dataclass
+class MicroResult:
+    S: torch.Tensor
+    beta: torch.Tensor
+    CV: torch.Tensor
+    E_T: torch.Tensor
+    cV_T: torch.Tensor
+    peak: torch.Tensor
+    S_err: torch.Tensor | None = None
+    beta_err: torch.Tensor | None = None
+    CV_err: torch.Tensor | None = None
+    E_T_err: torch.Tensor | None = None
+    cV_T_err: torch.Tensor | None = None
+    peak_err: torch.Tensor | None = None
+
+
+def phast_micro_analysis(lnW: torch.Tensor, e_min: float, bin_width: float, hist: torch.Tensor | None = None,
+                         fd_half_width: int = 1, n_monomers: int = 1, T: torch.Tensor | None = None,
+                         workspace: torch.Tensor | None = None, stream=None) -> MicroResult:
+    """Eq. 4-6 plus canonical reweighting; hist int64 [n_blocks, K]; errors when n_blocks >= 2."""
+    dev = lnW.device
+    K = lnW.numel()
+    n_blocks = 0 if hist is None else hist.numel() // K
+    if T is None:
+        T = torch.empty(0, dtype=torch.float64, device=dev)
+    n_T = T.numel()
+    f = lambda n: torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    errs = n_blocks >= 2
+    r = MicroResult(f(K), f(K), f(K), f(n_T), f(n_T), f(2))
+    if errs:
+        r.S_err, r.beta_err, r.CV_err, r.E_T_err, r.cV_T_err, r.peak_err = f(K), f(K), f(K), f(n_T), f(n_T), f(2)
+    o = _MicroOut()
+    for name in _MicroOut._fields_:
+        v = getattr(r, name[0])
+        setattr(o, name[0], None if v is None else v.data_ptr())
+    need = lib().phast_micro_workspace_size(K, n_T, n_blocks)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    _check(lib().phast_micro_analysis(K, float(e_min), float(bin_width), _ptr(lnW), _ptr(hist), n_blocks,
+                                      fd_half_width, n_monomers, n_T, _ptr(T), C.byref(o), _ptr(workspace),
+                                      workspace.numel(), _stream(stream)))
+    return r
+
+
+def phast_version() -> int:
+    return lib().phast_version()
