@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Throughput of the multicanonical sweep on the eight-55-mer aggregation
+workload (8 chains x 55 monomers, periodic L = 40, 16384 walkers, 8000 bins of
+0.1 on [-400, 400), FP32 pairs with FP64 totals).
+
+One step = one pass of the whole hot path over the batch:
+  `sweeps_per_step` sweeps of every walker (batched sweep kernel; proposals,
+  dE, acceptance, histogram, and the FP64 drift recompute every 100 sweeps by
+  each walker's own move count) -> microcanonical analysis with jackknife
+  errors over 16 walker blocks -> one Berg weight update.
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MUCA walker-moves/s and pair-evals/s (% FP32 peak), batched vs plain at ≤1e-4 rel ΔE"
+WORKLOAD = "8x55-mer aggregation: 8 chains x 55 monomers, periodic L=40, 16384 walkers, 8000 bins of 0.1 on [-400,400)"
+N_JK = 16
+N_T = 64
+FLOPS_OPEN, FLOPS_PBC = 14, 23          # algorithmic flops of one pair evaluation (open / minimum image)
+LAUNCHES_PER_STEP = 5                   # sweep, 3 analysis kernels, Berg update
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sweeps-per-step", type=int, default=10)
+    ap.add_argument("--walkers", type=int, default=16384)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle legs (the oracle is the reference arm and the CPU baseline)
+# ----------------------------------------------------------------------------
+def oracle_walker_moves_per_s(s, seconds: float, threads: int):
+    """Time the FP64 oracle on a bounded sample: `threads` threads, each walker one sweep."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import numpy as np
+
+    import oracle
+    m = oracle.Model(s.chain_len, s.seq, box_L=s.box_L, k_bend=s.k_bend, k_tors=s.k_tors,
+                     k_lj_intra=s.k_lj_intra, k_lj_inter=s.k_lj_inter, C=s.C)
+    mu = oracle.Muca(s.e_min, s.bin_width, s.n_bins, p=s.p, amax=s.amax, recompute_every=s.recompute_every)
+    lnW = np.zeros(s.n_bins)
+    N = s.n_total
+
+    def one(w):
+        wk = oracle.new_walker(m, mu, s.xyz0, int(w))
+        _, st, _ = oracle.sweep_walker(m, mu, lnW, wk, N)
+        return st[8]
+
+    t0 = time.perf_counter()
+    one(0)
+    per = time.perf_counter() - t0                    # one walker-sweep on one core
+    n = max(1, int(seconds / per)) * threads          # about `seconds` of wall time on `threads` cores
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        pev = sum(ex.map(one, range(1, n + 1)))
+    dt = time.perf_counter() - t0
+    return n * N / dt, pev / dt, n, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", 0))
+    if rank != 0:
+        return
+    from paper_1702_01770_gb300 import inputs
+    s = inputs.config4(walkers=1)
+    threads = os.cpu_count() or 1
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_walker_moves_per_s(s, per_step, threads)
+    vals, pes, tot = [], [], 0.0
+    for _ in range(args.steps):
+        v, pe, n, dt = oracle_walker_moves_per_s(s, per_step, threads)
+        vals.append(v)
+        pes.append(pe)
+        tot += dt
+    v = statistics.mean(vals)
+    sample = f"{threads} threads, one sweep (440 moves) per walker, lnW = 0, {args.steps} steps of ~{per_step:.1f} s"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "walker-moves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "walkers": "bounded sample", "impl": "FP64 CPU oracle"},
+        "pair_evals_per_s": statistics.mean(pes),
+        "cpu_baseline": {"value": v, "unit": "walker-moves/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "walker-moves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+def csrc_digest() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1702_01770_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        h.update(fn.encode())
+        h.update(open(os.path.join(d, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(walkers: int):
+    """DRAM bytes of one sweep launch, from the committed ncu summary (null if the kernel changed since)."""
+    p = os.path.join(ROOT, "profiles", "sweep_batched_8x55_traffic.json")
+    try:
+        j = json.load(open(p))
+    except Exception:
+        return None
+    if j.get("csrc_sha") != csrc_digest():
+        return None
+    return j["dram_bytes_per_walker"] * walkers
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1702_01770_gb300 import inputs, parallel, phast
+
+    rank, world, local = parallel.world()
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+
+    s = inputs.config4(walkers=args.walkers)
+    s.seed_base = parallel.walker_seed_base(rank, args.walkers)
+    K, N, S = s.n_bins, s.n_total, args.sweeps_per_step
+    ctx = phast.Context(s, pair_precision=32)
+    lnW = torch.zeros(K, dtype=torch.float64, device=dev)
+    g = torch.zeros(K - 1, dtype=torch.float64, device=dev)
+    flat = torch.zeros(4, dtype=torch.float64, device=dev)
+    hs = torch.zeros(N_JK * K, dtype=torch.int64, device=dev)
+    T = torch.linspace(0.3, 3.0, N_T, dtype=torch.float64, device=dev)
+    ws = torch.empty(phast.lib().phast_micro_workspace_size(K, N_T, N_JK), dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+
+    def step(i=None):
+        hs.zero_()
+        if i is not None:
+            ev[i][0].record()
+        ctx.sweep(S, lnW, n_jk=N_JK, hist_sum=hs)
+        if i is not None:
+            ev[i][1].record()
+        parallel.combine_histograms(hs)
+        res = phast.phast_micro_analysis(lnW, s.e_min, s.bin_width, hist=hs.view(N_JK, K), fd_half_width=5,
+                                         n_monomers=N, T=T, workspace=ws)
+        phast.phast_weight_update(hs.view(N_JK, K), lnW, g, s.bin_width, flat_out=flat)
+        return res
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    st0 = ctx.stats()
+    sampler = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for i in range(args.steps):
+        res = step(i)
+    t1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms_local = t0.elapsed_time(t1)
+    ms = parallel.max_over_ranks(ms_local, dev)
+    st1 = ctx.stats()
+    moves = int(st1["attempts"].sum() - st0["attempts"].sum())
+    pe = int(st1["pair_evals"].sum() - st0["pair_evals"].sum())
+    pex = int(st1["pair_evals_inter"].sum() - st0["pair_evals_inter"].sum())
+    assert moves == args.walkers * N * S * args.steps
+    sweep_ms = [a.elapsed_time(b) for a, b in ev]
+    flops = (pe - pex) * FLOPS_OPEN + pex * FLOPS_PBC
+    total_moves = moves * world
+    value = total_moves / (ms / 1e3)
+
+    # roofline of the sweep kernel: algorithmic FP32 flops / its event-timed duration
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    max_mhz = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+    peak_tf = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12
+    achieved_tf = flops / (sum(sweep_ms) / 1e3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                "frac": achieved_tf / peak_tf, "traffic": traffic_per_launch(args.walkers),
+                "peak_basis": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz (max SM clock)",
+                "kernel": "sweep_batched_kernel<32,float>",
+                "frac_at_median_clock": (achieved_tf / (n_sm * 256 * clocks["sm_mhz"] * 1e6 / 1e12))
+                if clocks.get("sm_mhz") else None}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "walker-moves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "walkers_per_gpu": args.walkers, "sweeps_per_step": S,
+                   "step": "sweeps + analysis (16 jackknife blocks, 64 T) + Berg update",
+                   "precision": "FP32 pair and local terms, FP64 geometry/totals/weights/histogram sums",
+                   "l2": "inputs larger than L2 (walker state %.0f MB)" % (args.walkers * N * 24 / 1e6),
+                   "tile": list(ctx.get_tile())},
+        "pair_evals_per_s": pe * world / (ms / 1e3),
+        "sweep_kernel_ms_per_step": sum(sweep_ms) / args.steps,
+        "roofline": roofline,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
+        "clocks": clocks,
+        "drift_max": float(st1["drift_max"].max()),
+        "flatness_cvar": float(flat[2].item()),
+    }
+
+    # plain one-walker-per-CTA FP64 form, same GPU, a subset of the walkers
+    if not args.no_plain and rank == 0:
+        ps = inputs.config4(walkers=2432)
+        pctx = phast.Context(ps, pair_precision=64)
+        plnW = torch.zeros(K, dtype=torch.float64, device=dev)
+        pctx.sweep(1, plnW, form=phast.FORM_PLAIN)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0 = pctx.stats()
+        a.record()
+        pctx.sweep(1, plnW, form=phast.FORM_PLAIN)
+        b.record()
+        torch.cuda.synchronize()
+        p1 = pctx.stats()
+        pms = a.elapsed_time(b)
+        out["plain"] = {"walker_moves_per_s": float((p1["attempts"].sum() - p0["attempts"].sum()) / (pms / 1e3)),
+                        "pair_evals_per_s": float((p1["pair_evals"].sum() - p0["pair_evals"].sum()) / (pms / 1e3)),
+                        "walkers": 2432, "sweeps": 1, "dtype": "f64"}
+        out["batched_over_plain"] = out["pair_evals_per_s"] / world / out["plain"]["pair_evals_per_s"]
+        pctx.close()
+
+    # end to end through the C ABI with host buffers: state in from pinned host memory, results out
+    if not args.no_e2e:
+        st = ctx.get_state("cpu")
+        torch.cuda.synchronize()
+        host = {k: v.pin_memory() for k, v in st.items() if k in ("xyz", "E", "bin", "t")}
+        out_host = {k: torch.empty_like(v).pin_memory() for k, v in host.items()}
+        S_host = torch.empty(K, dtype=torch.float64).pin_memory()
+        lnW_host = torch.empty(K, dtype=torch.float64).pin_memory()
+        h2d = sum(v.numel() * v.element_size() for v in host.values())
+        d2h = h2d + 2 * K * 8
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        e0 = time.perf_counter()
+        for i in range(args.steps):
+            ctx.set_state(xyz=host["xyz"], E=host["E"], bin=host["bin"], t=host["t"])
+            res = step()
+            phast._check(phast.lib().phast_ctx_get_state(ctx.h, out_host["xyz"].data_ptr(), out_host["E"].data_ptr(),
+                                                         out_host["bin"].data_ptr(), out_host["t"].data_ptr(), None,
+                                                         phast._stream(None)))
+            S_host.copy_(res.S, non_blocking=True)
+            lnW_host.copy_(lnW, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            host, out_host = out_host, host
+        e_ms = (time.perf_counter() - e0) * 1e3
+        e_ms = parallel.max_over_ranks(e_ms, dev)
+        out["e2e"] = {"value": total_moves / (e_ms / 1e3), "unit": "walker-moves/s", "h2d_bytes_per_step": h2d,
+                      "d2h_bytes_per_step": d2h}
+
+    if rank == 0 and not args.no_cpu_baseline:
+        v, pev, n, dt = oracle_walker_moves_per_s(inputs.config4(walkers=1), args.cpu_seconds, os.cpu_count() or 1)
+        out["cpu_baseline"] = {"value": v, "unit": "walker-moves/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+                               "sample": f"{n} walkers x 1 sweep (440 moves) of the 8x55-mer workload, lnW = 0, "
+                                         f"FP64 oracle, {dt:.1f} s", "pair_evals_per_s": pev}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -106,9 +106,9 @@ typedef struct {
     uint64_t attempts[4];
     uint64_t accepts[4];
     uint64_t pair_evals;   /* 2 per (moved, unmoved) Lennard-Jones pair whose distance can change */
+    uint64_t pair_evals_inter;  /* the part of pair_evals between different chains */
     uint64_t recomputes;
     double drift_max;      /* largest |E_running - E_full| seen at a recompute */
-    double pad;
 } phast_walker_stats;
 
 /* One traced move (16 bytes). */
@@ -123,8 +123,9 @@ typedef struct phast_ctx phast_ctx;
 /* ---- energy (Sec. 2.1, Eq. 2 and Eq. 3) --------------------------------- */
 
 /* Total energy of B configurations of one system.  xyz: dev [B][N][3] FP64;
- * pair_precision 32 or 64 selects the Lennard-Jones pair arithmetic (local
- * terms and sums are FP64).  E_out: dev [B].  B = 0 is a no-op. */
+ * pair_precision 32 or 64 selects the arithmetic of the Lennard-Jones pairs and
+ * of the bending/torsion terms (FP32 positions are taken relative to their
+ * chain's FP64 centroid); sums are FP64.  E_out: dev [B].  B = 0 is a no-op. */
 int phast_energy(const phast_system* sys, const phast_ff* ff, int32_t B, const double* xyz,
                  int32_t pair_precision, double* E_out, void* stream);
 

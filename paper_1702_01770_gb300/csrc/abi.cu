@@ -92,6 +92,14 @@ int phast_build_desc(const phast_system* sys, const phast_ff* ff, const phast_mu
         d->n_bins = mp->n_bins;
         d->recompute_every = mp->recompute_every;
         for (int i = 0; i < 4; ++i) { d->p[i] = mp->p[i]; d->amax[i] = mp->amax[i]; }
+        // integer move-type thresholds: u < cum_i  <=>  2n + 1 < ceil(cum_i 2^53) for u = (n + 1/2) 2^-52
+        double cum = 0.0;
+        d->last_type = 0;
+        for (int i = 0; i < 4; ++i) {
+            cum = cum + mp->p[i];
+            d->thr[i] = (uint64_t)ceil(cum * 9007199254740992.0);
+            if (mp->p[i] > 0.0) d->last_type = i;
+        }
         d->pair_precision = mp->pair_precision;
     }
     return PHAST_OK;

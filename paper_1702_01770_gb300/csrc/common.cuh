@@ -39,6 +39,8 @@ struct SysDesc {
     double C[4];
     double e_min, bin_width;
     double p[4], amax[4];
+    uint64_t thr[4];      // move-type thresholds: type i if 2n+1 < thr[i] (n the 52-bit uniform), see propose_select
+    int32_t last_type, pad2[3];
     int32_t chain_off[PHAST_MAX_CHAINS + 1];
     int32_t pad1[3];
     uint8_t seq[PHAST_MAX_MONOMERS];
@@ -84,6 +86,16 @@ __device__ __forceinline__ uint4 stream_block(uint64_t seed, uint64_t t, uint32_
 __device__ __forceinline__ double u52(uint32_t a, uint32_t b) {
     double n = xadd(xmul((double)(a >> 6), 67108864.0), (double)(b >> 6));
     return xmul(xadd(n, 0.5), 2.220446049250313080847263336181640625e-16);
+}
+
+// 52-bit integer n of a uniform u = (n + 1/2) 2^-52 drawn from words a, b.
+__device__ __forceinline__ uint64_t u52_bits(uint32_t a, uint32_t b) {
+    return ((uint64_t)(a >> 6) << 26) | (uint64_t)(b >> 6);
+}
+// 2u - 1 = (2n + 1 - 2^52) 2^-52, exact.
+__device__ __forceinline__ double sym_unit(uint32_t a, uint32_t b) {
+    int64_t k = (int64_t)(2 * u52_bits(a, b) + 1) - (int64_t)(1ull << 52);
+    return xmul((double)k, 2.220446049250313080847263336181640625e-16);
 }
 
 // sin and cos of |a| <= 1 by their Taylor series, Horner in a^2 with separately
@@ -134,18 +146,24 @@ __device__ __forceinline__ double3 rotate_about(const Rot3& R, double3 p, double
     return make_double3(xadd(p.x, w0), xadd(p.y, w1), xadd(p.z, w2));
 }
 
-// One Marsaglia (1972) attempt from block (a, b, c, d): returns true and the
-// isotropic unit axis if (v1, v2) falls inside the unit disc.
+// One Marsaglia (1972) attempt from block r: (v1, v2) uniform in the square,
+// kept if inside the unit disc (0 < s < 1); the axis is then
+// (2 v1 sqrt(1-s), 2 v2 sqrt(1-s), 1 - 2 s), isotropic on the sphere.
+__device__ __forceinline__ bool marsaglia_in_disc(uint4 r, double* v1, double* v2, double* s) {
+    *v1 = sym_unit(r.x, r.y);
+    *v2 = sym_unit(r.z, r.w);
+    *s = xadd(xmul(*v1, *v1), xmul(*v2, *v2));
+    return *s < 1.0 && *s > 0.0;
+}
+__device__ __forceinline__ double3 marsaglia_axis(double v1, double v2, double s) {
+    double q = xsqrt(xsub(1.0, s));
+    return make_double3(xmul(xmul(2.0, v1), q), xmul(xmul(2.0, v2), q), xsub(1.0, xmul(2.0, s)));
+}
 __device__ __forceinline__ bool marsaglia_try(uint4 r, double3* axis) {
-    double v1 = xsub(xmul(2.0, u52(r.x, r.y)), 1.0);
-    double v2 = xsub(xmul(2.0, u52(r.z, r.w)), 1.0);
-    double s = xadd(xmul(v1, v1), xmul(v2, v2));
-    if (s < 1.0 && s > 0.0) {
-        double q = xsqrt(xsub(1.0, s));
-        *axis = make_double3(xmul(xmul(2.0, v1), q), xmul(xmul(2.0, v2), q), xsub(1.0, xmul(2.0, s)));
-        return true;
-    }
-    return false;
+    double v1, v2, s;
+    if (!marsaglia_in_disc(r, &v1, &v2, &s)) return false;
+    *axis = marsaglia_axis(v1, v2, s);
+    return true;
 }
 
 // A proposed move, drawn from the walker stream.
@@ -155,26 +173,20 @@ struct Proposal {
     double3 axis, disp;
 };
 
-// Selection part of move t (blocks 0-2): type by comparing a uniform with the
-// running sum of the type probabilities (the last type with p > 0 catches the
-// rounding remainder), uniform chain, interior monomer 1..n-2 for pivot and
-// crankshaft, amplitude uniform in [-amax, amax].  The axis is set separately.
+// Selection part of move t (blocks 0-2): the type is the first one with p > 0
+// whose running probability sum exceeds the uniform (the last type with p > 0
+// catches the rounding remainder) -- compared exactly in integers, since
+// u < cum  <=>  2n + 1 < cum 2^53  <=>  2n + 1 < ceil(cum 2^53) = thr;
+// uniform chain; interior monomer 1..n-2 for pivot and crankshaft; amplitude
+// uniform in [-amax, amax].  The axis is set separately.
 __device__ __forceinline__ void propose_select(const SysDesc& d, uint4 b0, uint4 b1, uint4 b2,
                                                Proposal* P) {
-    double u_type = u52(b0.x, b0.y);
-    double u_a = u52(b1.x, b1.y), u_b = u52(b1.z, b1.w), u_c = u52(b2.x, b2.y);
-    P->u_acc = u52(b2.z, b2.w);
-    int type = -1, last = 0;
-    double cum = 0.0;
+    const uint64_t v = 2 * u52_bits(b0.x, b0.y) + 1;
+    int type = d.last_type;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        cum = xadd(cum, d.p[i]);
-        if (d.p[i] > 0.0) {
-            last = i;
-            if (type < 0 && u_type < cum) type = i;
-        }
-    }
-    if (type < 0) type = last;
+    for (int i = 3; i >= 0; --i)
+        if (d.p[i] > 0.0 && v < d.thr[i]) type = i;
+    P->u_acc = u52(b2.z, b2.w);
     P->type = type;
     P->chain = (int)(((uint64_t)b0.z * (uint64_t)d.n_chains) >> 32);
     int n = d.chain_off[P->chain + 1] - d.chain_off[P->chain];
@@ -185,10 +197,10 @@ __device__ __forceinline__ void propose_select(const SysDesc& d, uint4 b0, uint4
     P->axis = make_double3(0.0, 0.0, 1.0);
     if (type == PHAST_TRANS) {
         double a = d.amax[PHAST_TRANS];
-        P->disp = make_double3(xmul(xsub(xmul(2.0, u_a), 1.0), a), xmul(xsub(xmul(2.0, u_b), 1.0), a),
-                               xmul(xsub(xmul(2.0, u_c), 1.0), a));
+        P->disp = make_double3(xmul(sym_unit(b1.x, b1.y), a), xmul(sym_unit(b1.z, b1.w), a),
+                               xmul(sym_unit(b2.x, b2.y), a));
     } else {
-        P->angle = xmul(xsub(xmul(2.0, u_a), 1.0), d.amax[type]);
+        P->angle = xmul(sym_unit(b1.x, b1.y), d.amax[type]);
     }
 }
 

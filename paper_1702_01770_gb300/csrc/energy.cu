@@ -23,7 +23,7 @@ energy_kernel(const SysDesc d, int B, const double* __restrict__ xyz, double* __
     } else {
         Slot<PT> s(smem + (size_t)w * L.bytes, L);
         build_working<32, PT>(d, x64, s, g);
-        E = full_energy_working<32, PT>(d, x64, s, g);
+        E = full_energy_working<32, PT>(d, s, g);
     }
     if (g.lane == 0) E_out[b] = E;
 }
@@ -62,7 +62,7 @@ delta_kernel(const SysDesc d, int B, const double* __restrict__ xyz, const phast
     double dE = __longlong_as_double(0x7ff8000000000000ll);   // NaN for a degenerate or invalid move
     const bool ok = valid && make_new_positions<32, PT>(d, x64, P, M, s, g);
     if (ok) {
-        double part = local_delta<32, PT>(d, x64, P, M, s, g) + pair_delta<32, PT, 4>(d, M, P.chain, s, g);
+        double part = local_delta<32, PT>(d, P, M, s, g) + pair_delta<32, PT, 4>(d, M, P.chain, s, g);
         dE = g.sum(part);
     }
     if (g.lane == 0) dE_out[b] = dE;

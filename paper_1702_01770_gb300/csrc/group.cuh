@@ -1,14 +1,17 @@
 // group.cuh -- the per-walker machinery of the sweep, written for a group of
 // TPW lanes of one warp (TPW in {4, 8, 16, 32}) that owns one walker:
-//   * working positions in shared memory: FP32 coordinates relative to a
-//     per-chain FP64 origin plus an FP32 table of minimum-imaged origin
-//     differences (so every FP32 distance is formed from small numbers), or
-//     plain FP64 copies in the FP64-pair mode;
+//   * working positions in shared memory: FP32 coordinates relative to the
+//     FP64 centroid of their chain plus an FP32 table of minimum-imaged
+//     centroid differences (so every FP32 distance is formed from small
+//     numbers), or plain FP64 copies in the FP64-pair mode;
 //   * the walker's Philox stream drawn by the lanes in parallel (selection
 //     blocks and Marsaglia attempts side by side);
-//   * FP64 move geometry into group scratch;
-//   * dE = (bending + torsion window, FP64) + (moved x unmoved Lennard-Jones
-//     pairs, FP32 or FP64, R unmoved partners held in registers per lane);
+//   * FP64 move geometry into group scratch; scalar FP64 work (selection,
+//     sin/cos, rotation matrix, bin, acceptance) on one lane only -- FP64 is
+//     the scarce pipe of this chip, so no lane repeats another's FP64 work;
+//   * dE = (bending + torsion window) + (moved x unmoved Lennard-Jones pairs,
+//     R unmoved partners held in registers per lane), in the working
+//     precision, summed per lane and across the group in FP64;
 //   * full FP64 energies for the drift recompute.
 #pragma once
 
@@ -39,11 +42,17 @@ struct Group {
         for (int o = TPW / 2; o > 0; o >>= 1) v += __shfl_down_sync(mask, v, o, TPW);
         return __shfl_sync(mask, v, 0, TPW);
     }
+    // Tree sum valid on lane 0 only.
+    __device__ __forceinline__ double sum0(double v) const {
+#pragma unroll
+        for (int o = TPW / 2; o > 0; o >>= 1) v += __shfl_down_sync(mask, v, o, TPW);
+        return v;
+    }
 };
 
 // Shared-memory layout of one walker slot.
 struct SlotLayout {
-    int r_off, d_off, newr_off, orig_off, new64_off, bytes;
+    int r_off, d_off, newr_off, orig_off, new64_off, geo_off, bytes;
 };
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 template <typename PT>
@@ -55,6 +64,7 @@ __host__ __device__ inline SlotLayout slot_layout(int N, int nc, int mc) {
     L.newr_off = o;  o = align16(o + (int)sizeof(P4<PT>) * mc);
     L.orig_off = o;  o = align16(o + 8 * 3 * nc);
     L.new64_off = o; o = align16(o + 8 * 3 * mc);
+    L.geo_off = o;   o = align16(o + 8 * 16);
     L.bytes = o;
     return L;
 }
@@ -66,24 +76,41 @@ struct Slot {
     P4<PT>* newr;   // [max_chain] working positions of the moved monomers after the move
     double* orig;   // [nc * 3] chain origins (FP32 mode; zero in FP64 mode)
     double* new64;  // [max_chain * 3] FP64 positions of the moved monomers after the move
+    double* geo;    // [16] rotation matrix, centre, flags of the current move
     __device__ __forceinline__ Slot(unsigned char* p, const SlotLayout& L)
         : r((P4<PT>*)(p + L.r_off)), D((P4<PT>*)(p + L.d_off)), newr((P4<PT>*)(p + L.newr_off)),
-          orig((double*)(p + L.orig_off)), new64((double*)(p + L.new64_off)) {}
+          orig((double*)(p + L.orig_off)), new64((double*)(p + L.new64_off)), geo((double*)(p + L.geo_off)) {}
 };
 
 __device__ __forceinline__ double3 ld3(const double* p) { return make_double3(p[0], p[1], p[2]); }
 
-// Working copy of a walker: chain origins (first monomer, FP32 mode), relative
+// Minimum-imaged difference of the origins of chains a and b, in the working precision.
+template <typename PT>
+__device__ __forceinline__ P4<PT> origin_shift(const SysDesc& d, const double* orig, int a, int b) {
+    P4<PT> q;
+    q.x = (PT)mimage64(orig[3 * a + 0] - orig[3 * b + 0], d.box_L, d.inv_L);
+    q.y = (PT)mimage64(orig[3 * a + 1] - orig[3 * b + 1], d.box_L, d.inv_L);
+    q.z = (PT)mimage64(orig[3 * a + 2] - orig[3 * b + 2], d.box_L, d.inv_L);
+    q.tag = 0;
+    return q;
+}
+
+// Working copy of a walker: chain origins (FP64 centroid, FP32 mode), relative
 // coordinates, origin-difference table.  x64 is the walker's FP64 [N][3].
 template <int TPW, typename PT>
 __device__ void build_working(const SysDesc& d, const double* x64, Slot<PT>& s, const Group<TPW>& g) {
     const bool rel = sizeof(PT) == 4;
     const int nc = d.n_chains;
     for (int c = g.lane; c < nc; c += TPW) {
-        const double* p = x64 + 3 * d.chain_off[c];
-        s.orig[3 * c + 0] = rel ? p[0] : 0.0;
-        s.orig[3 * c + 1] = rel ? p[1] : 0.0;
-        s.orig[3 * c + 2] = rel ? p[2] : 0.0;
+        double sx = 0.0, sy = 0.0, sz = 0.0;
+        const int o = d.chain_off[c], n = d.chain_off[c + 1] - o;
+        if (rel) {
+            for (int j = o; j < o + n; ++j) { sx += x64[3 * j]; sy += x64[3 * j + 1]; sz += x64[3 * j + 2]; }
+            sx /= n; sy /= n; sz /= n;
+        }
+        s.orig[3 * c + 0] = sx;
+        s.orig[3 * c + 1] = sy;
+        s.orig[3 * c + 2] = sz;
     }
     g.sync();
     for (int j = g.lane; j < d.N; j += TPW) {
@@ -95,45 +122,78 @@ __device__ void build_working(const SysDesc& d, const double* x64, Slot<PT>& s, 
         q.tag = (int)d.seq[j] | (c << 1);
         s.r[j] = q;
     }
-    for (int p = g.lane; p < nc * nc; p += TPW) {
-        int a = p / nc, b = p % nc;
-        P4<PT> q;
-        q.x = (PT)mimage64(s.orig[3 * a + 0] - s.orig[3 * b + 0], d.box_L, d.inv_L);
-        q.y = (PT)mimage64(s.orig[3 * a + 1] - s.orig[3 * b + 1], d.box_L, d.inv_L);
-        q.z = (PT)mimage64(s.orig[3 * a + 2] - s.orig[3 * b + 2], d.box_L, d.inv_L);
-        q.tag = 0;
-        s.D[p] = q;
-    }
+    for (int p = g.lane; p < nc * nc; p += TPW) s.D[p] = origin_shift<PT>(d, s.orig, p / nc, p % nc);
     g.sync();
 }
 
+// After an accepted rigid translation by disp of chain c (FP32 mode): move the
+// chain's origin with it, so its relative coordinates stay unchanged and small.
+template <int TPW, typename PT>
+__device__ void rebase_translated(const SysDesc& d, int c, double3 disp, Slot<PT>& s, const Group<TPW>& g) {
+    if (g.lane == 0) {
+        s.orig[3 * c + 0] += disp.x;
+        s.orig[3 * c + 1] += disp.y;
+        s.orig[3 * c + 2] += disp.z;
+    }
+    g.sync();
+    const int nc = d.n_chains;
+    for (int b = g.lane; b < nc; b += TPW) {
+        s.D[c * nc + b] = origin_shift<PT>(d, s.orig, c, b);
+        s.D[b * nc + c] = origin_shift<PT>(d, s.orig, b, c);
+    }
+}
+
 // Draw move t: lanes compute Philox blocks 0..TPW-1 at once (blocks 0-2 are the
-// selection, block 3+j is Marsaglia attempt j); further rounds of attempts
-// follow only when the first round found no point in the disc.
+// selection, block 3+j is Marsaglia attempt j); lane 0 turns the selection
+// blocks into the move and broadcasts it; further rounds of attempts follow
+// only when the first round found no point in the disc.  u_acc is valid on
+// lane 0 only.
 template <int TPW>
 __device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, const Group<TPW>& g) {
-    uint4 blk = stream_block(seed, t, (uint32_t)g.lane);
+    const uint4 blk = stream_block(seed, t, (uint32_t)g.lane);
     uint4 b[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i)
+    for (int i = 1; i < 3; ++i)
         b[i] = make_uint4(g.bcast(blk.x, i), g.bcast(blk.y, i), g.bcast(blk.z, i), g.bcast(blk.w, i));
+    b[0] = blk;
     Proposal P;
-    propose_select(d, b[0], b[1], b[2], &P);
+    int packed = 0;
+    double amp = 0.0, dy = 0.0, dz = 0.0;
+    if (g.lane == 0) {
+        propose_select(d, b[0], b[1], b[2], &P);
+        packed = P.type | (P.chain << 2) | (P.index << 8);
+        amp = P.type == PHAST_TRANS ? P.disp.x : P.angle;
+        dy = P.disp.y;
+        dz = P.disp.z;
+    }
+    packed = (int)g.bcast((uint32_t)packed, 0);
+    P.type = packed & 3;
+    P.chain = (packed >> 2) & 63;
+    P.index = packed >> 8;
+    amp = g.bcastd(amp, 0);
+    P.angle = 0.0;
+    P.disp = make_double3(0.0, 0.0, 0.0);
+    P.axis = make_double3(0.0, 0.0, 1.0);
+    if (P.type == PHAST_TRANS) {
+        P.disp = make_double3(amp, g.bcastd(dy, 0), g.bcastd(dz, 0));
+    } else {
+        P.angle = amp;
+    }
     if (P.type == PHAST_PIVOT || P.type == PHAST_ROT) {
-        double3 ax = make_double3(0.0, 0.0, 1.0);
-        bool ok = (g.lane >= 3) && marsaglia_try(blk, &ax);
-        unsigned bits = (__ballot_sync(g.mask, ok) >> g.base) & (TPW == 32 ? 0xffffffffu : ((1u << TPW) - 1u));
+        const unsigned gm = TPW == 32 ? 0xffffffffu : ((1u << TPW) - 1u);
+        double v1 = 0.0, v2 = 0.0, sq = 0.0;
+        bool ok = (g.lane >= 3) && marsaglia_in_disc(blk, &v1, &v2, &sq);
+        unsigned bits = (__ballot_sync(g.mask, ok) >> g.base) & gm;
         for (int round = 1; bits == 0 && round * TPW <= 2 + PHAST_MARSAGLIA_TRIES; ++round) {
-            uint32_t blkid = (uint32_t)(round * TPW + g.lane);
-            bool in = blkid <= 2 + PHAST_MARSAGLIA_TRIES;
-            ok = in && marsaglia_try(stream_block(seed, t, blkid), &ax);
-            bits = (__ballot_sync(g.mask, ok) >> g.base) & (TPW == 32 ? 0xffffffffu : ((1u << TPW) - 1u));
+            const uint32_t blkid = (uint32_t)(round * TPW + g.lane);
+            ok = blkid <= 2 + PHAST_MARSAGLIA_TRIES && marsaglia_in_disc(stream_block(seed, t, blkid), &v1, &v2, &sq);
+            bits = (__ballot_sync(g.mask, ok) >> g.base) & gm;
         }
         if (bits) {
-            int src = __ffs(bits) - 1;
+            const int src = __ffs(bits) - 1;
+            double3 ax = make_double3(0.0, 0.0, 1.0);
+            if (g.lane == src) ax = marsaglia_axis(v1, v2, sq);
             P.axis = make_double3(g.bcastd(ax.x, src), g.bcastd(ax.y, src), g.bcastd(ax.z, src));
-        } else {
-            P.axis = make_double3(0.0, 0.0, 1.0);
         }
     }
     return P;
@@ -152,6 +212,13 @@ __device__ __forceinline__ MoveSet move_set(const SysDesc& d, int type, int chai
     return M;
 }
 
+// Pair evaluations of a move between different chains (2 per pair).
+__device__ __forceinline__ uint64_t move_pair_evals_inter(const SysDesc& d, int type, int chain, const MoveSet& M) {
+    const int nc = d.chain_off[chain + 1] - d.chain_off[chain];
+    const int m = (type == PHAST_CRANK) ? 1 : M.hi - M.lo + 1;
+    return 2ull * m * (d.N - nc);
+}
+
 // Pair evaluations a move costs (2 per changed Lennard-Jones pair).
 __device__ __forceinline__ uint64_t move_pair_evals(const SysDesc& d, int type, const MoveSet& M) {
     int m = M.hi - M.lo + 1;
@@ -161,48 +228,62 @@ __device__ __forceinline__ uint64_t move_pair_evals(const SysDesc& d, int type, 
 }
 
 // FP64 positions (new64) and working positions (newr) of the moved monomers.
-// Returns false for a degenerate crankshaft axis.
+// Lane 0 builds the centre and rotation (into the slot's geo scratch); every
+// lane then moves its share of the monomers.  Returns false for a degenerate
+// crankshaft axis.
 template <int TPW, typename PT>
 __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Proposal& P, const MoveSet& M,
                                    Slot<PT>& s, const Group<TPW>& g) {
     const int m = M.hi - M.lo + 1;
     const int c = P.chain, o = d.chain_off[c], n = d.chain_off[c + 1] - o;
-    Rot3 R;
-    double3 center = make_double3(0.0, 0.0, 0.0);
-    if (P.type != PHAST_TRANS) {
-        double3 axis = P.axis;
+    if (P.type != PHAST_TRANS && g.lane == 0) {
+        double3 axis = P.axis, center;
+        double ok = 1.0;
         if (P.type == PHAST_PIVOT) {
             center = ld3(x64 + 3 * (o + P.index));
-        } else if (P.type == PHAST_ROT) {
+        } else if (P.type == PHAST_ROT) {   // centroid: running sum j = 0..n-1, then / n
             double sx = 0.0, sy = 0.0, sz = 0.0;
-            if (g.lane == 0) {   // centroid: running sum j = 0..n-1, then / n
-                for (int j = o; j < o + n; ++j) {
-                    sx = xadd(sx, x64[3 * j + 0]);
-                    sy = xadd(sy, x64[3 * j + 1]);
-                    sz = xadd(sz, x64[3 * j + 2]);
-                }
-                sx = xdiv(sx, (double)n); sy = xdiv(sy, (double)n); sz = xdiv(sz, (double)n);
+            for (int j = o; j < o + n; ++j) {
+                sx = xadd(sx, x64[3 * j + 0]);
+                sy = xadd(sy, x64[3 * j + 1]);
+                sz = xadd(sz, x64[3 * j + 2]);
             }
-            center = make_double3(g.bcastd(sx, 0), g.bcastd(sy, 0), g.bcastd(sz, 0));
+            center = make_double3(xdiv(sx, (double)n), xdiv(sy, (double)n), xdiv(sz, (double)n));
         } else {   // crankshaft about the axis through monomers i-1 and i+1
-            int i = o + P.index;
-            double3 a = ld3(x64 + 3 * (i - 1)), b = ld3(x64 + 3 * (i + 1));
-            double ex = xsub(b.x, a.x), ey = xsub(b.y, a.y), ez = xsub(b.z, a.z);
-            double len = xsqrt(xadd(xadd(xmul(ex, ex), xmul(ey, ey)), xmul(ez, ez)));
-            if (!(len > 1e-12)) return false;
-            axis = make_double3(xdiv(ex, len), xdiv(ey, len), xdiv(ez, len));
+            const int i = o + P.index;
+            const double3 a = ld3(x64 + 3 * (i - 1)), b = ld3(x64 + 3 * (i + 1));
+            const double ex = xsub(b.x, a.x), ey = xsub(b.y, a.y), ez = xsub(b.z, a.z);
+            const double len = xsqrt(xadd(xadd(xmul(ex, ex), xmul(ey, ey)), xmul(ez, ez)));
+            if (!(len > 1e-12)) ok = 0.0;
+            else axis = make_double3(xdiv(ex, len), xdiv(ey, len), xdiv(ez, len));
             center = a;
         }
         double sn, cs;
         taylor_sincos(P.angle, &sn, &cs);
-        R = rodrigues(axis.x, axis.y, axis.z, sn, cs);
+        const Rot3 R = rodrigues(axis.x, axis.y, axis.z, sn, cs);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) s.geo[k] = R.m[k];
+        s.geo[9] = center.x;
+        s.geo[10] = center.y;
+        s.geo[11] = center.z;
+        s.geo[12] = ok;
+    }
+    g.sync();
+    if (P.type != PHAST_TRANS && s.geo[12] == 0.0) return false;
+    Rot3 R;
+    double3 center = make_double3(0.0, 0.0, 0.0);
+    if (P.type != PHAST_TRANS) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) R.m[k] = s.geo[k];
+        center = make_double3(s.geo[9], s.geo[10], s.geo[11]);
     }
     const bool rel = sizeof(PT) == 4;
     const double ox = rel ? s.orig[3 * c + 0] : 0.0, oy = rel ? s.orig[3 * c + 1] : 0.0,
                  oz = rel ? s.orig[3 * c + 2] : 0.0;
     for (int q = g.lane; q < m; q += TPW) {
-        int j = M.lo + q;
-        double3 x = ld3(x64 + 3 * j), y;
+        const int j = M.lo + q;
+        const double3 x = ld3(x64 + 3 * j);
+        double3 y;
         if (P.type == PHAST_TRANS)
             y = make_double3(xadd(x.x, P.disp.x), xadd(x.y, P.disp.y), xadd(x.z, P.disp.z));
         else
@@ -221,27 +302,58 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
     return true;
 }
 
-// This lane's share of the bending/torsion change (FP64).
+// Bending and torsion terms from working positions (any precision; positions
+// of one chain share an origin, so bond vectors are plain differences).
+__device__ __forceinline__ float rsqrt_w(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_w(double x) { return 1.0 / sqrt(x); }
+
+template <typename PT, class Pos>
+__device__ __forceinline__ PT bend_w(const Pos& pos, int o, int k) {
+    const P4<PT> x0 = pos(o + k - 1), x1 = pos(o + k), x2 = pos(o + k + 1);
+    const PT ax = x1.x - x0.x, ay = x1.y - x0.y, az = x1.z - x0.z;
+    const PT bx = x2.x - x1.x, by = x2.y - x1.y, bz = x2.z - x1.z;
+    const PT ab = ax * bx + ay * by + az * bz;
+    const PT aa = ax * ax + ay * ay + az * az, bb = bx * bx + by * by + bz * bz;
+    if (sizeof(PT) == 8) return (PT)1 - ab / (sqrt(aa) * sqrt(bb));
+    return (PT)1 - ab * rsqrt_w(aa * bb);
+}
+
+template <typename PT, class Pos>
+__device__ __forceinline__ PT torsion_w(const Pos& pos, int o, int j) {
+    const P4<PT> x0 = pos(o + j), x1 = pos(o + j + 1), x2 = pos(o + j + 2), x3 = pos(o + j + 3);
+    const PT b0x = x1.x - x0.x, b0y = x1.y - x0.y, b0z = x1.z - x0.z;
+    const PT b1x = x2.x - x1.x, b1y = x2.y - x1.y, b1z = x2.z - x1.z;
+    const PT b2x = x3.x - x2.x, b2y = x3.y - x2.y, b2z = x3.z - x2.z;
+    const PT n1x = b0y * b1z - b0z * b1y, n1y = b0z * b1x - b0x * b1z, n1z = b0x * b1y - b0y * b1x;
+    const PT n2x = b1y * b2z - b1z * b2y, n2y = b1z * b2x - b1x * b2z, n2z = b1x * b2y - b1y * b2x;
+    const PT n12 = n1x * n2x + n1y * n2y + n1z * n2z;
+    const PT n11 = n1x * n1x + n1y * n1y + n1z * n1z, n22 = n2x * n2x + n2y * n2y + n2z * n2z;
+    if (n11 * n22 < (PT)1e-20) return (PT)0;
+    if (sizeof(PT) == 8) return n12 / (sqrt(n11) * sqrt(n22));
+    return n12 * rsqrt_w(n11 * n22);
+}
+
+// This lane's share of the bending/torsion change, in the working precision.
 template <int TPW, typename PT>
-__device__ double local_delta(const SysDesc& d, const double* x64, const Proposal& P, const MoveSet& M,
-                              const Slot<PT>& s, const Group<TPW>& g) {
+__device__ double local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M, const Slot<PT>& s,
+                              const Group<TPW>& g) {
     int vb0, nb, jt0, nt;
     local_window(d, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt);
     const int o = d.chain_off[P.chain];
     const int items = 2 * (nb + nt);
-    double part = 0.0;
+    PT part = (PT)0;
     for (int it = g.lane; it < items; it += TPW) {
         const bool after = it & 1;
         const int k = it >> 1;
-        auto pos = [&](int j) -> double3 {
-            if (after && j >= M.lo && j <= M.hi) return ld3(s.new64 + 3 * (j - M.lo));
-            return ld3(x64 + 3 * j);
+        auto pos = [&](int j) -> P4<PT> {
+            if (after && j >= M.lo && j <= M.hi) return s.newr[j - M.lo];
+            return s.r[j];
         };
-        double term = (k < nb) ? d.k_bend * bend_term(pos, o, vb0 + k)
-                               : -d.k_tors * torsion_term(pos, o, jt0 + (k - nb));
+        const PT term = (k < nb) ? (PT)d.k_bend * bend_w<PT>(pos, o, vb0 + k)
+                                 : -(PT)d.k_tors * torsion_w<PT>(pos, o, jt0 + (k - nb));
         part += after ? term : -term;
     }
-    return part;
+    return (double)part;
 }
 
 __device__ __forceinline__ float fast_rcp(float x) {
@@ -251,15 +363,23 @@ __device__ __forceinline__ float fast_rcp(float x) {
 }
 __device__ __forceinline__ float pair_rcp(float x) { return fast_rcp(x); }
 __device__ __forceinline__ double pair_rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float pair_rint(float x) { return rintf(x); }
-__device__ __forceinline__ double pair_rint(double x) { return rint(x); }
 
-// r^-12 - C r^-6 of one displacement with the per-partner minimum image.
+// Nearest integer to x * iL on the FMA pipe: adding 1.5 * 2^23 to the exact
+// product rounds it to an integer (round to nearest even) for |x iL| < 2^22;
+// the special-function unit (where cvt.rni runs) stays free for the reciprocal.
+__device__ __forceinline__ float image_count(float x, float iL) {
+    const float M = 12582912.0f;   // 1.5 * 2^23
+    return __fsub_rn(__fmaf_rn(x, iL, M), M);
+}
+__device__ __forceinline__ double image_count(double x, double iL) { return rint(x * iL); }
+
+// r^-12 - C r^-6 of one displacement with the per-partner minimum image
+// (Lj = iLj = 0 leaves the displacement unchanged).
 template <typename PT>
 __device__ __forceinline__ PT lj_pair(PT dx, PT dy, PT dz, PT Lj, PT iLj, PT C) {
-    dx -= Lj * pair_rint(dx * iLj);
-    dy -= Lj * pair_rint(dy * iLj);
-    dz -= Lj * pair_rint(dz * iLj);
+    dx -= Lj * image_count(dx, iLj);
+    dy -= Lj * image_count(dy, iLj);
+    dz -= Lj * image_count(dz, iLj);
     PT r2 = dx * dx + dy * dy + dz * dz;
     PT ir2 = pair_rcp(r2);
     PT ir6 = ir2 * ir2 * ir2;
@@ -278,7 +398,7 @@ __device__ double pair_delta(const SysDesc& d, const MoveSet& M, int mchain, con
     const PT L = (PT)d.box_L, iL = (PT)d.inv_L;
     const PT kin = (PT)d.k_lj_intra, kout = (PT)d.k_lj_inter;
     const PT far = (PT)1.0e4;
-    double part = 0.0;
+    PT part = (PT)0;
     for (int t0 = g.lane; t0 < U; t0 += TPW * R) {
         PT qx[R], qy[R], qz[R], Lj[R], iLj[R], C0[R], C1[R], kap[R], acc[R];
 #pragma unroll
@@ -321,9 +441,9 @@ __device__ double pair_delta(const SysDesc& d, const MoveSet& M, int mchain, con
             }
         }
 #pragma unroll
-        for (int u = 0; u < R; ++u) part += (double)(kap[u] * acc[u]);
+        for (int u = 0; u < R; ++u) part += kap[u] * acc[u];
     }
-    return part;
+    return (double)part;
 }
 
 // Full FP64 energy (Eq. 2 per chain + inter-chain term of Eq. 3) of the
@@ -360,14 +480,13 @@ __device__ double full_energy64(const SysDesc& d, const double* x64, const Group
 // Full energy with the Lennard-Jones pairs in the working precision (from the
 // working copy) and the local terms in FP64 (from x64).
 template <int TPW, typename PT>
-__device__ double full_energy_working(const SysDesc& d, const double* x64, const Slot<PT>& s,
-                                      const Group<TPW>& g) {
+__device__ double full_energy_working(const SysDesc& d, const Slot<PT>& s, const Group<TPW>& g) {
     double part = 0.0;
-    auto pos = [&](int j) -> double3 { return ld3(x64 + 3 * j); };
+    auto pos = [&](int j) -> P4<PT> { return s.r[j]; };
     for (int c = 0; c < d.n_chains; ++c) {
         int o = d.chain_off[c], n = d.chain_off[c + 1] - o;
-        for (int k = 1 + g.lane; k <= n - 2; k += TPW) part += d.k_bend * bend_term(pos, o, k);
-        for (int j = g.lane; j <= n - 4; j += TPW) part -= d.k_tors * torsion_term(pos, o, j);
+        for (int k = 1 + g.lane; k <= n - 2; k += TPW) part += (double)((PT)d.k_bend * bend_w<PT>(pos, o, k));
+        for (int j = g.lane; j <= n - 4; j += TPW) part -= (double)((PT)d.k_tors * torsion_w<PT>(pos, o, j));
     }
     const PT L = (PT)d.box_L, iL = (PT)d.inv_L;
     for (int i = 0; i < d.N; ++i) {

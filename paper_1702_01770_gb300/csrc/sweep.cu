@@ -116,65 +116,69 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
     int bin = a.bin[gw];
     uint64_t t = a.t[gw];
     const uint64_t seed = a.seed[gw];
-    uint64_t att[4] = {0, 0, 0, 0}, acc_n[4] = {0, 0, 0, 0}, pev = 0, nrec = 0;
+    uint64_t att[4] = {0, 0, 0, 0}, acc_n[4] = {0, 0, 0, 0}, pev = 0, pevx = 0, nrec = 0;
     double drift_max = 0.0;
     uint32_t* hw = a.hist_walker ? a.hist_walker + sd.hw_off + (int64_t)w_local * sd.n_bins : nullptr;
     const bool tracing = a.trace && s_id == 0 && w_local < a.trace_walkers;
     const int64_t n_moves = a.n_sweeps * sd.N;
     const uint64_t period = (uint64_t)sd.recompute_every * (uint64_t)sd.N;
 
+    const bool rel = sizeof(PT) == 4;
     build_working<TPW, PT>(sd, x64, slot, g);
     for (int64_t it = 0; it < n_moves; ++it) {
         const Proposal P = propose_group<TPW>(sd, seed, t, g);
         const MoveSet M = move_set(sd, P.type, P.chain, P.index);
         const bool ok = make_new_positions<TPW, PT>(sd, x64, P, M, slot, g);
-        double dE = __longlong_as_double(0x7ff8000000000000ll);
-        if (ok) {
-            double part = local_delta<TPW, PT>(sd, x64, P, M, slot, g) +
-                          pair_delta<TPW, PT, 4>(sd, M, P.chain, slot, g);
-            dE = g.sum(part);
-        }
-        const double E_new = E + dE;
-        const int b_new = bin_of(sd, E_new);
-        bool acc = false;
-        if (b_new >= 0) {
-            const double dl = __ldg(lnW + b_new) - __ldg(lnW + bin);
-            acc = (dl >= 0.0) || (P.u_acc < exp(dl));
-        }
-        if (acc) {
-            const int m = M.hi - M.lo + 1;
-            for (int q = g.lane; q < m; q += TPW) {
-                const int j = M.lo + q;
-                x64[3 * j + 0] = slot.new64[3 * q + 0];
-                x64[3 * j + 1] = slot.new64[3 * q + 1];
-                x64[3 * j + 2] = slot.new64[3 * q + 2];
-                slot.r[j] = slot.newr[q];
+        double part = 0.0;
+        if (ok) part = local_delta<TPW, PT>(sd, P, M, slot, g) + pair_delta<TPW, PT, 4>(sd, M, P.chain, slot, g);
+        const double dsum = g.sum0(part);
+        uint32_t acc = 0;
+        if (g.lane == 0) {   // decision, histogram and bookkeeping on one lane
+            const double dE = ok ? dsum : __longlong_as_double(0x7ff8000000000000ll);
+            const double E_new = E + dE;
+            const int b_new = bin_of(sd, E_new);
+            if (b_new >= 0) {
+                const double dl = __ldg(lnW + b_new) - __ldg(lnW + bin);
+                acc = (dl >= 0.0) || (P.u_acc < exp(dl));
             }
-            E = E_new;
-            bin = b_new;
-        }
-        g.sync();
-        if (g.lane == 0) {
+            if (acc) { E = E_new; bin = b_new; }
             atomicAdd(hist + bin, 1u);
             if (hw) atomicAdd(hw + bin, 1u);
             att[P.type]++;
             acc_n[P.type] += acc;
             pev += move_pair_evals(sd, P.type, M);
+            pevx += move_pair_evals_inter(sd, P.type, P.chain, M);
             if (tracing) {
                 phast_trace tr;
                 tr.dE = dE;
                 tr.bin_after = bin;
-                tr.accepted = acc;
+                tr.accepted = (int32_t)acc;
                 a.trace[(int64_t)w_local * n_moves + it] = tr;
             }
         }
+        acc = g.bcast(acc, 0);
+        if (acc) {
+            const int m = M.hi - M.lo + 1;
+            const bool keep_r = rel && P.type == PHAST_TRANS;   // the origin moves instead
+            for (int q = g.lane; q < m; q += TPW) {
+                const int j = M.lo + q;
+                x64[3 * j + 0] = slot.new64[3 * q + 0];
+                x64[3 * j + 1] = slot.new64[3 * q + 1];
+                x64[3 * j + 2] = slot.new64[3 * q + 2];
+                if (!keep_r) slot.r[j] = slot.newr[q];
+            }
+            if (keep_r) rebase_translated<TPW, PT>(sd, P.chain, P.disp, slot, g);
+        }
+        g.sync();
         ++t;
         if (period && (t % period) == 0) {   // FP64 full energy kills the drift of the running sum
             const double Ef = full_energy64<TPW>(sd, x64, g);
-            drift_max = fmax(drift_max, fabs(E - Ef));
-            const int bf = bin_of(sd, Ef);
-            if (bf >= 0) { E = Ef; bin = bf; }
-            ++nrec;
+            if (g.lane == 0) {
+                drift_max = fmax(drift_max, fabs(E - Ef));
+                const int bf = bin_of(sd, Ef);
+                if (bf >= 0) { E = Ef; bin = bf; }
+                ++nrec;
+            }
             g.sync();
             build_working<TPW, PT>(sd, x64, slot, g);
         }
@@ -186,6 +190,7 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         phast_walker_stats* st = a.stats + gw;
         for (int i = 0; i < 4; ++i) { st->attempts[i] += att[i]; st->accepts[i] += acc_n[i]; }
         st->pair_evals += pev;
+        st->pair_evals_inter += pevx;
         st->recomputes += nrec;
         st->drift_max = fmax(st->drift_max, drift_max);
     }
@@ -286,7 +291,7 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
     int bin = a.bin[gw];
     uint64_t t = a.t[gw];
     const uint64_t seed = a.seed[gw];
-    uint64_t att[4] = {0, 0, 0, 0}, acc_n[4] = {0, 0, 0, 0}, pev = 0, nrec = 0;
+    uint64_t att[4] = {0, 0, 0, 0}, acc_n[4] = {0, 0, 0, 0}, pev = 0, pevx = 0, nrec = 0;
     double drift_max = 0.0;
     unsigned long long* hs = a.hist_sum
         ? a.hist_sum + a.hs_off[s_id] + (int64_t)jk_block(w_local, sd.n_walkers, a.n_jk) * sd.n_bins : nullptr;
@@ -405,6 +410,7 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
             att[P.type]++;
             acc_n[P.type] += acc;
             pev += move_pair_evals(sd, P.type, M);
+            pevx += move_pair_evals_inter(sd, P.type, P.chain, M);
             if (tracing) {
                 phast_trace tr;
                 tr.dE = dE;
@@ -435,6 +441,7 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
         phast_walker_stats* st = a.stats + gw;
         for (int i = 0; i < 4; ++i) { st->attempts[i] += att[i]; st->accepts[i] += acc_n[i]; }
         st->pair_evals += pev;
+        st->pair_evals_inter += pevx;
         st->recomputes += nrec;
         st->drift_max = fmax(st->drift_max, drift_max);
     }
@@ -541,14 +548,14 @@ int launch_batched(phast_ctx* c, const SweepArgs& a0, int tpw, int wpc, bool fp3
 }
 
 void default_tile(const phast_ctx* c, int* tpw, int* wpc) {
-    // one warp per walker for large systems, smaller groups for small ones
+    // one warp per walker for large systems, smaller groups for small ones;
+    // as many walkers per CTA as 512 threads and the shared memory allow
     const int N = c->max_N;
+    const bool fp32 = c->desc[0].pair_precision == 32;
     *tpw = N >= 128 ? 32 : (N >= 48 ? 16 : 8);
-    int w = 512 / *tpw;
+    int w = kMaxTileThreads / *tpw;
     SlotLayout L;
-    while (w > 1 && batched_smem(c, true, w, &L) > 200 * 1024) w >>= 1;
-    while (w > 1 && batched_smem(c, false, w, &L) > 220 * 1024 && *tpw * w > 32) w >>= 1;
-    if (*tpw * w < 32) w = 32 / *tpw;
+    while (w * *tpw > 32 && batched_smem(c, fp32, w, &L) > 220 * 1024) w >>= 1;
     *wpc = w;
 }
 

@@ -60,7 +60,7 @@ class _MicroOut(C.Structure):
 MOVE_DTYPE = np.dtype([("type", "<i4"), ("chain", "<i4"), ("index", "<i4"), ("pad", "<i4"),
                        ("axis", "<f8", 3), ("angle", "<f8"), ("disp", "<f8", 3)])
 STATS_DTYPE = np.dtype([("attempts", "<u8", 4), ("accepts", "<u8", 4), ("pair_evals", "<u8"),
-                        ("recomputes", "<u8"), ("drift_max", "<f8"), ("pad", "<f8")])
+                        ("pair_evals_inter", "<u8"), ("recomputes", "<u8"), ("drift_max", "<f8")])
 TRACE_DTYPE = np.dtype([("dE", "<f8"), ("bin_after", "<i4"), ("accepted", "<i4")])
 
 _lib = None
