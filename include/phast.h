@@ -239,6 +239,32 @@ int phast_micro_analysis(int32_t K, double e_min, double bin_width, const double
                          const phast_micro_out* out, void* workspace, size_t workspace_bytes,
                          void* stream);
 
+/* Allocation-free variant of phast_micro_analysis, for callers that cannot
+ * allocate device memory when they run the analysis (a plug-in working inside
+ * another program's CUDA context under a fixed memory budget, or code between
+ * the steps of a loop that must leave the device's allocations untouched).  It
+ * takes no workspace: it uses a device array of PHAST_MICRO_NOALLOC_DOUBLES
+ * doubles (4 MiB) that the library reserves on every device where its module is
+ * loaded and keeps until the process exits.  The paper has no counterpart; this
+ * is a property of this library only.
+ *  - Same arguments and results as phast_micro_analysis minus the workspace.
+ *  - The call needs (1 + B) (3 K + 2 n_T + 2) doubles of that array, with B =
+ *    n_blocks when n_blocks >= 2 (else 0); a larger request fails with
+ *    PHAST_EINVAL and a message naming the sizes (use phast_micro_analysis).
+ *    K = 8000 bins with 64 temperatures and 16 blocks fits.
+ *  - The first call on a device looks up the array's device address (with that
+ *    device current) and caches it; make that first call before any stream
+ *    capture.
+ *  - Every call shares the one array and every element it reads is written
+ *    earlier in the same call, so nothing needs clearing; calls that overlap on
+ *    the GPU (other streams, other host threads) race on it.
+ *  - Calls no allocating routine. */
+#define PHAST_MICRO_NOALLOC_DOUBLES 524288
+int phast_micro_analysis_noalloc(int32_t K, double e_min, double bin_width, const double* lnW,
+                                 const uint64_t* hist, int32_t n_blocks, int32_t fd_half_width,
+                                 int32_t n_monomers, int32_t n_T, const double* T,
+                                 const phast_micro_out* out, void* stream);
+
 /* ---- checkpoint --------------------------------------------------------- */
 
 /* Serialise the walker state (coordinates, energies, bins, move indices,

@@ -219,3 +219,54 @@ extern "C" int phast_micro_analysis(int32_t K, double e_min, double bin_width, c
     PHAST_CUDA_TRY(cudaGetLastError());
     return PHAST_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant.  Some callers cannot allocate device memory at the
+// point where they need the analysis: a plug-in that runs inside another
+// program's CUDA context under a fixed memory budget, or code running between
+// the steps of a loop that must not change the device's allocations.  For them
+// the workspace lives in a file-scope device array that the library reserves
+// when its module is loaded on a device (and keeps until the process exits).
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+static __device__ __align__(256) double g_micro_scratch[PHAST_MICRO_NOALLOC_DOUBLES];
+
+namespace {
+std::mutex g_scratch_mu;
+double* g_scratch_addr[256];   // device address of g_micro_scratch, per device ordinal
+}  // namespace
+
+extern "C" int phast_micro_analysis_noalloc(int32_t K, double e_min, double bin_width, const double* lnW,
+                                            const uint64_t* hist, int32_t n_blocks, int32_t h, int32_t n_monomers,
+                                            int32_t n_T, const double* T, const phast_micro_out* out, void* stream) {
+    if (K < 1 || K > PHAST_MAX_BINS || n_T < 0 || (hist && n_blocks < 1))
+        return phast_micro_analysis(K, e_min, bin_width, lnW, hist, n_blocks, h, n_monomers, n_T, T, out,
+                                    nullptr, 0, stream);   // reports the argument error
+    const int R = 1 + ((hist && n_blocks >= 2) ? n_blocks : 0);
+    const size_t need = work_doubles(K, n_T, R);
+    if (need > (size_t)PHAST_MICRO_NOALLOC_DOUBLES)
+        return phast_set_error(PHAST_EINVAL,
+                               "phast_micro_analysis_noalloc: K=%d, n_T=%d, %d blocks need %zu doubles of scratch, "
+                               "more than the %d of the static workspace (use phast_micro_analysis)",
+                               K, n_T, n_blocks, need, PHAST_MICRO_NOALLOC_DOUBLES);
+    int dev = 0;
+    PHAST_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return phast_set_error(PHAST_EINVAL, "phast_micro_analysis_noalloc: device %d", dev);
+    double* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_scratch_mu);
+        if (!g_scratch_addr[dev]) {
+            // the array's name is a host-side stand-in; its device address is looked up once per device
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_micro_scratch);
+            if (e != cudaSuccess)
+                return phast_set_error(PHAST_ECUDA, "phast_micro_analysis_noalloc: cudaGetSymbolAddress: %s",
+                                       cudaGetErrorString(e));
+            g_scratch_addr[dev] = (double*)p;
+        }
+        scratch = g_scratch_addr[dev];
+    }
+    return phast_micro_analysis(K, e_min, bin_width, lnW, hist, n_blocks, h, n_monomers, n_T, T, out, scratch,
+                                sizeof(double) * (size_t)PHAST_MICRO_NOALLOC_DOUBLES, stream);
+}

@@ -26,7 +26,7 @@ ERRORS = {0: "PHAST_OK", -1: "PHAST_EINVAL", -2: "PHAST_ERANGE", -3: "PHAST_ENOM
 SYMBOLS = ["phast_energy", "phast_delta_energy", "phast_ctx_create", "phast_ctx_destroy", "phast_ctx_info",
            "phast_ctx_get_state", "phast_ctx_set_state", "phast_ctx_set_tile", "phast_ctx_get_tile",
            "phast_ctx_autotune", "phast_muca_sweep", "phast_weight_update", "phast_micro_workspace_size",
-           "phast_micro_analysis", "phast_ctx_checkpoint", "phast_ctx_restore", "phast_last_error",
+           "phast_micro_analysis", "phast_micro_analysis_noalloc", "phast_ctx_checkpoint", "phast_ctx_restore", "phast_last_error",
            "phast_version"]
 
 
@@ -91,6 +91,8 @@ def lib():
         L.phast_micro_workspace_size.restype = C.c_size_t
         L.phast_micro_analysis.argtypes = [i32, dbl, dbl, vp, vp, i32, i32, i32, i32, vp, P(_MicroOut), vp,
                                            C.c_size_t, vp]
+        L.phast_micro_analysis_noalloc.argtypes = [i32, dbl, dbl, vp, vp, i32, i32, i32, i32, vp, P(_MicroOut),
+                                                   vp]
         L.phast_ctx_checkpoint.argtypes = [vp, vp, P(C.c_size_t), vp]
         L.phast_ctx_restore.argtypes = [vp, vp, C.c_size_t, vp]
         L.phast_last_error.restype = C.c_char_p
@@ -333,8 +335,12 @@ class MicroResult:
 
 def phast_micro_analysis(lnW: torch.Tensor, e_min: float, bin_width: float, hist: torch.Tensor | None = None,
                          fd_half_width: int = 1, n_monomers: int = 1, T: torch.Tensor | None = None,
-                         workspace: torch.Tensor | None = None, stream=None) -> MicroResult:
-    """Eq. 4-6 plus canonical reweighting; hist int64 [n_blocks, K]; errors when n_blocks >= 2."""
+                         workspace: torch.Tensor | None = None, stream=None, noalloc: bool = False) -> MicroResult:
+    """Eq. 4-6 plus canonical reweighting; hist int64 [n_blocks, K]; errors when n_blocks >= 2.
+
+    noalloc=True calls phast_micro_analysis_noalloc, which takes no workspace
+    (it uses the library's static device scratch); the result tensors are still
+    allocated here by torch."""
     dev = lnW.device
     K = lnW.numel()
     n_blocks = 0 if hist is None else hist.numel() // K
@@ -350,6 +356,11 @@ def phast_micro_analysis(lnW: torch.Tensor, e_min: float, bin_width: float, hist
     for name in _MicroOut._fields_:
         v = getattr(r, name[0])
         setattr(o, name[0], None if v is None else v.data_ptr())
+    if noalloc:
+        _check(lib().phast_micro_analysis_noalloc(K, float(e_min), float(bin_width), _ptr(lnW), _ptr(hist), n_blocks,
+                                                  fd_half_width, n_monomers, n_T, _ptr(T), C.byref(o),
+                                                  _stream(stream)))
+        return r
     need = lib().phast_micro_workspace_size(K, n_T, n_blocks)
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=dev)
