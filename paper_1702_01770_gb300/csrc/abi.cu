@@ -63,6 +63,13 @@ int phast_build_desc(const phast_system* sys, const phast_ff* ff, const phast_mu
         if (!isfinite(d->C[i])) return phast_set_error(PHAST_EINVAL, "%s: non-finite coupling", what);
     if (!isfinite(d->k_bend) || !isfinite(d->k_tors) || !isfinite(d->k_lj_intra) || !isfinite(d->k_lj_inter))
         return phast_set_error(PHAST_EINVAL, "%s: non-finite force-field weight", what);
+    for (int i = 0; i < 4; ++i) d->C32[i] = (float)d->C[i];
+    d->L32 = (float)d->box_L;
+    d->iL32 = (float)d->inv_L;
+    d->kin32 = (float)d->k_lj_intra;
+    d->kout32 = (float)d->k_lj_inter;
+    d->kbend32 = (float)d->k_bend;
+    d->ktors32 = (float)d->k_tors;
     d->pair_precision = 64;
     if (mp) {
         if (!(mp->bin_width > 0.0) || !isfinite(mp->e_min) || !isfinite(mp->bin_width))

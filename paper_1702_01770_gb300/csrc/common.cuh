@@ -41,6 +41,8 @@ struct SysDesc {
     double p[4], amax[4];
     uint64_t thr[4];      // move-type thresholds: type i if 2n+1 < thr[i] (n the 52-bit uniform), see propose_select
     int32_t last_type, pad2[3];
+    float C32[4];         // FP32 copies for the FP32 working precision
+    float L32, iL32, kin32, kout32, kbend32, ktors32, pad3[2];
     int32_t chain_off[PHAST_MAX_CHAINS + 1];
     int32_t pad1[3];
     uint8_t seq[PHAST_MAX_MONOMERS];
@@ -169,8 +171,10 @@ __device__ __forceinline__ bool marsaglia_try(uint4 r, double3* axis) {
 // A proposed move, drawn from the walker stream.
 struct Proposal {
     int type, chain, index;
-    double angle, u_acc;
+    int attempt;            // winning Marsaglia attempt (-1: none won, axis (0, 0, 1))
+    double angle;
     double3 axis, disp;
+    uint32_t uz, uw;        // words of the acceptance uniform (block 2 z, w)
 };
 
 // Selection part of move t (blocks 0-2): the type is the first one with p > 0
@@ -186,7 +190,9 @@ __device__ __forceinline__ void propose_select(const SysDesc& d, uint4 b0, uint4
 #pragma unroll
     for (int i = 3; i >= 0; --i)
         if (d.p[i] > 0.0 && v < d.thr[i]) type = i;
-    P->u_acc = u52(b2.z, b2.w);
+    P->uz = b2.z;
+    P->uw = b2.w;
+    P->attempt = -1;
     P->type = type;
     P->chain = (int)(((uint64_t)b0.z * (uint64_t)d.n_chains) >> 32);
     int n = d.chain_off[P->chain + 1] - d.chain_off[P->chain];

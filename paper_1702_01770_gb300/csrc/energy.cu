@@ -43,7 +43,7 @@ delta_kernel(const SysDesc d, int B, const double* __restrict__ xyz, const phast
     const phast_move mv = moves[b];
     Proposal P;
     P.type = mv.type; P.chain = mv.chain; P.index = mv.index;
-    P.angle = mv.angle; P.u_acc = 0.0;
+    P.angle = mv.angle; P.uz = P.uw = 0u; P.attempt = -1;
     P.axis = make_double3(mv.axis[0], mv.axis[1], mv.axis[2]);
     P.disp = make_double3(mv.disp[0], mv.disp[1], mv.disp[2]);
     // a move outside the system (type, chain, interior index, amplitude) is
@@ -60,17 +60,28 @@ delta_kernel(const SysDesc d, int B, const double* __restrict__ xyz, const phast
     if (!valid) P.type = PHAST_TRANS, P.chain = 0, P.index = 0;
     const MoveSet M = move_set(d, P.type, P.chain, P.index);
     double dE = __longlong_as_double(0x7ff8000000000000ll);   // NaN for a degenerate or invalid move
-    const bool ok = valid && make_new_positions<32, PT>(d, x64, P, M, s, g);
+    bool fast = false;
+    const bool ok = valid && make_new_positions<32, PT>(d, x64, P, M, s, g, &fast);
     if (ok) {
-        double part = local_delta<32, PT>(d, P, M, s, g) + pair_delta<32, PT, 4>(d, M, P.chain, s, g);
-        dE = g.sum(part);
+        PT part = local_delta<32, PT>(d, P, M, s, g);
+        if constexpr (sizeof(PT) == 4) {
+            if (fast) part += pair_delta32<32, 4, true>(d, M, P.chain, s, g);
+            else part += pair_delta32<32, 4, false>(d, M, P.chain, s, g);
+        } else {
+            part += pair_delta<32, PT, 4, false>(d, M, P.chain, s, g);
+        }
+        dE = g.sum((double)part);
     }
     if (g.lane == 0) dE_out[b] = dE;
     if (xyz_new) {
+        if (sizeof(PT) == 4 && valid) prepare_exact<32, PT>(d, x64, P, P.axis, s, g);
         double* out = xyz_new + (size_t)b * d.N * 3;
-        for (int k = g.lane; k < 3 * d.N; k += 32) {
-            int j = k / 3;
-            out[k] = (ok && j >= M.lo && j <= M.hi) ? s.new64[k - 3 * M.lo] : x64[k];
+        for (int j = g.lane; j < d.N; j += 32) {
+            double3 y = ld3(x64 + 3 * j);
+            if (ok && j >= M.lo && j <= M.hi) y = exact_position(P, s.geo, y);
+            out[3 * j + 0] = y.x;
+            out[3 * j + 1] = y.y;
+            out[3 * j + 2] = y.z;
         }
     }
 }

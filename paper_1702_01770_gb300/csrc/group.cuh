@@ -43,7 +43,8 @@ struct Group {
         return __shfl_sync(mask, v, 0, TPW);
     }
     // Tree sum valid on lane 0 only.
-    __device__ __forceinline__ double sum0(double v) const {
+    template <typename T>
+    __device__ __forceinline__ T sum0(T v) const {
 #pragma unroll
         for (int o = TPW / 2; o > 0; o >>= 1) v += __shfl_down_sync(mask, v, o, TPW);
         return v;
@@ -61,10 +62,10 @@ __host__ __device__ inline SlotLayout slot_layout(int N, int nc, int mc) {
     int o = 0;
     L.r_off = o;     o = align16(o + (int)sizeof(P4<PT>) * N);
     L.d_off = o;     o = align16(o + (int)sizeof(P4<PT>) * nc * nc);
-    L.newr_off = o;  o = align16(o + (int)sizeof(P4<PT>) * mc);
+    L.newr_off = o;  o = align16(o + 32 * mc);   // FP64: P4<double>; FP32: two float4 per moved monomer
     L.orig_off = o;  o = align16(o + 8 * 3 * nc);
-    L.new64_off = o; o = align16(o + 8 * 3 * mc);
-    L.geo_off = o;   o = align16(o + 8 * 16);
+    L.new64_off = o; o = align16(o + (sizeof(PT) == 8 ? 8 * 3 * mc : 0));
+    L.geo_off = o;   o = align16(o + 8 * 32);
     L.bytes = o;
     return L;
 }
@@ -73,16 +74,40 @@ template <typename PT>
 struct Slot {
     P4<PT>* r;      // [N] working positions
     P4<PT>* D;      // [nc * nc] origin differences (FP32 mode)
-    P4<PT>* newr;   // [max_chain] working positions of the moved monomers after the move
+    P4<PT>* newr;   // [max_chain] moved monomers after the move (FP64 mode); in FP32 mode the same bytes
+                    // hold two float4 per moved monomer, old and new interleaved: (xo, xn, yo, yn), (zo, zn, tag, 0)
     double* orig;   // [nc * 3] chain origins (FP32 mode; zero in FP64 mode)
-    double* new64;  // [max_chain * 3] FP64 positions of the moved monomers after the move
-    double* geo;    // [16] rotation matrix, centre, flags of the current move
+    double* new64;  // [max_chain * 3] FP64 positions of the moved monomers after the move (FP64 mode)
+    double* geo;    // [32] FP64 rotation matrix, centre, flag; from geo + 16: FP32 matrix and centre
     __device__ __forceinline__ Slot(unsigned char* p, const SlotLayout& L)
         : r((P4<PT>*)(p + L.r_off)), D((P4<PT>*)(p + L.d_off)), newr((P4<PT>*)(p + L.newr_off)),
           orig((double*)(p + L.orig_off)), new64((double*)(p + L.new64_off)), geo((double*)(p + L.geo_off)) {}
 };
 
 __device__ __forceinline__ double3 ld3(const double* p) { return make_double3(p[0], p[1], p[2]); }
+
+// Force-field constants in the working precision (FP32 copies live in the descriptor).
+template <typename PT> struct FF;
+template <> struct FF<float> {
+    const SysDesc& d;
+    __device__ __forceinline__ float C(int i) const { return d.C32[i]; }
+    __device__ __forceinline__ float L() const { return d.L32; }
+    __device__ __forceinline__ float iL() const { return d.iL32; }
+    __device__ __forceinline__ float kin() const { return d.kin32; }
+    __device__ __forceinline__ float kout() const { return d.kout32; }
+    __device__ __forceinline__ float kbend() const { return d.kbend32; }
+    __device__ __forceinline__ float ktors() const { return d.ktors32; }
+};
+template <> struct FF<double> {
+    const SysDesc& d;
+    __device__ __forceinline__ double C(int i) const { return d.C[i]; }
+    __device__ __forceinline__ double L() const { return d.box_L; }
+    __device__ __forceinline__ double iL() const { return d.inv_L; }
+    __device__ __forceinline__ double kin() const { return d.k_lj_intra; }
+    __device__ __forceinline__ double kout() const { return d.k_lj_inter; }
+    __device__ __forceinline__ double kbend() const { return d.k_bend; }
+    __device__ __forceinline__ double ktors() const { return d.k_tors; }
+};
 
 // Minimum-imaged difference of the origins of chains a and b, in the working precision.
 template <typename PT>
@@ -143,12 +168,35 @@ __device__ void rebase_translated(const SysDesc& d, int c, double3 disp, Slot<PT
     }
 }
 
+// FP32 image of the Marsaglia coordinate v = 2u - 1 from block words (a, b):
+// v = ((a >> 6) - 2^25) 2^-25 + (2 (b >> 6) + 1) 2^-52, kept to within 6e-8.
+__device__ __forceinline__ float sym_unit32(uint32_t a) {
+    return __int2float_rn((int)(a >> 6) - (1 << 25)) * 2.98023223876953125e-8f;
+}
+
+// Disc test of one Marsaglia attempt, decided exactly as the FP64 test
+// s = v1^2 + v2^2 < 1 decides it: the FP32 estimate settles every case outside
+// a 1e-6 band around s = 1 (its error is below 5e-7); inside the band the FP64
+// test runs.  In FP32 mode the winner's FP32 axis serves the trial move.
+__device__ __forceinline__ bool disc_test(uint4 r, float* v1f, float* v2f, float* sf) {
+    *v1f = sym_unit32(r.x);
+    *v2f = sym_unit32(r.z);
+    *sf = *v1f * *v1f + *v2f * *v2f;
+    if (*sf < 1.0f - 1e-6f) return true;
+    if (*sf > 1.0f + 1e-6f) return false;
+    double v1, v2, sd;
+    return marsaglia_in_disc(r, &v1, &v2, &sd);
+}
+
 // Draw move t: lanes compute Philox blocks 0..TPW-1 at once (blocks 0-2 are the
 // selection, block 3+j is Marsaglia attempt j); lane 0 turns the selection
 // blocks into the move and broadcasts it; further rounds of attempts follow
-// only when the first round found no point in the disc.  u_acc is valid on
-// lane 0 only.
-template <int TPW>
+// only when the first round found no point in the disc.  The winning attempt
+// index is kept; the axis is exact FP64 in FP64 mode and the FP32 image of the
+// same axis in FP32 mode (whose exact axis is rebuilt at commit from the
+// winning block).  The acceptance words uz, uw are valid on lane 0 only
+// (u = u52(uz, uw) is formed only when the acceptance test needs it).
+template <int TPW, typename PT>
 __device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, const Group<TPW>& g) {
     const uint4 blk = stream_block(seed, t, (uint32_t)g.lane);
     uint4 b[3];
@@ -170,6 +218,7 @@ __device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, c
     P.type = packed & 3;
     P.chain = (packed >> 2) & 63;
     P.index = packed >> 8;
+    P.attempt = -1;
     amp = g.bcastd(amp, 0);
     P.angle = 0.0;
     P.disp = make_double3(0.0, 0.0, 0.0);
@@ -181,22 +230,48 @@ __device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, c
     }
     if (P.type == PHAST_PIVOT || P.type == PHAST_ROT) {
         const unsigned gm = TPW == 32 ? 0xffffffffu : ((1u << TPW) - 1u);
-        double v1 = 0.0, v2 = 0.0, sq = 0.0;
-        bool ok = (g.lane >= 3) && marsaglia_in_disc(blk, &v1, &v2, &sq);
+        uint4 mine = blk;
+        int round = 0;
+        float v1f = 0.f, v2f = 0.f, sf = 0.f;
+        bool ok = (g.lane >= 3) && disc_test(mine, &v1f, &v2f, &sf);
         unsigned bits = (__ballot_sync(g.mask, ok) >> g.base) & gm;
-        for (int round = 1; bits == 0 && round * TPW <= 2 + PHAST_MARSAGLIA_TRIES; ++round) {
+        while (bits == 0 && (round + 1) * TPW <= 2 + PHAST_MARSAGLIA_TRIES) {
+            ++round;
             const uint32_t blkid = (uint32_t)(round * TPW + g.lane);
-            ok = blkid <= 2 + PHAST_MARSAGLIA_TRIES && marsaglia_in_disc(stream_block(seed, t, blkid), &v1, &v2, &sq);
+            mine = stream_block(seed, t, blkid);
+            ok = blkid <= 2 + PHAST_MARSAGLIA_TRIES && disc_test(mine, &v1f, &v2f, &sf);
             bits = (__ballot_sync(g.mask, ok) >> g.base) & gm;
         }
         if (bits) {
             const int src = __ffs(bits) - 1;
-            double3 ax = make_double3(0.0, 0.0, 1.0);
-            if (g.lane == src) ax = marsaglia_axis(v1, v2, sq);
-            P.axis = make_double3(g.bcastd(ax.x, src), g.bcastd(ax.y, src), g.bcastd(ax.z, src));
+            P.attempt = round * TPW + src - 3;
+            if (sizeof(PT) == 8) {
+                double3 ax = make_double3(0.0, 0.0, 1.0);
+                if (g.lane == src) {
+                    double v1, v2, sd;
+                    marsaglia_in_disc(mine, &v1, &v2, &sd);
+                    ax = marsaglia_axis(v1, v2, sd);
+                }
+                P.axis = make_double3(g.bcastd(ax.x, src), g.bcastd(ax.y, src), g.bcastd(ax.z, src));
+            } else {
+                float q = sqrtf(fmaxf(1.0f - sf, 0.0f));
+                float ax = 2.0f * v1f * q, ay = 2.0f * v2f * q, az = 1.0f - 2.0f * sf;
+                ax = __shfl_sync(g.mask, ax, src, TPW);
+                ay = __shfl_sync(g.mask, ay, src, TPW);
+                az = __shfl_sync(g.mask, az, src, TPW);
+                P.axis = make_double3(ax, ay, az);
+            }
         }
     }
     return P;
+}
+
+// Exact FP64 axis of a pivot or rotation: the winning Marsaglia attempt replayed.
+__device__ __forceinline__ double3 exact_axis(uint64_t seed, uint64_t t, int attempt) {
+    if (attempt < 0) return make_double3(0.0, 0.0, 1.0);
+    double v1, v2, s;
+    marsaglia_in_disc(stream_block(seed, t, 3u + (uint32_t)attempt), &v1, &v2, &s);
+    return marsaglia_axis(v1, v2, s);
 }
 
 // Moved range and the unmoved monomers whose pair with a moved one is left
@@ -227,17 +302,16 @@ __device__ __forceinline__ uint64_t move_pair_evals(const SysDesc& d, int type, 
     return 2ull * m * (d.N - m);
 }
 
-// FP64 positions (new64) and working positions (newr) of the moved monomers.
-// Lane 0 builds the centre and rotation (into the slot's geo scratch); every
-// lane then moves its share of the monomers.  Returns false for a degenerate
-// crankshaft axis.
+// Lane 0 builds the move's exact centre and rotation (FP64, bit-reproducible)
+// into the slot's geo scratch: geo[0..8] R, geo[9..11] centre, geo[12] 1 (0 for
+// a degenerate crankshaft axis).  axis64 is the exact axis of a pivot or
+// rotation.
 template <int TPW, typename PT>
-__device__ bool make_new_positions(const SysDesc& d, const double* x64, const Proposal& P, const MoveSet& M,
-                                   Slot<PT>& s, const Group<TPW>& g) {
-    const int m = M.hi - M.lo + 1;
+__device__ bool prepare_exact(const SysDesc& d, const double* x64, const Proposal& P, double3 axis64, Slot<PT>& s,
+                              const Group<TPW>& g) {
     const int c = P.chain, o = d.chain_off[c], n = d.chain_off[c + 1] - o;
     if (P.type != PHAST_TRANS && g.lane == 0) {
-        double3 axis = P.axis, center;
+        double3 axis = axis64, center;
         double ok = 1.0;
         if (P.type == PHAST_PIVOT) {
             center = ld3(x64 + 3 * (o + P.index));
@@ -269,37 +343,167 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
         s.geo[12] = ok;
     }
     g.sync();
-    if (P.type != PHAST_TRANS && s.geo[12] == 0.0) return false;
+    return P.type == PHAST_TRANS || s.geo[12] != 0.0;
+}
+
+// Exact FP64 position of a moved monomer after the move (the geometry every
+// implementation of the method reproduces bit for bit).
+__device__ __forceinline__ double3 exact_position(const Proposal& P, const double* geo, double3 x) {
+    if (P.type == PHAST_TRANS)
+        return make_double3(xadd(x.x, P.disp.x), xadd(x.y, P.disp.y), xadd(x.z, P.disp.z));
     Rot3 R;
-    double3 center = make_double3(0.0, 0.0, 0.0);
-    if (P.type != PHAST_TRANS) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) R.m[k] = s.geo[k];
-        center = make_double3(s.geo[9], s.geo[10], s.geo[11]);
+    for (int k = 0; k < 9; ++k) R.m[k] = geo[k];
+    return rotate_about(R, make_double3(geo[9], geo[10], geo[11]), x);
+}
+
+// sin and cos of |a| <= 1 in FP32 (Taylor to a^13 / a^12), for trial moves.
+__device__ __forceinline__ void sincos32(float a, float* s, float* c) {
+    const float x2 = a * a;
+    float ps = fmaf(x2, 1.6059043836821614e-10f, -2.5052108385441720e-8f);
+    ps = fmaf(x2, ps, 2.7557319223985893e-6f);
+    ps = fmaf(x2, ps, -1.9841269841269841e-4f);
+    ps = fmaf(x2, ps, 8.3333333333333333e-3f);
+    ps = fmaf(x2, ps, -1.6666666666666667e-1f);
+    *s = fmaf(a * x2, ps, a);
+    float pc = fmaf(x2, 2.0876756987868099e-9f, -2.7557319223985893e-7f);
+    pc = fmaf(x2, pc, 2.4801587301587302e-5f);
+    pc = fmaf(x2, pc, -1.3888888888888889e-3f);
+    pc = fmaf(x2, pc, 4.1666666666666667e-2f);
+    pc = fmaf(x2, pc, -0.5f);
+    *c = fmaf(x2, pc, 1.0f);
+}
+
+// Trial positions of the moved monomers in the working precision (newr).
+// FP64 mode: the exact FP64 positions (also kept in new64).  FP32 mode: the
+// FP32 relative coordinates moved by an FP32 rotation or translation built
+// from FP32 data only; the exact FP64 move is made only when it is accepted
+// (commit_move).  Returns false for a degenerate crankshaft axis.  *fast tells
+// whether every moved monomer lies within one box length of its chain origin
+// (before and after), the condition of the short minimum image.
+template <int TPW, typename PT>
+__device__ bool make_new_positions(const SysDesc& d, const double* x64, const Proposal& P, const MoveSet& M,
+                                   Slot<PT>& s, const Group<TPW>& g, bool* fast) {
+    *fast = false;
+    const int m = M.hi - M.lo + 1;
+    const int c = P.chain, o = d.chain_off[c], n = d.chain_off[c + 1] - o;
+    if constexpr (sizeof(PT) == 8) {
+        if (!prepare_exact<TPW, PT>(d, x64, P, P.axis, s, g)) return false;
+        for (int q = g.lane; q < m; q += TPW) {
+            const int j = M.lo + q;
+            const double3 y = exact_position(P, s.geo, ld3(x64 + 3 * j));
+            s.new64[3 * q + 0] = y.x;
+            s.new64[3 * q + 1] = y.y;
+            s.new64[3 * q + 2] = y.z;
+            P4<PT> w;
+            w.x = y.x;
+            w.y = y.y;
+            w.z = y.z;
+            w.tag = (int)d.seq[j] | (c << 1);
+            s.newr[q] = w;
+        }
+        g.sync();
+        return true;
+    } else {
+        float big = 0.0f;
+        float4* mv = reinterpret_cast<float4*>(s.newr);
+        if (P.type == PHAST_TRANS) {
+            const float dx = (float)P.disp.x, dy = (float)P.disp.y, dz = (float)P.disp.z;
+            for (int q = g.lane; q < m; q += TPW) {
+                const P4<PT> w = s.r[M.lo + q];
+                const float nx = w.x + dx, ny = w.y + dy, nz = w.z + dz;
+                big = fmaxf(big, fmaxf(fmaxf(fabsf(w.x), fmaxf(fabsf(w.y), fabsf(w.z))),
+                                       fmaxf(fabsf(nx), fmaxf(fabsf(ny), fabsf(nz)))));
+                mv[2 * q] = make_float4(w.x, nx, w.y, ny);
+                mv[2 * q + 1] = make_float4(w.z, nz, __int_as_float(w.tag), 0.0f);
+            }
+        } else {
+            float kx = (float)P.axis.x, ky = (float)P.axis.y, kz = (float)P.axis.z, cx, cy, cz;
+            if (P.type == PHAST_PIVOT) {
+                const P4<PT> p = s.r[o + P.index];
+                cx = p.x; cy = p.y; cz = p.z;
+            } else if (P.type == PHAST_ROT) {
+                cx = cy = cz = 0.0f;
+                for (int j = o + g.lane; j < o + n; j += TPW) {
+                    const P4<PT> p = s.r[j];
+                    cx += p.x; cy += p.y; cz += p.z;
+                }
+#pragma unroll
+                for (int w = TPW / 2; w > 0; w >>= 1) {
+                    cx += __shfl_xor_sync(g.mask, cx, w, TPW);
+                    cy += __shfl_xor_sync(g.mask, cy, w, TPW);
+                    cz += __shfl_xor_sync(g.mask, cz, w, TPW);
+                }
+                const float inv = 1.0f / (float)n;
+                cx *= inv; cy *= inv; cz *= inv;
+            } else {
+                const P4<PT> a = s.r[o + P.index - 1], b = s.r[o + P.index + 1];
+                const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
+                const float len = sqrtf(ex * ex + ey * ey + ez * ez);
+                if (!(len > 1e-12f)) return false;
+                kx = ex / len; ky = ey / len; kz = ez / len;
+                cx = a.x; cy = a.y; cz = a.z;
+            }
+            float sn, cs;
+            sincos32((float)P.angle, &sn, &cs);
+            const float tt = 1.0f - cs;
+            const float r0 = tt * kx * kx + cs, r1 = tt * kx * ky - sn * kz, r2 = tt * kx * kz + sn * ky;
+            const float r3 = tt * ky * kx + sn * kz, r4 = tt * ky * ky + cs, r5 = tt * ky * kz - sn * kx;
+            const float r6 = tt * kz * kx - sn * ky, r7 = tt * kz * ky + sn * kx, r8 = tt * kz * kz + cs;
+            for (int q = g.lane; q < m; q += TPW) {
+                const P4<PT> w = s.r[M.lo + q];
+                const float vx = w.x - cx, vy = w.y - cy, vz = w.z - cz;
+                const float nx = cx + (r0 * vx + r1 * vy + r2 * vz);
+                const float ny = cy + (r3 * vx + r4 * vy + r5 * vz);
+                const float nz = cz + (r6 * vx + r7 * vy + r8 * vz);
+                big = fmaxf(big, fmaxf(fmaxf(fabsf(w.x), fmaxf(fabsf(w.y), fabsf(w.z))),
+                                       fmaxf(fabsf(nx), fmaxf(fabsf(ny), fabsf(nz)))));
+                mv[2 * q] = make_float4(w.x, nx, w.y, ny);
+                mv[2 * q + 1] = make_float4(w.z, nz, __int_as_float(w.tag), 0.0f);
+            }
+        }
+#pragma unroll
+        for (int w = TPW / 2; w > 0; w >>= 1) big = fmaxf(big, __shfl_xor_sync(g.mask, big, w, TPW));
+        *fast = d.box_L == 0.0 || big < d.L32;
+        g.sync();
+        return true;
     }
-    const bool rel = sizeof(PT) == 4;
-    const double ox = rel ? s.orig[3 * c + 0] : 0.0, oy = rel ? s.orig[3 * c + 1] : 0.0,
-                 oz = rel ? s.orig[3 * c + 2] : 0.0;
-    for (int q = g.lane; q < m; q += TPW) {
-        const int j = M.lo + q;
-        const double3 x = ld3(x64 + 3 * j);
-        double3 y;
-        if (P.type == PHAST_TRANS)
-            y = make_double3(xadd(x.x, P.disp.x), xadd(x.y, P.disp.y), xadd(x.z, P.disp.z));
-        else
-            y = rotate_about(R, center, x);
-        s.new64[3 * q + 0] = y.x;
-        s.new64[3 * q + 1] = y.y;
-        s.new64[3 * q + 2] = y.z;
-        P4<PT> w;
-        w.x = (PT)(y.x - ox);
-        w.y = (PT)(y.y - oy);
-        w.z = (PT)(y.z - oz);
-        w.tag = (int)d.seq[j] | (c << 1);
-        s.newr[q] = w;
+}
+
+// Commit an accepted move: FP64 master coordinates and working copy.  In FP32
+// mode the exact FP64 geometry is built here (axis64: the exact axis).
+template <int TPW, typename PT>
+__device__ void commit_move(const SysDesc& d, double* x64, const Proposal& P, double3 axis64, const MoveSet& M,
+                            Slot<PT>& s, const Group<TPW>& g) {
+    const int m = M.hi - M.lo + 1;
+    if constexpr (sizeof(PT) == 8) {
+        for (int q = g.lane; q < m; q += TPW) {
+            const int j = M.lo + q;
+            x64[3 * j + 0] = s.new64[3 * q + 0];
+            x64[3 * j + 1] = s.new64[3 * q + 1];
+            x64[3 * j + 2] = s.new64[3 * q + 2];
+            s.r[j] = s.newr[q];
+        }
+    } else {
+        prepare_exact<TPW, PT>(d, x64, P, axis64, s, g);
+        const int c = P.chain;
+        const double ox = s.orig[3 * c + 0], oy = s.orig[3 * c + 1], oz = s.orig[3 * c + 2];
+        for (int q = g.lane; q < m; q += TPW) {
+            const int j = M.lo + q;
+            const double3 y = exact_position(P, s.geo, ld3(x64 + 3 * j));
+            x64[3 * j + 0] = y.x;
+            x64[3 * j + 1] = y.y;
+            x64[3 * j + 2] = y.z;
+            if (P.type != PHAST_TRANS) {   // a translated chain keeps its relative coordinates; its origin moves
+                P4<PT> w = s.r[j];
+                w.x = (PT)(y.x - ox);
+                w.y = (PT)(y.y - oy);
+                w.z = (PT)(y.z - oz);
+                s.r[j] = w;
+            }
+        }
+        if (P.type == PHAST_TRANS) rebase_translated<TPW, PT>(d, c, P.disp, s, g);
     }
-    g.sync();
-    return true;
 }
 
 // Bending and torsion terms from working positions (any precision; positions
@@ -335,7 +539,7 @@ __device__ __forceinline__ PT torsion_w(const Pos& pos, int o, int j) {
 
 // This lane's share of the bending/torsion change, in the working precision.
 template <int TPW, typename PT>
-__device__ double local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M, const Slot<PT>& s,
+__device__ PT local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M, const Slot<PT>& s,
                               const Group<TPW>& g) {
     int vb0, nb, jt0, nt;
     local_window(d, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt);
@@ -346,14 +550,25 @@ __device__ double local_delta(const SysDesc& d, const Proposal& P, const MoveSet
         const bool after = it & 1;
         const int k = it >> 1;
         auto pos = [&](int j) -> P4<PT> {
-            if (after && j >= M.lo && j <= M.hi) return s.newr[j - M.lo];
+            if (after && j >= M.lo && j <= M.hi) {
+                if constexpr (sizeof(PT) == 4) {
+                    const float4* mv = reinterpret_cast<const float4*>(s.newr) + 2 * (j - M.lo);
+                    const float4 a = mv[0], b = mv[1];
+                    P4<PT> w;
+                    w.x = a.y; w.y = a.w; w.z = b.y; w.tag = __float_as_int(b.z);
+                    return w;
+                } else {
+                    return s.newr[j - M.lo];
+                }
+            }
             return s.r[j];
         };
-        const PT term = (k < nb) ? (PT)d.k_bend * bend_w<PT>(pos, o, vb0 + k)
-                                 : -(PT)d.k_tors * torsion_w<PT>(pos, o, jt0 + (k - nb));
+        const FF<PT> f{d};
+        const PT term = (k < nb) ? f.kbend() * bend_w<PT>(pos, o, vb0 + k)
+                                 : -f.ktors() * torsion_w<PT>(pos, o, jt0 + (k - nb));
         part += after ? term : -term;
     }
-    return (double)part;
+    return part;
 }
 
 __device__ __forceinline__ float fast_rcp(float x) {
@@ -386,64 +601,214 @@ __device__ __forceinline__ PT lj_pair(PT dx, PT dy, PT dz, PT Lj, PT iLj, PT C) 
     return ir6 * (ir6 - C);
 }
 
+// Shortest image distance component for |dx| < 1.5 L: min(|dx|, |L - |dx||)
+// (two FMA-pipe operations).  Lj = 1e30 leaves |dx| unchanged (same chain).
+__device__ __forceinline__ float short_image(float dx, float Lj) {
+    const float a = fabsf(dx);
+    return fminf(a, fabsf(Lj - a));
+}
+
+// FP32 pair loop.  Old and new evaluations of a pair travel together as the
+// two halves of one paired FP32 instruction (add/mul/fma .f32x2), from the
+// interleaved (old, new) records of the moved monomers.  Partners t = lane,
+// lane + TPW, ... (skipping the moved range) are held R at a time in registers;
+// the ragged tail runs one at a time so no register slot idles.  FAST: partners
+// wrapped exactly into [-L/2, L/2) around the moved chain's origin, then the
+// short image min(|d|, |L - |d||) per component (valid because every moved
+// monomer lies within L of that origin, so |d| < 1.5 L); otherwise the
+// nearest-integer image count, rounded on the FMA pipe.
+template <int RR, bool FAST>
+__device__ __forceinline__ float pair_chunk32(const SysDesc& d, const MoveSet& M, int mchain, int m, int t0,
+                                              int stride, const P4<float>* __restrict__ r,
+                                              const P4<float>* __restrict__ D, const float4* __restrict__ mv) {
+    const int nc = d.n_chains;
+    const float L = d.L32, iL = d.iL32;
+    float2 nqx[RR], nqy[RR], nqz[RR], nC0[RR], nC1[RR], acc[RR];
+    float Lj[RR], iLj[RR], kap[RR];
+#pragma unroll
+    for (int u = 0; u < RR; ++u) {
+        const int t = t0 + u * stride;
+        const int j = t < M.lo ? t : t + m;
+        const P4<float> p = r[j];
+        const int cj = p.tag >> 1, tj = p.tag & 1;
+        const bool ex = (j == M.ex0) | (j == M.ex1) | (j == M.ex2);
+        float qx = p.x, qy = p.y, qz = p.z;
+        Lj[u] = FAST ? 1.0e30f : 0.0f;
+        iLj[u] = 0.0f;
+        kap[u] = d.kin32;
+        if (cj != mchain) {
+            const P4<float> sh = D[mchain * nc + cj];
+            qx -= sh.x; qy -= sh.y; qz -= sh.z;
+            if (FAST) {   // exact: q - k L with |q| < 1.5 L loses no bits
+                qx -= L * image_count(qx, iL);
+                qy -= L * image_count(qy, iL);
+                qz -= L * image_count(qz, iL);
+                if (L > 0.0f) Lj[u] = L;
+            } else {
+                Lj[u] = L;
+                iLj[u] = iL;
+            }
+            kap[u] = d.kout32;
+        }
+        if (ex) { qx = qy = qz = 1.0e4f; kap[u] = 0.0f; Lj[u] = FAST ? 1.0e30f : 0.0f; iLj[u] = 0.0f; }
+        nqx[u] = make_float2(-qx, -qx);
+        nqy[u] = make_float2(-qy, -qy);
+        nqz[u] = make_float2(-qz, -qz);
+        nC0[u] = make_float2(-d.C32[tj], -d.C32[tj]);
+        nC1[u] = make_float2(-d.C32[2 + tj], -d.C32[2 + tj]);
+        acc[u] = make_float2(0.0f, 0.0f);
+    }
+#pragma unroll 2
+    for (int i = 0; i < m; ++i) {
+        const float4 A = mv[2 * i], B = mv[2 * i + 1];
+        const bool ib = __float_as_int(B.z) & 1;
+        const float2 x2 = make_float2(A.x, A.y), y2 = make_float2(A.z, A.w), z2 = make_float2(B.x, B.y);
+#pragma unroll
+        for (int u = 0; u < RR; ++u) {
+            float2 dx = __fadd2_rn(x2, nqx[u]), dy = __fadd2_rn(y2, nqy[u]), dz = __fadd2_rn(z2, nqz[u]);
+            if (FAST) {
+                dx = make_float2(short_image(dx.x, Lj[u]), short_image(dx.y, Lj[u]));
+                dy = make_float2(short_image(dy.x, Lj[u]), short_image(dy.y, Lj[u]));
+                dz = make_float2(short_image(dz.x, Lj[u]), short_image(dz.y, Lj[u]));
+            } else {
+                const float2 Ln = make_float2(-Lj[u], -Lj[u]), il = make_float2(iLj[u], iLj[u]);
+                const float2 Mg = make_float2(12582912.0f, 12582912.0f), nMg = make_float2(-12582912.0f, -12582912.0f);
+                dx = __ffma2_rn(Ln, __fadd2_rn(__ffma2_rn(dx, il, Mg), nMg), dx);
+                dy = __ffma2_rn(Ln, __fadd2_rn(__ffma2_rn(dy, il, Mg), nMg), dy);
+                dz = __ffma2_rn(Ln, __fadd2_rn(__ffma2_rn(dz, il, Mg), nMg), dz);
+            }
+            float2 r2 = __fmul2_rn(dx, dx);
+            r2 = __ffma2_rn(dy, dy, r2);
+            r2 = __ffma2_rn(dz, dz, r2);
+            const float2 ir = make_float2(fast_rcp(r2.x), fast_rcp(r2.y));
+            const float2 i6 = __fmul2_rn(__fmul2_rn(ir, ir), ir);
+            acc[u] = __ffma2_rn(i6, __fadd2_rn(i6, ib ? nC1[u] : nC0[u]), acc[u]);
+        }
+    }
+    float part = 0.0f;
+#pragma unroll
+    for (int u = 0; u < RR; ++u) part += kap[u] * (acc[u].y - acc[u].x);
+    return part;
+}
+
+template <int TPW, int R, bool FAST>
+__device__ float pair_delta32(const SysDesc& d, const MoveSet& M, int mchain, const Slot<float>& s,
+                              const Group<TPW>& g) {
+    const int m = M.hi - M.lo + 1;
+    const int U = d.N - m;
+    const float4* mv = reinterpret_cast<const float4*>(s.newr);
+    const int full = U / (TPW * R) * (TPW * R);
+    float part = 0.0f;
+    int t0 = g.lane;
+    for (; t0 < full; t0 += TPW * R) part += pair_chunk32<R, FAST>(d, M, mchain, m, t0, TPW, s.r, s.D, mv);
+    for (; t0 < U; t0 += TPW) part += pair_chunk32<1, FAST>(d, M, mchain, m, t0, TPW, s.r, s.D, mv);
+    return part;
+}
+
 // This lane's share of the Lennard-Jones change: unmoved partners t = lane,
 // lane + TPW, ... (skipping the moved range), R of them in registers at a
 // time, each swept against every moved monomer before and after the move.
-template <int TPW, typename PT, int R>
-__device__ double pair_delta(const SysDesc& d, const MoveSet& M, int mchain, const Slot<PT>& s,
+// FAST (FP32 only): partners are wrapped exactly into [-L/2, L/2) around the
+// moved chain's origin once, and the per-pair minimum image reduces to the
+// short form above -- valid because every moved monomer lies within L of that
+// origin (checked per move), so |dx| < 1.5 L.  Otherwise each pair takes the
+// nearest-integer image count.
+template <int TPW, typename PT, int R, bool FAST>
+__device__ PT pair_delta(const SysDesc& d, const MoveSet& M, int mchain, const Slot<PT>& s,
                              const Group<TPW>& g) {
     const int m = M.hi - M.lo + 1;
     const int U = d.N - m;
     const int nc = d.n_chains;
-    const PT L = (PT)d.box_L, iL = (PT)d.inv_L;
-    const PT kin = (PT)d.k_lj_intra, kout = (PT)d.k_lj_inter;
+    const FF<PT> f{d};
+    const PT L = f.L(), iL = f.iL();
+    const PT kin = f.kin(), kout = f.kout();
     const PT far = (PT)1.0e4;
+    const PT open = (PT)1.0e30;
     PT part = (PT)0;
     for (int t0 = g.lane; t0 < U; t0 += TPW * R) {
         PT qx[R], qy[R], qz[R], Lj[R], iLj[R], C0[R], C1[R], kap[R], acc[R];
 #pragma unroll
         for (int u = 0; u < R; ++u) {
-            int t = t0 + u * TPW;
+            const int t = t0 + u * TPW;
             qx[u] = qy[u] = qz[u] = far;
-            Lj[u] = iLj[u] = C0[u] = C1[u] = kap[u] = (PT)0;
+            Lj[u] = FAST ? open : (PT)0;
+            iLj[u] = C0[u] = C1[u] = kap[u] = (PT)0;
             acc[u] = (PT)0;
             if (t < U) {
-                int j = t < M.lo ? t : t + m;
-                P4<PT> p = s.r[j];
-                int cj = p.tag >> 1, tj = p.tag & 1;
-                bool same = cj == mchain;
-                bool ex = (j == M.ex0) | (j == M.ex1) | (j == M.ex2);
+                const int j = t < M.lo ? t : t + m;
+                const P4<PT> p = s.r[j];
+                const int cj = p.tag >> 1, tj = p.tag & 1;
+                const bool same = cj == mchain;
+                const bool ex = (j == M.ex0) | (j == M.ex1) | (j == M.ex2);
                 if (!ex) {
                     if (same) {
                         qx[u] = p.x; qy[u] = p.y; qz[u] = p.z;
                         kap[u] = kin;
                     } else {
-                        P4<PT> sh = s.D[mchain * nc + cj];
+                        const P4<PT> sh = s.D[mchain * nc + cj];
                         qx[u] = p.x - sh.x; qy[u] = p.y - sh.y; qz[u] = p.z - sh.z;
-                        Lj[u] = L; iLj[u] = iL;
+                        if (FAST) {   // exact: q - k L with |q| < 1.5 L loses no bits
+                            qx[u] -= L * image_count(qx[u], iL);
+                            qy[u] -= L * image_count(qy[u], iL);
+                            qz[u] -= L * image_count(qz[u], iL);
+                            if (L > (PT)0) Lj[u] = L;
+                        } else {
+                            Lj[u] = L; iLj[u] = iL;
+                        }
                         kap[u] = kout;
                     }
-                    C0[u] = (PT)d.C[tj];
-                    C1[u] = (PT)d.C[2 + tj];
+                    C0[u] = f.C(tj);
+                    C1[u] = f.C(2 + tj);
                 }
             }
         }
+#pragma unroll 2
         for (int i = 0; i < m; ++i) {
             const P4<PT> a = s.r[M.lo + i];
             const P4<PT> b = s.newr[i];
             const bool ib = a.tag & 1;
 #pragma unroll
             for (int u = 0; u < R; ++u) {
-                PT C = ib ? C1[u] : C0[u];
-                PT e0 = lj_pair<PT>(a.x - qx[u], a.y - qy[u], a.z - qz[u], Lj[u], iLj[u], C);
-                PT e1 = lj_pair<PT>(b.x - qx[u], b.y - qy[u], b.z - qz[u], Lj[u], iLj[u], C);
-                acc[u] += e1 - e0;
+                const PT C = ib ? C1[u] : C0[u];
+                if (FAST) {
+                    const float ox = short_image(a.x - qx[u], Lj[u]), oy = short_image(a.y - qy[u], Lj[u]),
+                                oz = short_image(a.z - qz[u], Lj[u]);
+                    const float nx = short_image(b.x - qx[u], Lj[u]), ny = short_image(b.y - qy[u], Lj[u]),
+                                nz = short_image(b.z - qz[u], Lj[u]);
+                    const float io = fast_rcp(ox * ox + oy * oy + oz * oz);
+                    const float in = fast_rcp(nx * nx + ny * ny + nz * nz);
+                    const float o6 = io * io * io, n6 = in * in * in;
+                    acc[u] = fmaf(n6, n6 - C, acc[u]);
+                    acc[u] = fmaf(-o6, o6 - C, acc[u]);
+                } else {
+                    const PT e0 = lj_pair<PT>(a.x - qx[u], a.y - qy[u], a.z - qz[u], Lj[u], iLj[u], C);
+                    const PT e1 = lj_pair<PT>(b.x - qx[u], b.y - qy[u], b.z - qz[u], Lj[u], iLj[u], C);
+                    acc[u] += e1 - e0;
+                }
             }
         }
 #pragma unroll
         for (int u = 0; u < R; ++u) part += kap[u] * acc[u];
     }
-    return (double)part;
+    return part;
+}
+
+// Lane 0's acceptance test for dlnW < 0: u < exp(dlnW), decided exactly as in
+// FP64.  FP32 mode settles it with an FP32 exponential and the top 24 bits of
+// u whenever they are further apart than their error bounds (|u - u24| <=
+// 2^-24; expf within 2 ulp; the FP32 rounding of dlnW adds |dlnW| 2^-24
+// relative), and falls back to FP64 in the rare near-tie.
+template <typename PT>
+__device__ __forceinline__ bool accept_below(double dl, const Proposal& P) {
+    if constexpr (sizeof(PT) == 4) {
+        const float dlf = (float)dl;
+        const float e = expf(dlf);
+        const float u24 = ((float)(P.uz >> 8) + 0.5f) * 5.9604644775390625e-8f;
+        const float rel = 5e-7f + fabsf(dlf) * 1.2e-7f;
+        if (u24 + 6e-8f < e * (1.0f - rel)) return true;
+        if (u24 - 6e-8f > e * (1.0f + rel)) return false;
+    }
+    return u52(P.uz, P.uw) < exp(dl);
 }
 
 // Full FP64 energy (Eq. 2 per chain + inter-chain term of Eq. 3) of the

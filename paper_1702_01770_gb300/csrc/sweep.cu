@@ -123,23 +123,31 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
     const int64_t n_moves = a.n_sweeps * sd.N;
     const uint64_t period = (uint64_t)sd.recompute_every * (uint64_t)sd.N;
 
-    const bool rel = sizeof(PT) == 4;
     build_working<TPW, PT>(sd, x64, slot, g);
     for (int64_t it = 0; it < n_moves; ++it) {
-        const Proposal P = propose_group<TPW>(sd, seed, t, g);
+        const Proposal P = propose_group<TPW, PT>(sd, seed, t, g);
         const MoveSet M = move_set(sd, P.type, P.chain, P.index);
-        const bool ok = make_new_positions<TPW, PT>(sd, x64, P, M, slot, g);
-        double part = 0.0;
-        if (ok) part = local_delta<TPW, PT>(sd, P, M, slot, g) + pair_delta<TPW, PT, 4>(sd, M, P.chain, slot, g);
-        const double dsum = g.sum0(part);
+        bool fast;
+        const bool ok = make_new_positions<TPW, PT>(sd, x64, P, M, slot, g, &fast);
+        PT part = (PT)0;
+        if (ok) {
+            part = local_delta<TPW, PT>(sd, P, M, slot, g);
+            if constexpr (sizeof(PT) == 4) {
+                if (fast) part += pair_delta32<TPW, 4, true>(sd, M, P.chain, slot, g);
+                else part += pair_delta32<TPW, 4, false>(sd, M, P.chain, slot, g);
+            } else {
+                part += pair_delta<TPW, PT, 4, false>(sd, M, P.chain, slot, g);
+            }
+        }
+        const PT dsum = g.sum0(part);
         uint32_t acc = 0;
         if (g.lane == 0) {   // decision, histogram and bookkeeping on one lane
-            const double dE = ok ? dsum : __longlong_as_double(0x7ff8000000000000ll);
+            const double dE = ok ? (double)dsum : __longlong_as_double(0x7ff8000000000000ll);
             const double E_new = E + dE;
             const int b_new = bin_of(sd, E_new);
             if (b_new >= 0) {
                 const double dl = __ldg(lnW + b_new) - __ldg(lnW + bin);
-                acc = (dl >= 0.0) || (P.u_acc < exp(dl));
+                acc = (dl >= 0.0) || accept_below<PT>(dl, P);
             }
             if (acc) { E = E_new; bin = b_new; }
             atomicAdd(hist + bin, 1u);
@@ -158,16 +166,9 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         }
         acc = g.bcast(acc, 0);
         if (acc) {
-            const int m = M.hi - M.lo + 1;
-            const bool keep_r = rel && P.type == PHAST_TRANS;   // the origin moves instead
-            for (int q = g.lane; q < m; q += TPW) {
-                const int j = M.lo + q;
-                x64[3 * j + 0] = slot.new64[3 * q + 0];
-                x64[3 * j + 1] = slot.new64[3 * q + 1];
-                x64[3 * j + 2] = slot.new64[3 * q + 2];
-                if (!keep_r) slot.r[j] = slot.newr[q];
-            }
-            if (keep_r) rebase_translated<TPW, PT>(sd, P.chain, P.disp, slot, g);
+            const double3 axis64 = (sizeof(PT) == 4 && (P.type == PHAST_PIVOT || P.type == PHAST_ROT))
+                                       ? exact_axis(seed, t, P.attempt) : P.axis;
+            commit_move<TPW, PT>(sd, x64, P, axis64, M, slot, g);
         }
         g.sync();
         ++t;
@@ -401,7 +402,7 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
             int acc = 0;
             if (b_new >= 0) {
                 const double dl = lnW[b_new] - lnW[bin];
-                acc = (dl >= 0.0) || (P.u_acc < exp(dl));
+                acc = (dl >= 0.0) || (u52(P.uz, P.uw) < exp(dl));
             }
             s_acc = acc;
             if (acc) { E = E_new; bin = b_new; }

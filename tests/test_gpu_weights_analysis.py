@@ -139,8 +139,10 @@ def test_full_muca_on_trimer_recovers_exact_entropy(phast, orc):
     sel = (mass > 5e-3) & ~np.isnan(S)
     exact = np.log(mass[sel])
     d = S[sel] - exact
-    # S is normalised to max S = 0, so the maximum bin has zero jackknife error;
-    # remove the free additive constant with weights that stay finite there
-    d -= np.average(d, weights=1 / (err[sel] ** 2 + 1e-4))
-    assert np.all(np.abs(d) < 5 * err[sel] + 0.02), np.max(np.abs(d) - 5 * err[sel])
+    # S is normalised to max S = 0, so its maximum bin shows zero jackknife
+    # error although it carries the normalisation's uncertainty: use the typical
+    # error as a floor and remove the free additive constant
+    e = np.maximum(err[sel], np.median(err[sel]))
+    d -= np.average(d, weights=1 / e ** 2)
+    assert np.all(np.abs(d) < 5 * e), np.max(np.abs(d) / e)
     ctx.close()
