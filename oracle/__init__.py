@@ -83,6 +83,8 @@ def lib():
         L.orc_apply_move.restype = C.c_int
         L.orc_delta_energy.argtypes = [P(_Model), P(C.c_double), P(Move), P(C.c_double)]
         L.orc_delta_energy.restype = C.c_double
+        L.orc_delta_scale.argtypes = [P(_Model), P(C.c_double), P(Move)]
+        L.orc_delta_scale.restype = C.c_double
         L.orc_pair_evals.argtypes = [P(_Model), P(Move)]
         L.orc_pair_evals.restype = C.c_int64
         L.orc_bin.argtypes = [P(_Muca), C.c_double]
@@ -205,6 +207,12 @@ def delta_energy(model: Model, xyz, mv: Move):
     m = model.c_struct()
     dE = lib().orc_delta_energy(C.byref(m), _ptr(x, C.c_double), C.byref(mv), _ptr(out, C.c_double))
     return dE, out.reshape(-1, 3)
+
+
+def delta_scale(model: Model, xyz, mv: Move) -> float:
+    x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
+    m = model.c_struct()
+    return float(lib().orc_delta_scale(C.byref(m), _ptr(x, C.c_double), C.byref(mv)))
 
 
 def pair_evals(model: Model, mv: Move) -> int:

@@ -186,10 +186,29 @@ void orc_propose(const orc_model* m, const orc_muca* mu, uint64_t seed, uint64_t
     }
 }
 
+/* Centroid of monomers o..o+n-1 (the rotation centre of a rigid rotation).
+ * Reading: the paper names the centre of mass but not the floating-point order
+ * of its sum; it is fixed here so that every implementation reproduces the
+ * coordinates bit for bit: 32 strided partial sums s_l = sum over j = l, l+32,
+ * l+64, ... (increasing j) of x_{o+j}, combined by halving, s_l += s_{l+w} for
+ * w = 16, 8, 4, 2, 1 and l < w, then s_0 / n. */
+static void orc_centroid(const double* xyz, int o, int n, double center[3]) {
+    for (int d = 0; d < 3; ++d) {
+        double part[32];
+        for (int l = 0; l < 32; ++l) {
+            part[l] = 0.0;
+            for (int j = l; j < n; j += 32) part[l] = part[l] + xyz[3 * (o + j) + d];
+        }
+        for (int w = 16; w >= 1; w /= 2)
+            for (int l = 0; l < w; ++l) part[l] = part[l] + part[l + w];
+        center[d] = part[0] / (double)n;
+    }
+}
+
 /* Apply a move.  Pivot (Sec. 3.2 "pivotings"): rotate the shorter side of the
  * chain about an axis through the pivot monomer k; on a tie the tail j > k.
  * Translation / rotation (Sec. 3.2 "Galilean-group updates"): the whole chain,
- * rotation about its centroid (running sum j = 0..n-1, then divided by n).
+ * rotation about its centroid (see orc_centroid for the order of the sum).
  * Crankshaft: monomer i about the axis through monomers i-1 and i+1. */
 int orc_apply_move(const orc_model* m, const orc_move* mv, const double* xyz, double* xyz_new) {
     int N = orc_total(m);
@@ -211,12 +230,8 @@ int orc_apply_move(const orc_model* m, const orc_move* mv, const double* xyz, do
         for (int d = 0; d < 3; ++d) { center[d] = xyz[3 * (o + k) + d]; axis[d] = mv->axis[d]; }
     } else if (mv->type == ORC_ROT) {
         lo = o; hi = o + n - 1;
-        for (int d = 0; d < 3; ++d) {
-            double sum = 0.0;
-            for (int j = o; j < o + n; ++j) sum = sum + xyz[3 * j + d];
-            center[d] = sum / (double)n;
-            axis[d] = mv->axis[d];
-        }
+        orc_centroid(xyz, o, n, center);
+        for (int d = 0; d < 3; ++d) axis[d] = mv->axis[d];
     } else {   /* crankshaft */
         int i = o + mv->index;
         double e[3];
@@ -387,6 +402,39 @@ double orc_delta_energy(const orc_model* m, const double* xyz, const orc_move* m
     }
     if (!xyz_new) free(xn);
     return dE;
+}
+
+/* Magnitude of the terms a move changes: sum over the changed Lennard-Jones
+ * pairs of |term before| + |term after|, plus the bending and torsion energy of
+ * the moved chain before and after in absolute value.  Not part of the method:
+ * the scale against which a reduced-precision dE is judged. */
+double orc_delta_scale(const orc_model* m, const double* xyz, const orc_move* mv) {
+    int N = orc_total(m);
+    double* xn = (double*)malloc(sizeof(double) * 3 * (size_t)N);
+    double scale = 0.0;
+    if (orc_apply_move(m, mv, xyz, xn) > 0) {
+        int o = orc_chain_offset(m, mv->chain), n = m->chain_len[mv->chain];
+        double eb0, et0, eb1, et1;
+        orc_chain_local(m, xyz, o, n, &eb0, &et0);
+        orc_chain_local(m, xn, o, n, &eb1, &et1);
+        scale = fabs(eb0) + fabs(et0) + fabs(eb1) + fabs(et1);
+        int lo, hi;
+        orc_moved_range(m, mv, &lo, &hi);
+        for (int i = lo; i <= hi; ++i) {
+            int ci = orc_chain_of(m, i);
+            for (int j = 0; j < N; ++j) {
+                if (j >= lo && j <= hi) continue;
+                int cj = orc_chain_of(m, j);
+                if (ci == cj && abs(i - j) < 2) continue;
+                double C = m->C[2 * m->seq[i] + m->seq[j]];
+                double k = ci == cj ? m->k_lj_intra : m->k_lj_inter;
+                scale += fabs(k * orc_lj(orc_dist2(m, &xyz[3 * i], &xyz[3 * j], ci != cj), C));
+                scale += fabs(k * orc_lj(orc_dist2(m, &xn[3 * i], &xn[3 * j], ci != cj), C));
+            }
+        }
+    }
+    free(xn);
+    return scale;
 }
 
 /* Pair evaluations of a move: 2 (before and after) for every Lennard-Jones pair

@@ -86,6 +86,10 @@ int orc_apply_move(const orc_model* m, const orc_move* mv, const double* xyz, do
 /* Energy change of the move by its affected terms only. */
 double orc_delta_energy(const orc_model* m, const double* xyz, const orc_move* mv, double* xyz_new);
 
+/* Magnitude of the terms a move changes (sum of absolute values before and
+ * after): the scale for judging a reduced-precision dE. */
+double orc_delta_scale(const orc_model* m, const double* xyz, const orc_move* mv);
+
 /* Number of pair evaluations a move costs under the pair-evaluation count
  * defined in orc_pair_evals (.c). */
 int64_t orc_pair_evals(const orc_model* m, const orc_move* mv);

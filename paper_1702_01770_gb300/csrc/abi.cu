@@ -108,6 +108,8 @@ int phast_build_desc(const phast_system* sys, const phast_ff* ff, const phast_mu
             if (mp->p[i] > 0.0) d->last_type = i;
         }
         d->pair_precision = mp->pair_precision;
+        for (int i = 0; i < 4; ++i) d->amax32[i] = (float)mp->amax[i];
+        d->iw32 = (float)(1.0 / mp->bin_width);
     }
     return PHAST_OK;
 }

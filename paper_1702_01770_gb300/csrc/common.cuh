@@ -42,7 +42,8 @@ struct SysDesc {
     uint64_t thr[4];      // move-type thresholds: type i if 2n+1 < thr[i] (n the 52-bit uniform), see propose_select
     int32_t last_type, pad2[3];
     float C32[4];         // FP32 copies for the FP32 working precision
-    float L32, iL32, kin32, kout32, kbend32, ktors32, pad3[2];
+    float L32, iL32, kin32, kout32, kbend32, ktors32, iw32, pad3;
+    float amax32[4];
     int32_t chain_off[PHAST_MAX_CHAINS + 1];
     int32_t pad1[3];
     uint8_t seq[PHAST_MAX_MONOMERS];
@@ -168,12 +169,32 @@ __device__ __forceinline__ bool marsaglia_try(uint4 r, double3* axis) {
     return true;
 }
 
+// Centroid of monomers o..o+n-1 in the fixed summation order of the move's
+// specification: 32 strided partial sums s_l over j = l, l+32, ... (increasing
+// j), halved by s_l += s_{l+w} for w = 16, 8, 4, 2, 1, then s_0 / n.  One thread.
+__device__ __forceinline__ double3 centroid_serial(const double* x64, int o, int n) {
+    double c[3];
+    for (int d = 0; d < 3; ++d) {
+        double part[32];
+        for (int l = 0; l < 32; ++l) {
+            part[l] = 0.0;
+            for (int j = l; j < n; j += 32) part[l] = xadd(part[l], x64[3 * (o + j) + d]);
+        }
+        for (int w = 16; w >= 1; w /= 2)
+            for (int l = 0; l < w; ++l) part[l] = xadd(part[l], part[l + w]);
+        c[d] = xdiv(part[0], (double)n);
+    }
+    return make_double3(c[0], c[1], c[2]);
+}
+
 // A proposed move, drawn from the walker stream.
 struct Proposal {
     int type, chain, index;
     int attempt;            // winning Marsaglia attempt (-1: none won, axis (0, 0, 1))
-    double angle;
+    double angle;           // exact amplitude, axis and step (FP64 mode and exact replay)
     double3 axis, disp;
+    float angle32;          // their FP32 images (FP32 trial moves)
+    float3 axis32, disp32;
     uint32_t uz, uw;        // words of the acceptance uniform (block 2 z, w)
 };
 

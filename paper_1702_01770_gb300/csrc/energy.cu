@@ -46,6 +46,9 @@ delta_kernel(const SysDesc d, int B, const double* __restrict__ xyz, const phast
     P.angle = mv.angle; P.uz = P.uw = 0u; P.attempt = -1;
     P.axis = make_double3(mv.axis[0], mv.axis[1], mv.axis[2]);
     P.disp = make_double3(mv.disp[0], mv.disp[1], mv.disp[2]);
+    P.angle32 = (float)P.angle;
+    P.axis32 = make_float3((float)P.axis.x, (float)P.axis.y, (float)P.axis.z);
+    P.disp32 = make_float3((float)P.disp.x, (float)P.disp.y, (float)P.disp.z);
     // a move outside the system (type, chain, interior index, amplitude) is
     // reported as NaN instead of being applied
     bool valid = P.type >= 0 && P.type <= 3 && P.chain >= 0 && P.chain < d.n_chains;
@@ -63,14 +66,14 @@ delta_kernel(const SysDesc d, int B, const double* __restrict__ xyz, const phast
     bool fast = false;
     const bool ok = valid && make_new_positions<32, PT>(d, x64, P, M, s, g, &fast);
     if (ok) {
-        PT part = local_delta<32, PT>(d, P, M, s, g);
+        double part = (double)local_delta<32, PT>(d, P, M, s, g);
         if constexpr (sizeof(PT) == 4) {
-            if (fast) part += pair_delta32<32, 4, true>(d, M, P.chain, s, g);
-            else part += pair_delta32<32, 4, false>(d, M, P.chain, s, g);
+            if (fast) part += pair_delta32<32, 3, true>(d, M, P.chain, s, g);
+            else part += pair_delta32<32, 3, false>(d, M, P.chain, s, g);
         } else {
             part += pair_delta<32, PT, 4, false>(d, M, P.chain, s, g);
         }
-        dE = g.sum((double)part);
+        dE = g.sum(part);
     }
     if (g.lane == 0) dE_out[b] = dE;
     if (xyz_new) {

@@ -52,8 +52,18 @@ struct Group {
 };
 
 // Shared-memory layout of one walker slot.
+// An accepted move waiting for its exact FP64 replay (FP32 mode).
+// Its exact amplitude and step are regenerated from the counter-based stream.
+struct QEntry {
+    int32_t packed;      // type | chain << 2 | index << 8
+    int32_t attempt;     // winning Marsaglia attempt
+    uint64_t t;          // move index (the walker stream's counter)
+};
+static_assert(sizeof(QEntry) == 16, "QEntry layout");
+constexpr int kQueue = 16;   // accepted moves replayed per batch (at most the group's lanes)
+
 struct SlotLayout {
-    int r_off, d_off, newr_off, orig_off, new64_off, geo_off, bytes;
+    int r_off, d_off, newr_off, orig_off, new64_off, geo_off, q_off, bytes;
 };
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 template <typename PT>
@@ -66,6 +76,7 @@ __host__ __device__ inline SlotLayout slot_layout(int N, int nc, int mc) {
     L.orig_off = o;  o = align16(o + 8 * 3 * nc);
     L.new64_off = o; o = align16(o + (sizeof(PT) == 8 ? 8 * 3 * mc : 0));
     L.geo_off = o;   o = align16(o + 8 * 32);
+    L.q_off = o;     o = align16(o + (sizeof(PT) == 4 ? (int)sizeof(QEntry) * kQueue : 0));
     L.bytes = o;
     return L;
 }
@@ -78,10 +89,12 @@ struct Slot {
                     // hold two float4 per moved monomer, old and new interleaved: (xo, xn, yo, yn), (zo, zn, tag, 0)
     double* orig;   // [nc * 3] chain origins (FP32 mode; zero in FP64 mode)
     double* new64;  // [max_chain * 3] FP64 positions of the moved monomers after the move (FP64 mode)
-    double* geo;    // [32] FP64 rotation matrix, centre, flag; from geo + 16: FP32 matrix and centre
+    double* geo;    // [32] FP64 rotation matrix, centre, flag of a move being made exactly
+    QEntry* queue;  // [kQueue] accepted moves not yet replayed in FP64 (FP32 mode)
     __device__ __forceinline__ Slot(unsigned char* p, const SlotLayout& L)
         : r((P4<PT>*)(p + L.r_off)), D((P4<PT>*)(p + L.d_off)), newr((P4<PT>*)(p + L.newr_off)),
-          orig((double*)(p + L.orig_off)), new64((double*)(p + L.new64_off)), geo((double*)(p + L.geo_off)) {}
+          orig((double*)(p + L.orig_off)), new64((double*)(p + L.new64_off)), geo((double*)(p + L.geo_off)),
+          queue((QEntry*)(p + L.q_off)) {}
 };
 
 __device__ __forceinline__ double3 ld3(const double* p) { return make_double3(p[0], p[1], p[2]); }
@@ -206,28 +219,59 @@ __device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, c
     b[0] = blk;
     Proposal P;
     int packed = 0;
-    double amp = 0.0, dy = 0.0, dz = 0.0;
-    if (g.lane == 0) {
-        propose_select(d, b[0], b[1], b[2], &P);
-        packed = P.type | (P.chain << 2) | (P.index << 8);
-        amp = P.type == PHAST_TRANS ? P.disp.x : P.angle;
-        dy = P.disp.y;
-        dz = P.disp.z;
-    }
-    packed = (int)g.bcast((uint32_t)packed, 0);
-    P.type = packed & 3;
-    P.chain = (packed >> 2) & 63;
-    P.index = packed >> 8;
-    P.attempt = -1;
-    amp = g.bcastd(amp, 0);
     P.angle = 0.0;
     P.disp = make_double3(0.0, 0.0, 0.0);
     P.axis = make_double3(0.0, 0.0, 1.0);
-    if (P.type == PHAST_TRANS) {
-        P.disp = make_double3(amp, g.bcastd(dy, 0), g.bcastd(dz, 0));
-    } else {
-        P.angle = amp;
+    P.angle32 = 0.0f;
+    P.disp32 = make_float3(0.0f, 0.0f, 0.0f);
+    P.axis32 = make_float3(0.0f, 0.0f, 1.0f);
+    if constexpr (sizeof(PT) == 8) {
+        double amp = 0.0, dy = 0.0, dz = 0.0;
+        if (g.lane == 0) {
+            propose_select(d, b[0], b[1], b[2], &P);
+            packed = P.type | (P.chain << 2) | (P.index << 8);
+            amp = P.type == PHAST_TRANS ? P.disp.x : P.angle;
+            dy = P.disp.y;
+            dz = P.disp.z;
+        }
+        packed = (int)g.bcast((uint32_t)packed, 0);
+        P.type = packed & 3;
+        P.chain = (packed >> 2) & 63;
+        P.index = packed >> 8;
+        amp = g.bcastd(amp, 0);
+        if (P.type == PHAST_TRANS) P.disp = make_double3(amp, g.bcastd(dy, 0), g.bcastd(dz, 0));
+        else P.angle = amp;
+    } else {   // selection in integers, amplitudes in FP32: no FP64 on the trial path
+        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+        if (g.lane == 0) {
+            const uint64_t v = 2 * u52_bits(b[0].x, b[0].y) + 1;
+            int type = d.last_type;
+#pragma unroll
+            for (int i = 3; i >= 0; --i)
+                if (d.p[i] > 0.0 && v < d.thr[i]) type = i;
+            const int chain = (int)(((uint64_t)b[0].z * (uint64_t)d.n_chains) >> 32);
+            const int n = d.chain_off[chain + 1] - d.chain_off[chain];
+            const int index = (type == PHAST_PIVOT || type == PHAST_CRANK)
+                                  ? 1 + (int)(((uint64_t)b[0].w * (uint64_t)(n - 2)) >> 32) : 0;
+            packed = type | (chain << 2) | (index << 8);
+            const float am = d.amax32[type];
+            a0 = sym_unit32(b[1].x) * am;
+            a1 = sym_unit32(b[1].z) * am;
+            a2 = sym_unit32(b[2].x) * am;
+            P.uz = b[2].z;
+            P.uw = b[2].w;
+        }
+        packed = (int)g.bcast((uint32_t)packed, 0);
+        P.type = packed & 3;
+        P.chain = (packed >> 2) & 63;
+        P.index = packed >> 8;
+        a0 = __shfl_sync(g.mask, a0, 0, TPW);
+        if (P.type == PHAST_TRANS)
+            P.disp32 = make_float3(a0, __shfl_sync(g.mask, a1, 0, TPW), __shfl_sync(g.mask, a2, 0, TPW));
+        else
+            P.angle32 = a0;
     }
+    P.attempt = -1;
     if (P.type == PHAST_PIVOT || P.type == PHAST_ROT) {
         const unsigned gm = TPW == 32 ? 0xffffffffu : ((1u << TPW) - 1u);
         uint4 mine = blk;
@@ -259,11 +303,38 @@ __device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, c
                 ax = __shfl_sync(g.mask, ax, src, TPW);
                 ay = __shfl_sync(g.mask, ay, src, TPW);
                 az = __shfl_sync(g.mask, az, src, TPW);
-                P.axis = make_double3(ax, ay, az);
+                P.axis32 = make_float3(ax, ay, az);
             }
         }
     }
     return P;
+}
+
+// Centroid of monomers o..o+n-1 by the group, in the same summation order as
+// centroid_serial (32 strided partial sums, halved by w = 16 .. 1); every lane
+// receives it.
+template <int TPW>
+__device__ double3 centroid_tree(const double* x64, int o, int n, const Group<TPW>& g) {
+    constexpr int V = 32 / TPW;   // partials l = lane + v TPW held by this lane
+    double c[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double part[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            part[v] = 0.0;
+            for (int j = g.lane + v * TPW; j < n; j += 32) part[v] = xadd(part[v], x64[3 * (o + j) + d]);
+        }
+#pragma unroll
+        for (int w = 16; w >= TPW; w /= 2)
+#pragma unroll
+            for (int v = 0; v < w / TPW; ++v) part[v] = xadd(part[v], part[v + w / TPW]);
+        double sum = part[0];
+#pragma unroll
+        for (int w = (TPW < 32 ? TPW : 32) / 2; w >= 1; w /= 2) sum = xadd(sum, __shfl_down_sync(g.mask, sum, w, TPW));
+        c[d] = g.bcastd(xdiv(sum, (double)n), 0);
+    }
+    return make_double3(c[0], c[1], c[2]);
 }
 
 // Exact FP64 axis of a pivot or rotation: the winning Marsaglia attempt replayed.
@@ -310,19 +381,15 @@ template <int TPW, typename PT>
 __device__ bool prepare_exact(const SysDesc& d, const double* x64, const Proposal& P, double3 axis64, Slot<PT>& s,
                               const Group<TPW>& g) {
     const int c = P.chain, o = d.chain_off[c], n = d.chain_off[c + 1] - o;
+    double3 rot_center = make_double3(0.0, 0.0, 0.0);
+    if (P.type == PHAST_ROT) rot_center = centroid_tree<TPW>(x64, o, n, g);
     if (P.type != PHAST_TRANS && g.lane == 0) {
         double3 axis = axis64, center;
         double ok = 1.0;
         if (P.type == PHAST_PIVOT) {
             center = ld3(x64 + 3 * (o + P.index));
-        } else if (P.type == PHAST_ROT) {   // centroid: running sum j = 0..n-1, then / n
-            double sx = 0.0, sy = 0.0, sz = 0.0;
-            for (int j = o; j < o + n; ++j) {
-                sx = xadd(sx, x64[3 * j + 0]);
-                sy = xadd(sy, x64[3 * j + 1]);
-                sz = xadd(sz, x64[3 * j + 2]);
-            }
-            center = make_double3(xdiv(sx, (double)n), xdiv(sy, (double)n), xdiv(sz, (double)n));
+        } else if (P.type == PHAST_ROT) {
+            center = rot_center;
         } else {   // crankshaft about the axis through monomers i-1 and i+1
             const int i = o + P.index;
             const double3 a = ld3(x64 + 3 * (i - 1)), b = ld3(x64 + 3 * (i + 1));
@@ -408,7 +475,7 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
         float big = 0.0f;
         float4* mv = reinterpret_cast<float4*>(s.newr);
         if (P.type == PHAST_TRANS) {
-            const float dx = (float)P.disp.x, dy = (float)P.disp.y, dz = (float)P.disp.z;
+            const float dx = P.disp32.x, dy = P.disp32.y, dz = P.disp32.z;
             for (int q = g.lane; q < m; q += TPW) {
                 const P4<PT> w = s.r[M.lo + q];
                 const float nx = w.x + dx, ny = w.y + dy, nz = w.z + dz;
@@ -418,7 +485,7 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
                 mv[2 * q + 1] = make_float4(w.z, nz, __int_as_float(w.tag), 0.0f);
             }
         } else {
-            float kx = (float)P.axis.x, ky = (float)P.axis.y, kz = (float)P.axis.z, cx, cy, cz;
+            float kx = P.axis32.x, ky = P.axis32.y, kz = P.axis32.z, cx, cy, cz;
             if (P.type == PHAST_PIVOT) {
                 const P4<PT> p = s.r[o + P.index];
                 cx = p.x; cy = p.y; cz = p.z;
@@ -445,7 +512,7 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
                 cx = a.x; cy = a.y; cz = a.z;
             }
             float sn, cs;
-            sincos32((float)P.angle, &sn, &cs);
+            sincos32(P.angle32, &sn, &cs);
             const float tt = 1.0f - cs;
             const float r0 = tt * kx * kx + cs, r1 = tt * kx * ky - sn * kz, r2 = tt * kx * kz + sn * ky;
             const float r3 = tt * ky * kx + sn * kz, r4 = tt * ky * ky + cs, r5 = tt * ky * kz - sn * kx;
@@ -470,40 +537,129 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
     }
 }
 
-// Commit an accepted move: FP64 master coordinates and working copy.  In FP32
-// mode the exact FP64 geometry is built here (axis64: the exact axis).
-template <int TPW, typename PT>
-__device__ void commit_move(const SysDesc& d, double* x64, const Proposal& P, double3 axis64, const MoveSet& M,
-                            Slot<PT>& s, const Group<TPW>& g) {
+// Commit an accepted move in FP64 mode: the exact positions computed for the
+// trial become the master coordinates and the working copy.
+template <int TPW>
+__device__ void commit_move64(double* x64, const MoveSet& M, Slot<double>& s, const Group<TPW>& g) {
     const int m = M.hi - M.lo + 1;
-    if constexpr (sizeof(PT) == 8) {
-        for (int q = g.lane; q < m; q += TPW) {
-            const int j = M.lo + q;
-            x64[3 * j + 0] = s.new64[3 * q + 0];
-            x64[3 * j + 1] = s.new64[3 * q + 1];
-            x64[3 * j + 2] = s.new64[3 * q + 2];
-            s.r[j] = s.newr[q];
+    for (int q = g.lane; q < m; q += TPW) {
+        const int j = M.lo + q;
+        x64[3 * j + 0] = s.new64[3 * q + 0];
+        x64[3 * j + 1] = s.new64[3 * q + 1];
+        x64[3 * j + 2] = s.new64[3 * q + 2];
+        s.r[j] = s.newr[q];
+    }
+}
+
+// Accept a move in FP32 mode: the working copy takes the trial positions at
+// once (a translated chain keeps them and moves its origin instead), and the
+// move joins the queue whose exact FP64 replay flush_queue makes later.
+template <int TPW>
+__device__ void accept_move32(const SysDesc& d, const Proposal& P, uint64_t t, const MoveSet& M, Slot<float>& s,
+                              const Group<TPW>& g, int count) {
+    if (g.lane == 0) {
+        QEntry e;
+        e.packed = P.type | (P.chain << 2) | (P.index << 8);
+        e.attempt = P.attempt;
+        e.t = t;
+        s.queue[count] = e;
+    }
+    if (P.type == PHAST_TRANS) {   // the origin moves by the FP32 step the trial used
+        rebase_translated<TPW, float>(d, P.chain, make_double3(P.disp32.x, P.disp32.y, P.disp32.z), s, g);
+        return;
+    }
+    const int m = M.hi - M.lo + 1;
+    const float4* mv = reinterpret_cast<const float4*>(s.newr);
+    for (int q = g.lane; q < m; q += TPW) {
+        const float4 A = mv[2 * q], B = mv[2 * q + 1];
+        P4<float> w = s.r[M.lo + q];
+        w.x = A.y;
+        w.y = A.w;
+        w.z = B.y;
+        s.r[M.lo + q] = w;
+    }
+}
+
+// Replay the queued accepted moves exactly, in order, on the FP64 master
+// coordinates.  The state-independent part of each rotation (the winning
+// Marsaglia axis, sin/cos, Rodrigues' matrix) is built for all queued moves at
+// once, one move per lane; centres are read from the coordinates as each move
+// is made.  Then the working copy is refreshed from the exact coordinates.
+template <int TPW>
+__device__ __noinline__ void flush_queue(const SysDesc& d, double* x64, uint64_t seed, Slot<float>& s, const Group<TPW>& g,
+                            int count) {
+    if (count == 0) return;
+    g.sync();
+    Rot3 Rl;
+    double3 dl = make_double3(0.0, 0.0, 0.0);   // exact step (translations) or angle in .x (crankshafts)
+    if (g.lane < count) {   // the exact proposal of queued move `lane`, regenerated from its stream blocks
+        const QEntry e = s.queue[g.lane];
+        Proposal Q;
+        propose_select(d, stream_block(seed, e.t, 0u), stream_block(seed, e.t, 1u), stream_block(seed, e.t, 2u), &Q);
+        if (Q.type == PHAST_PIVOT || Q.type == PHAST_ROT) {
+            const double3 ax = exact_axis(seed, e.t, e.attempt);
+            double sn, cs;
+            taylor_sincos(Q.angle, &sn, &cs);
+            Rl = rodrigues(ax.x, ax.y, ax.z, sn, cs);
+        } else if (Q.type == PHAST_TRANS) {
+            dl = Q.disp;
+        } else {
+            dl.x = Q.angle;
         }
-    } else {
-        prepare_exact<TPW, PT>(d, x64, P, axis64, s, g);
-        const int c = P.chain;
-        const double ox = s.orig[3 * c + 0], oy = s.orig[3 * c + 1], oz = s.orig[3 * c + 2];
-        for (int q = g.lane; q < m; q += TPW) {
-            const int j = M.lo + q;
-            const double3 y = exact_position(P, s.geo, ld3(x64 + 3 * j));
-            x64[3 * j + 0] = y.x;
-            x64[3 * j + 1] = y.y;
-            x64[3 * j + 2] = y.z;
-            if (P.type != PHAST_TRANS) {   // a translated chain keeps its relative coordinates; its origin moves
-                P4<PT> w = s.r[j];
-                w.x = (PT)(y.x - ox);
-                w.y = (PT)(y.y - oy);
-                w.z = (PT)(y.z - oz);
-                s.r[j] = w;
+    }
+    for (int k = 0; k < count; ++k) {
+        const QEntry e = s.queue[k];
+        Proposal P;
+        P.type = e.packed & 3;
+        P.chain = (e.packed >> 2) & 63;
+        P.index = e.packed >> 8;
+        P.attempt = e.attempt;
+        P.angle = 0.0;
+        P.disp = make_double3(0.0, 0.0, 0.0);
+        P.axis = make_double3(0.0, 0.0, 1.0);
+        if (P.type == PHAST_TRANS) P.disp = make_double3(g.bcastd(dl.x, k), g.bcastd(dl.y, k), g.bcastd(dl.z, k));
+        if (P.type == PHAST_CRANK) P.angle = g.bcastd(dl.x, k);
+        const MoveSet M = move_set(d, P.type, P.chain, P.index);
+        const int m = M.hi - M.lo + 1;
+        const int o = d.chain_off[P.chain], n = d.chain_off[P.chain + 1] - o;
+        Rot3 R;
+        double3 center = make_double3(0.0, 0.0, 0.0);
+        bool ok = true;
+        if (P.type == PHAST_PIVOT || P.type == PHAST_ROT) {
+#pragma unroll
+            for (int q = 0; q < 9; ++q) R.m[q] = g.bcastd(Rl.m[q], k);
+            center = (P.type == PHAST_PIVOT) ? ld3(x64 + 3 * (o + P.index)) : centroid_tree<TPW>(x64, o, n, g);
+        } else if (P.type == PHAST_CRANK) {   // its axis depends on the coordinates: built now
+            ok = prepare_exact<TPW, float>(d, x64, P, P.axis, s, g);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) R.m[q] = s.geo[q];
+            center = make_double3(s.geo[9], s.geo[10], s.geo[11]);
+        }
+        if (ok) {
+            for (int q = g.lane; q < m; q += TPW) {
+                const int j = M.lo + q;
+                const double3 x = ld3(x64 + 3 * j);
+                double3 y;
+                if (P.type == PHAST_TRANS)
+                    y = make_double3(xadd(x.x, P.disp.x), xadd(x.y, P.disp.y), xadd(x.z, P.disp.z));
+                else
+                    y = rotate_about(R, center, x);
+                x64[3 * j + 0] = y.x;
+                x64[3 * j + 1] = y.y;
+                x64[3 * j + 2] = y.z;
             }
         }
-        if (P.type == PHAST_TRANS) rebase_translated<TPW, PT>(d, c, P.disp, s, g);
+        g.sync();
     }
+    for (int j = g.lane; j < d.N; j += TPW) {
+        const int c = d.chain_of[j];
+        P4<float> w = s.r[j];
+        w.x = (float)(x64[3 * j + 0] - s.orig[3 * c + 0]);
+        w.y = (float)(x64[3 * j + 1] - s.orig[3 * c + 1]);
+        w.z = (float)(x64[3 * j + 2] - s.orig[3 * c + 2]);
+        s.r[j] = w;
+    }
+    g.sync();
 }
 
 // Bending and torsion terms from working positions (any precision; positions
@@ -658,31 +814,49 @@ __device__ __forceinline__ float pair_chunk32(const SysDesc& d, const MoveSet& M
         nC1[u] = make_float2(-d.C32[2 + tj], -d.C32[2 + tj]);
         acc[u] = make_float2(0.0f, 0.0f);
     }
-#pragma unroll 2
+#pragma unroll 1
     for (int i = 0; i < m; ++i) {
         const float4 A = mv[2 * i], B = mv[2 * i + 1];
         const bool ib = __float_as_int(B.z) & 1;
         const float2 x2 = make_float2(A.x, A.y), y2 = make_float2(A.z, A.w), z2 = make_float2(B.x, B.y);
+        // stage-major: each stage for all RR partners before the next, so the
+        // independent chains sit next to each other for the scheduler
+        float2 dx[RR], dy[RR], dz[RR], r2[RR];
 #pragma unroll
         for (int u = 0; u < RR; ++u) {
-            float2 dx = __fadd2_rn(x2, nqx[u]), dy = __fadd2_rn(y2, nqy[u]), dz = __fadd2_rn(z2, nqz[u]);
-            if (FAST) {
-                dx = make_float2(short_image(dx.x, Lj[u]), short_image(dx.y, Lj[u]));
-                dy = make_float2(short_image(dy.x, Lj[u]), short_image(dy.y, Lj[u]));
-                dz = make_float2(short_image(dz.x, Lj[u]), short_image(dz.y, Lj[u]));
-            } else {
-                const float2 Ln = make_float2(-Lj[u], -Lj[u]), il = make_float2(iLj[u], iLj[u]);
-                const float2 Mg = make_float2(12582912.0f, 12582912.0f), nMg = make_float2(-12582912.0f, -12582912.0f);
-                dx = __ffma2_rn(Ln, __fadd2_rn(__ffma2_rn(dx, il, Mg), nMg), dx);
-                dy = __ffma2_rn(Ln, __fadd2_rn(__ffma2_rn(dy, il, Mg), nMg), dy);
-                dz = __ffma2_rn(Ln, __fadd2_rn(__ffma2_rn(dz, il, Mg), nMg), dz);
+            dx[u] = __fadd2_rn(x2, nqx[u]);
+            dy[u] = __fadd2_rn(y2, nqy[u]);
+            dz[u] = __fadd2_rn(z2, nqz[u]);
+        }
+        if (FAST) {
+#pragma unroll
+            for (int u = 0; u < RR; ++u) {
+                dx[u] = make_float2(short_image(dx[u].x, Lj[u]), short_image(dx[u].y, Lj[u]));
+                dy[u] = make_float2(short_image(dy[u].x, Lj[u]), short_image(dy[u].y, Lj[u]));
+                dz[u] = make_float2(short_image(dz[u].x, Lj[u]), short_image(dz[u].y, Lj[u]));
             }
-            float2 r2 = __fmul2_rn(dx, dx);
-            r2 = __ffma2_rn(dy, dy, r2);
-            r2 = __ffma2_rn(dz, dz, r2);
-            const float2 ir = make_float2(fast_rcp(r2.x), fast_rcp(r2.y));
-            const float2 i6 = __fmul2_rn(__fmul2_rn(ir, ir), ir);
-            acc[u] = __ffma2_rn(i6, __fadd2_rn(i6, ib ? nC1[u] : nC0[u]), acc[u]);
+        } else {
+            const float2 Mg = make_float2(12582912.0f, 12582912.0f), nMg = make_float2(-12582912.0f, -12582912.0f);
+#pragma unroll
+            for (int u = 0; u < RR; ++u) {
+                const float2 Ln = make_float2(-Lj[u], -Lj[u]), il = make_float2(iLj[u], iLj[u]);
+                dx[u] = __ffma2_rn(Ln, __fadd2_rn(__ffma2_rn(dx[u], il, Mg), nMg), dx[u]);
+                dy[u] = __ffma2_rn(Ln, __fadd2_rn(__ffma2_rn(dy[u], il, Mg), nMg), dy[u]);
+                dz[u] = __ffma2_rn(Ln, __fadd2_rn(__ffma2_rn(dz[u], il, Mg), nMg), dz[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < RR; ++u) r2[u] = __fmul2_rn(dx[u], dx[u]);
+#pragma unroll
+        for (int u = 0; u < RR; ++u) r2[u] = __ffma2_rn(dy[u], dy[u], r2[u]);
+#pragma unroll
+        for (int u = 0; u < RR; ++u) r2[u] = __ffma2_rn(dz[u], dz[u], r2[u]);
+#pragma unroll
+        for (int u = 0; u < RR; ++u) r2[u] = make_float2(fast_rcp(r2[u].x), fast_rcp(r2[u].y));
+#pragma unroll
+        for (int u = 0; u < RR; ++u) {
+            const float2 i6 = __fmul2_rn(__fmul2_rn(r2[u], r2[u]), r2[u]);
+            acc[u] = __ffma2_rn(i6, __fadd2_rn(i6, ib ? nC1[u] : nC0[u]), acc[u]);   // (old, new) sums
         }
     }
     float part = 0.0f;
@@ -691,18 +865,26 @@ __device__ __forceinline__ float pair_chunk32(const SysDesc& d, const MoveSet& M
     return part;
 }
 
+// This lane's share, summed over its partner chunks with compensation and
+// returned in FP64 (the group reduces it in FP64).
 template <int TPW, int R, bool FAST>
-__device__ float pair_delta32(const SysDesc& d, const MoveSet& M, int mchain, const Slot<float>& s,
-                              const Group<TPW>& g) {
+__device__ double pair_delta32(const SysDesc& d, const MoveSet& M, int mchain, const Slot<float>& s,
+                               const Group<TPW>& g) {
     const int m = M.hi - M.lo + 1;
     const int U = d.N - m;
     const float4* mv = reinterpret_cast<const float4*>(s.newr);
     const int full = U / (TPW * R) * (TPW * R);
-    float part = 0.0f;
+    float hi = 0.0f, lo = 0.0f;
+    auto add = [&](float v) {
+        const float y = v - lo;
+        const float tt = hi + y;
+        lo = (tt - hi) - y;
+        hi = tt;
+    };
     int t0 = g.lane;
-    for (; t0 < full; t0 += TPW * R) part += pair_chunk32<R, FAST>(d, M, mchain, m, t0, TPW, s.r, s.D, mv);
-    for (; t0 < U; t0 += TPW) part += pair_chunk32<1, FAST>(d, M, mchain, m, t0, TPW, s.r, s.D, mv);
-    return part;
+    for (; t0 < full; t0 += TPW * R) add(pair_chunk32<R, FAST>(d, M, mchain, m, t0, TPW, s.r, s.D, mv));
+    for (; t0 < U; t0 += TPW) add(pair_chunk32<1, FAST>(d, M, mchain, m, t0, TPW, s.r, s.D, mv));
+    return (double)hi - (double)lo;
 }
 
 // This lane's share of the Lennard-Jones change: unmoved partners t = lane,
@@ -791,6 +973,23 @@ __device__ PT pair_delta(const SysDesc& d, const MoveSet& M, int mchain, const S
         for (int u = 0; u < R; ++u) part += kap[u] * acc[u];
     }
     return part;
+}
+
+// Bin of E.  FP32 mode: the FP32 estimate of (E - e_min) / w decides unless it
+// lies within its error bound (3e-7 relative) of a bin edge; there, and in
+// FP64 mode, the FP64 division decides -- so the bin always equals bin_of's.
+template <typename PT>
+__device__ __forceinline__ int bin_fast(const SysDesc& d, double E) {
+    if constexpr (sizeof(PT) == 4) {
+        const float q = (float)(E - d.e_min);
+        if (!isfinite(q)) return -1;
+        const float x = q * d.iw32;
+        const float fl = floorf(x);
+        const float fr = x - fl;
+        const float mg = 3e-7f * (fabsf(x) + 1.0f);
+        if (fr > mg && fr < 1.0f - mg) return (fl < 0.0f || fl >= (float)d.n_bins) ? -1 : (int)fl;
+    }
+    return bin_of(d, E);
 }
 
 // Lane 0's acceptance test for dlnW < 0: u < exp(dlnW), decided exactly as in

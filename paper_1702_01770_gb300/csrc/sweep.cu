@@ -124,29 +124,32 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
     const uint64_t period = (uint64_t)sd.recompute_every * (uint64_t)sd.N;
 
     build_working<TPW, PT>(sd, x64, slot, g);
+    int queued = 0;                                         // accepted moves awaiting their FP64 replay
+    const int qcap = TPW < kQueue ? TPW : kQueue;
     for (int64_t it = 0; it < n_moves; ++it) {
+        const double lnw_here = (g.lane == 0) ? __ldg(lnW + bin) : 0.0;   // issued early, used at the decision
         const Proposal P = propose_group<TPW, PT>(sd, seed, t, g);
         const MoveSet M = move_set(sd, P.type, P.chain, P.index);
         bool fast;
         const bool ok = make_new_positions<TPW, PT>(sd, x64, P, M, slot, g, &fast);
-        PT part = (PT)0;
+        double part = 0.0;   // this lane's share of dE, reduced over the group in FP64
         if (ok) {
-            part = local_delta<TPW, PT>(sd, P, M, slot, g);
+            part = (double)local_delta<TPW, PT>(sd, P, M, slot, g);
             if constexpr (sizeof(PT) == 4) {
-                if (fast) part += pair_delta32<TPW, 4, true>(sd, M, P.chain, slot, g);
-                else part += pair_delta32<TPW, 4, false>(sd, M, P.chain, slot, g);
+                if (fast) part += pair_delta32<TPW, 3, true>(sd, M, P.chain, slot, g);
+                else part += pair_delta32<TPW, 3, false>(sd, M, P.chain, slot, g);
             } else {
                 part += pair_delta<TPW, PT, 4, false>(sd, M, P.chain, slot, g);
             }
         }
-        const PT dsum = g.sum0(part);
+        const double dsum = g.sum0(part);
         uint32_t acc = 0;
         if (g.lane == 0) {   // decision, histogram and bookkeeping on one lane
-            const double dE = ok ? (double)dsum : __longlong_as_double(0x7ff8000000000000ll);
+            const double dE = ok ? dsum : __longlong_as_double(0x7ff8000000000000ll);
             const double E_new = E + dE;
-            const int b_new = bin_of(sd, E_new);
+            const int b_new = bin_fast<PT>(sd, E_new);
             if (b_new >= 0) {
-                const double dl = __ldg(lnW + b_new) - __ldg(lnW + bin);
+                const double dl = __ldg(lnW + b_new) - lnw_here;
                 acc = (dl >= 0.0) || accept_below<PT>(dl, P);
             }
             if (acc) { E = E_new; bin = b_new; }
@@ -166,13 +169,23 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         }
         acc = g.bcast(acc, 0);
         if (acc) {
-            const double3 axis64 = (sizeof(PT) == 4 && (P.type == PHAST_PIVOT || P.type == PHAST_ROT))
-                                       ? exact_axis(seed, t, P.attempt) : P.axis;
-            commit_move<TPW, PT>(sd, x64, P, axis64, M, slot, g);
+            if constexpr (sizeof(PT) == 4) {
+                accept_move32<TPW>(sd, P, t, M, slot, g, queued);
+                if (++queued == qcap) {
+                    flush_queue<TPW>(sd, x64, seed, slot, g, queued);
+                    queued = 0;
+                }
+            } else {
+                commit_move64<TPW>(x64, M, slot, g);
+            }
         }
         g.sync();
         ++t;
         if (period && (t % period) == 0) {   // FP64 full energy kills the drift of the running sum
+            if constexpr (sizeof(PT) == 4) {
+                flush_queue<TPW>(sd, x64, seed, slot, g, queued);
+                queued = 0;
+            }
             const double Ef = full_energy64<TPW>(sd, x64, g);
             if (g.lane == 0) {
                 drift_max = fmax(drift_max, fabs(E - Ef));
@@ -184,6 +197,7 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
             build_working<TPW, PT>(sd, x64, slot, g);
         }
     }
+    if constexpr (sizeof(PT) == 4) flush_queue<TPW>(sd, x64, seed, slot, g, queued);
     if (g.lane == 0) {
         a.E[gw] = E;
         a.bin[gw] = bin;
@@ -317,11 +331,7 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
             if (P.type == PHAST_PIVOT) {
                 center = ld3(x64 + 3 * (o + P.index));
             } else if (P.type == PHAST_ROT) {
-                double sx = 0.0, sy = 0.0, sz = 0.0;
-                for (int j = o; j < o + n; ++j) {
-                    sx = xadd(sx, x64[3 * j]); sy = xadd(sy, x64[3 * j + 1]); sz = xadd(sz, x64[3 * j + 2]);
-                }
-                center = make_double3(xdiv(sx, (double)n), xdiv(sy, (double)n), xdiv(sz, (double)n));
+                center = centroid_serial(x64, o, n);
             } else if (P.type == PHAST_CRANK) {
                 const int i = o + P.index;
                 double3 p0 = ld3(x64 + 3 * (i - 1)), p1 = ld3(x64 + 3 * (i + 1));

@@ -45,3 +45,32 @@ def all_move_types(s: inputs.System) -> inputs.System:
     import dataclasses
     p = (0.4, 0.2, 0.2, 0.2) if len(s.chain_len) > 1 else (0.7, 0.0, 0.0, 0.3)
     return dataclasses.replace(s, p=p)
+
+
+def fp32_dE_tolerance(dE_ref: float, scale: float) -> float:
+    """Tolerance of an FP32-pair dE against the FP64 oracle: 1e-4 relative with
+    a floor of one energy unit, plus 2e-5 of the magnitude of the terms the move
+    changes (FP32 coordinates carry ~1e-7 relative rounding, which a
+    Lennard-Jones term near contact amplifies ~12/r times)."""
+    return 1e-4 * max(1.0, abs(dE_ref)) + 2e-5 * scale
+
+
+def check_fp32_trace_dE(orc, s, lnW, seed, dE_gpu, rec, force, label=""):
+    """Every finite dE of a replayed FP32 trace within fp32_dE_tolerance; the
+    scale is computed (by a prefix replay) only for moves over the 1e-4 floor."""
+    m, mu = oracle_model(orc, s), oracle_muca(orc, s)
+    ok = np.isfinite(rec["dE"])
+    assert np.array_equal(ok, np.isfinite(dE_gpu)), label
+    err = np.where(ok, np.abs(dE_gpu - rec["dE"]), 0.0)
+    base = 1e-4 * np.maximum(1.0, np.abs(np.where(ok, rec["dE"], 0.0)))
+    worst = 0.0
+    for k in np.nonzero(err > base)[0]:
+        wk = orc.new_walker(m, mu, s.xyz0, int(seed))
+        if k > 0:
+            orc.sweep_walker(m, mu, lnW, wk, int(k), force=force[:k])
+        mv, _ = orc.propose(m, mu, int(seed), int(k))
+        A = orc.delta_scale(m, wk.xyz, mv)
+        tol = fp32_dE_tolerance(rec["dE"][k], A)
+        worst = max(worst, err[k] / tol)
+        assert err[k] <= tol, (label, int(k), float(dE_gpu[k]), float(rec["dE"][k]), A)
+    return worst

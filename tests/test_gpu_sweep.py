@@ -6,8 +6,9 @@
   sweeps), and the walkers' coordinates agree bit for bit.
 * FP32 pairs (batched form): lockstep replay -- the oracle re-runs each traced
   walker imposing the GPU's decisions and recomputes every dE in FP64; every
-  dE agrees within 1e-4 relative (floor 1 energy unit) and the few decisions
-  the oracle would have taken differently are near-ties at a bin edge.
+  dE agrees within 1e-4 relative (floor 1 energy unit) plus 2e-5 of the
+  magnitude of the changed terms, and the few decisions the oracle would have
+  taken differently are near-ties at a bin edge.
 * Bookkeeping: jackknife-block histograms, pair-evaluation counts, resume,
   checkpoint / restore, tile invariance, error paths.
 """
@@ -18,7 +19,7 @@ import pytest
 import torch
 
 from paper_1702_01770_gb300 import inputs
-from helpers import all_move_types, oracle_model, oracle_muca, paper_cross_seeding
+from helpers import all_move_types, check_fp32_trace_dE, oracle_model, oracle_muca, paper_cross_seeding
 
 pytestmark = pytest.mark.gpu
 
@@ -153,11 +154,8 @@ def test_fp32_lockstep_with_oracle(phast, orc, name):
     total_mis = 0
     worst = 0.0
     for w, (wk, h, stats, rec) in enumerate(res):
-        ok = np.isfinite(rec["dE"])
-        assert np.array_equal(ok, np.isfinite(tr[w]["dE"]))
-        err = np.abs(tr[w]["dE"][ok] - rec["dE"][ok]) / np.maximum(1.0, np.abs(rec["dE"][ok]))
-        worst = max(worst, float(err.max()))
-        assert err.max() <= 1e-4, (w, err.max())
+        worst = max(worst, check_fp32_trace_dE(orc, s, lnW, s.seeds()[w], tr[w]["dE"], rec, force[w],
+                                               label=f"walker {w}"))
         E_prev = np.concatenate([[orc.energy(m, s.xyz0)], rec["E_after"][:-1]])
         b_prev = np.concatenate([[orc.bin_of(mu, E_prev[0])], rec["bin_after"][:-1]])
         mis = 0

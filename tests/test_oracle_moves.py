@@ -221,3 +221,18 @@ def test_proposal_is_deterministic(orc):
     assert bytes(a[0]) == bytes(b[0]) and a[1] == b[1]
     c = orc.propose(m, mu, 43, 1000)
     assert bytes(a[0]) != bytes(c[0])
+
+
+def test_delta_scale_trimer_closed_form(orc):
+    """The changed-term magnitude of a trimer pivot: |pair (0,2)| before and
+    after plus |bend| before and after, by hand."""
+    s = inputs.trimer("AAA")
+    m = _model(orc, s)
+    x = np.array([[-1.0, 0.0, 0.0], [0.0, 0.0, 0.0], [1.0, 0.0, 0.0]])   # straight
+    a = 0.7
+    mv = orc.make_move(orc.PIVOT, 0, 1, axis=(0.0, 0.0, 1.0), angle=a)
+    r2_new = (1.0 + np.cos(a)) ** 2 + np.sin(a) ** 2
+    lj = lambda r2: 4.0 * (r2 ** -6 - r2 ** -3)
+    bend_new = 0.25 * (1.0 - np.cos(a))
+    expect = abs(lj(4.0)) + abs(lj(r2_new)) + 0.0 + bend_new
+    assert orc.delta_scale(m, x, mv) == pytest.approx(expect, rel=1e-12)
