@@ -47,6 +47,8 @@ int phast_build_desc(const phast_system* sys, const phast_ff* ff, const phast_mu
         if (n > maxc) maxc = n;
     }
     d->chain_off[sys->n_chains] = N;
+    d->n_a_before[0] = 0;
+    for (int j = 0; j < N; ++j) d->n_a_before[j + 1] = (uint16_t)(d->n_a_before[j] + (d->seq[j] == 0));
     d->n_chains = sys->n_chains;
     d->N = N;
     d->max_chain = maxc;
@@ -102,10 +104,11 @@ int phast_build_desc(const phast_system* sys, const phast_ff* ff, const phast_mu
         // integer move-type thresholds: u < cum_i  <=>  2n + 1 < ceil(cum_i 2^53) for u = (n + 1/2) 2^-52
         double cum = 0.0;
         d->last_type = 0;
+        d->type_mask = 0;
         for (int i = 0; i < 4; ++i) {
             cum = cum + mp->p[i];
             d->thr[i] = (uint64_t)ceil(cum * 9007199254740992.0);
-            if (mp->p[i] > 0.0) d->last_type = i;
+            if (mp->p[i] > 0.0) { d->last_type = i; d->type_mask |= 1 << i; }
         }
         d->pair_precision = mp->pair_precision;
         for (int i = 0; i < 4; ++i) d->amax32[i] = (float)mp->amax[i];

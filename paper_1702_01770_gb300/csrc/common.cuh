@@ -40,7 +40,7 @@ struct SysDesc {
     double e_min, bin_width;
     double p[4], amax[4];
     uint64_t thr[4];      // move-type thresholds: type i if 2n+1 < thr[i] (n the 52-bit uniform), see propose_select
-    int32_t last_type, pad2[3];
+    int32_t last_type, type_mask, pad2[2];   // type_mask: bit i set when p[i] > 0
     float C32[4];         // FP32 copies for the FP32 working precision
     float L32, iL32, kin32, kout32, kbend32, ktors32, iw32, pad3;
     float amax32[4];
@@ -48,6 +48,7 @@ struct SysDesc {
     int32_t pad1[3];
     uint8_t seq[PHAST_MAX_MONOMERS];
     uint8_t chain_of[PHAST_MAX_MONOMERS];
+    uint16_t n_a_before[PHAST_MAX_MONOMERS + 8];   // number of A monomers with index < j
 };
 static_assert(sizeof(SysDesc) % 16 == 0, "SysDesc must be 16-byte sized for vector copies");
 
@@ -210,7 +211,7 @@ __device__ __forceinline__ void propose_select(const SysDesc& d, uint4 b0, uint4
     int type = d.last_type;
 #pragma unroll
     for (int i = 3; i >= 0; --i)
-        if (d.p[i] > 0.0 && v < d.thr[i]) type = i;
+        if (((d.type_mask >> i) & 1) && v < d.thr[i]) type = i;
     P->uz = b2.z;
     P->uw = b2.w;
     P->attempt = -1;

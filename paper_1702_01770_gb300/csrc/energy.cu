@@ -63,15 +63,15 @@ delta_kernel(const SysDesc d, int B, const double* __restrict__ xyz, const phast
     if (!valid) P.type = PHAST_TRANS, P.chain = 0, P.index = 0;
     const MoveSet M = move_set(d, P.type, P.chain, P.index);
     double dE = __longlong_as_double(0x7ff8000000000000ll);   // NaN for a degenerate or invalid move
-    bool fast = false;
-    const bool ok = valid && make_new_positions<32, PT>(d, x64, P, M, s, g, &fast);
+    const bool ok = valid && make_new_positions<32, PT>(d, x64, P, M, s, g);
     if (ok) {
         double part = (double)local_delta<32, PT>(d, P, M, s, g);
         if constexpr (sizeof(PT) == 4) {
-            if (fast) part += pair_delta32<32, 3, true>(d, M, P.chain, s, g);
-            else part += pair_delta32<32, 3, false>(d, M, P.chain, s, g);
+            const DF q = d.box_L > 0.0 ? pair_delta32<32, 3, true>(d, M, P.chain, s, g)
+                                       : pair_delta32<32, 3, false>(d, M, P.chain, s, g);
+            part += (double)q.hi + (double)q.lo;
         } else {
-            part += pair_delta<32, PT, 4, false>(d, M, P.chain, s, g);
+            part += pair_delta<32, PT, 4>(d, M, P.chain, s, g);
         }
         dE = g.sum(part);
     }

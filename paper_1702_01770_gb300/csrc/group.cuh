@@ -51,6 +51,27 @@ struct Group {
     }
 };
 
+// Double-float value hi + lo carried in two FP32 numbers; additions keep each
+// rounding error (Knuth's TwoSum), so a sum of FP32 terms loses nothing but
+// the final rounding of lo.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    return DF{s, e + (a.lo + b.lo)};
+}
+// Tree sum of the group's DF values; every lane receives lane 0's total.
+template <int TPW>
+__device__ __forceinline__ DF group_sum_df(DF v, const Group<TPW>& g) {
+#pragma unroll
+    for (int o = TPW / 2; o > 0; o >>= 1)
+        v = df_add(v, DF{__shfl_down_sync(g.mask, v.hi, o, TPW), __shfl_down_sync(g.mask, v.lo, o, TPW)});
+    return DF{__shfl_sync(g.mask, v.hi, 0, TPW), __shfl_sync(g.mask, v.lo, 0, TPW)};
+}
+
 // Shared-memory layout of one walker slot.
 // An accepted move waiting for its exact FP64 replay (FP32 mode).
 // Its exact amplitude and step are regenerated from the counter-based stream.
@@ -63,7 +84,7 @@ static_assert(sizeof(QEntry) == 16, "QEntry layout");
 constexpr int kQueue = 16;   // accepted moves replayed per batch (at most the group's lanes)
 
 struct SlotLayout {
-    int r_off, d_off, newr_off, orig_off, new64_off, geo_off, q_off, bytes;
+    int r_off, d_off, newr_off, orig_off, new64_off, geo_off, q_off, st_off, bytes;
 };
 __host__ __device__ inline int align16(int x) { return (x + 15) & ~15; }
 template <typename PT>
@@ -77,6 +98,7 @@ __host__ __device__ inline SlotLayout slot_layout(int N, int nc, int mc) {
     L.new64_off = o; o = align16(o + (sizeof(PT) == 8 ? 8 * 3 * mc : 0));
     L.geo_off = o;   o = align16(o + 8 * 32);
     L.q_off = o;     o = align16(o + (sizeof(PT) == 4 ? (int)sizeof(QEntry) * kQueue : 0));
+    L.st_off = o;    o = align16(o + (int)sizeof(phast_walker_stats));
     L.bytes = o;
     return L;
 }
@@ -86,15 +108,17 @@ struct Slot {
     P4<PT>* r;      // [N] working positions
     P4<PT>* D;      // [nc * nc] origin differences (FP32 mode)
     P4<PT>* newr;   // [max_chain] moved monomers after the move (FP64 mode); in FP32 mode the same bytes
-                    // hold two float4 per moved monomer, old and new interleaved: (xo, xn, yo, yn), (zo, zn, tag, 0)
+                    // hold two float4 per moved monomer, old and new interleaved: (xo, xn, yo, yn), (zo, zn, tag, 0),
+                    // in rec_slot order (A monomers first)
     double* orig;   // [nc * 3] chain origins (FP32 mode; zero in FP64 mode)
     double* new64;  // [max_chain * 3] FP64 positions of the moved monomers after the move (FP64 mode)
     double* geo;    // [32] FP64 rotation matrix, centre, flag of a move being made exactly
     QEntry* queue;  // [kQueue] accepted moves not yet replayed in FP64 (FP32 mode)
+    phast_walker_stats* st;   // this launch's counters of the walker (lane 0 writes them)
     __device__ __forceinline__ Slot(unsigned char* p, const SlotLayout& L)
         : r((P4<PT>*)(p + L.r_off)), D((P4<PT>*)(p + L.d_off)), newr((P4<PT>*)(p + L.newr_off)),
           orig((double*)(p + L.orig_off)), new64((double*)(p + L.new64_off)), geo((double*)(p + L.geo_off)),
-          queue((QEntry*)(p + L.q_off)) {}
+          queue((QEntry*)(p + L.q_off)), st((phast_walker_stats*)(p + L.st_off)) {}
 };
 
 __device__ __forceinline__ double3 ld3(const double* p) { return make_double3(p[0], p[1], p[2]); }
@@ -210,15 +234,9 @@ __device__ __forceinline__ bool disc_test(uint4 r, float* v1f, float* v2f, float
 // winning block).  The acceptance words uz, uw are valid on lane 0 only
 // (u = u52(uz, uw) is formed only when the acceptance test needs it).
 template <int TPW, typename PT>
-__device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, const Group<TPW>& g) {
-    const uint4 blk = stream_block(seed, t, (uint32_t)g.lane);
-    uint4 b[3];
-#pragma unroll
-    for (int i = 1; i < 3; ++i)
-        b[i] = make_uint4(g.bcast(blk.x, i), g.bcast(blk.y, i), g.bcast(blk.z, i), g.bcast(blk.w, i));
-    b[0] = blk;
+__device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, uint4 blk, const Group<TPW>& g) {
+    // blk: this lane's stream block (block index = lane) of move t
     Proposal P;
-    int packed = 0;
     P.angle = 0.0;
     P.disp = make_double3(0.0, 0.0, 0.0);
     P.axis = make_double3(0.0, 0.0, 1.0);
@@ -226,50 +244,31 @@ __device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, c
     P.disp32 = make_float3(0.0f, 0.0f, 0.0f);
     P.axis32 = make_float3(0.0f, 0.0f, 1.0f);
     if constexpr (sizeof(PT) == 8) {
-        double amp = 0.0, dy = 0.0, dz = 0.0;
-        if (g.lane == 0) {
-            propose_select(d, b[0], b[1], b[2], &P);
-            packed = P.type | (P.chain << 2) | (P.index << 8);
-            amp = P.type == PHAST_TRANS ? P.disp.x : P.angle;
-            dy = P.disp.y;
-            dz = P.disp.z;
-        }
-        packed = (int)g.bcast((uint32_t)packed, 0);
-        P.type = packed & 3;
-        P.chain = (packed >> 2) & 63;
-        P.index = packed >> 8;
-        amp = g.bcastd(amp, 0);
-        if (P.type == PHAST_TRANS) P.disp = make_double3(amp, g.bcastd(dy, 0), g.bcastd(dz, 0));
-        else P.angle = amp;
-    } else {   // selection in integers, amplitudes in FP32: no FP64 on the trial path
-        float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
-        if (g.lane == 0) {
-            const uint64_t v = 2 * u52_bits(b[0].x, b[0].y) + 1;
-            int type = d.last_type;
+        uint4 b[3];
 #pragma unroll
-            for (int i = 3; i >= 0; --i)
-                if (d.p[i] > 0.0 && v < d.thr[i]) type = i;
-            const int chain = (int)(((uint64_t)b[0].z * (uint64_t)d.n_chains) >> 32);
-            const int n = d.chain_off[chain + 1] - d.chain_off[chain];
-            const int index = (type == PHAST_PIVOT || type == PHAST_CRANK)
-                                  ? 1 + (int)(((uint64_t)b[0].w * (uint64_t)(n - 2)) >> 32) : 0;
-            packed = type | (chain << 2) | (index << 8);
-            const float am = d.amax32[type];
-            a0 = sym_unit32(b[1].x) * am;
-            a1 = sym_unit32(b[1].z) * am;
-            a2 = sym_unit32(b[2].x) * am;
-            P.uz = b[2].z;
-            P.uw = b[2].w;
-        }
-        packed = (int)g.bcast((uint32_t)packed, 0);
-        P.type = packed & 3;
-        P.chain = (packed >> 2) & 63;
-        P.index = packed >> 8;
-        a0 = __shfl_sync(g.mask, a0, 0, TPW);
-        if (P.type == PHAST_TRANS)
-            P.disp32 = make_float3(a0, __shfl_sync(g.mask, a1, 0, TPW), __shfl_sync(g.mask, a2, 0, TPW));
-        else
-            P.angle32 = a0;
+        for (int i = 0; i < 3; ++i)
+            b[i] = make_uint4(g.bcast(blk.x, i), g.bcast(blk.y, i), g.bcast(blk.z, i), g.bcast(blk.w, i));
+        propose_select(d, b[0], b[1], b[2], &P);
+    } else {   // selection in integers, amplitudes in FP32, on every lane: no FP64 on the trial path
+        const uint32_t w0x = g.bcast(blk.x, 0), w0y = g.bcast(blk.y, 0), w0z = g.bcast(blk.z, 0),
+                       w0w = g.bcast(blk.w, 0), w1x = g.bcast(blk.x, 1), w1z = g.bcast(blk.z, 1),
+                       w2x = g.bcast(blk.x, 2);
+        P.uz = g.bcast(blk.z, 2);
+        P.uw = g.bcast(blk.w, 2);
+        const uint64_t v = 2 * u52_bits(w0x, w0y) + 1;
+        int type = d.last_type;
+#pragma unroll
+        for (int i = 3; i >= 0; --i)
+            if (((d.type_mask >> i) & 1) && v < d.thr[i]) type = i;
+        P.type = type;
+        P.chain = (int)(((uint64_t)w0z * (uint64_t)d.n_chains) >> 32);
+        const int n = d.chain_off[P.chain + 1] - d.chain_off[P.chain];
+        P.index = (type == PHAST_PIVOT || type == PHAST_CRANK) ? 1 + (int)(((uint64_t)w0w * (uint64_t)(n - 2)) >> 32)
+                                                               : 0;
+        const float am = d.amax32[type];
+        const float a0 = sym_unit32(w1x) * am;
+        if (type == PHAST_TRANS) P.disp32 = make_float3(a0, sym_unit32(w1z) * am, sym_unit32(w2x) * am);
+        else P.angle32 = a0;
     }
     P.attempt = -1;
     if (P.type == PHAST_PIVOT || P.type == PHAST_ROT) {
@@ -347,7 +346,9 @@ __device__ __forceinline__ double3 exact_axis(uint64_t seed, uint64_t t, int att
 
 // Moved range and the unmoved monomers whose pair with a moved one is left
 // out (the pivot keeps its distances; a crankshaft's bonded neighbours).
-struct MoveSet { int lo, hi, ex0, ex1, ex2; };
+// Moved range [lo, hi], up to three excluded partners, and the A monomers of
+// the range: a_lo of them before lo in the system, n_a inside it.
+struct MoveSet { int lo, hi, ex0, ex1, ex2, a_lo, n_a; };
 __device__ __forceinline__ MoveSet move_set(const SysDesc& d, int type, int chain, int index) {
     MoveSet M;
     int fixed;
@@ -355,7 +356,17 @@ __device__ __forceinline__ MoveSet move_set(const SysDesc& d, int type, int chai
     M.ex0 = fixed;
     M.ex1 = (type == PHAST_CRANK) ? M.lo - 1 : -1;
     M.ex2 = (type == PHAST_CRANK) ? M.hi + 1 : -1;
+    M.a_lo = d.n_a_before[M.lo];
+    M.n_a = d.n_a_before[M.hi + 1] - M.a_lo;
     return M;
+}
+
+// Record slot of moved monomer j in the FP32 trial records: the A monomers of
+// the moved range first, then the B monomers, each in chain order, so that the
+// pair loop runs over each type with its Lennard-Jones constants fixed.
+__device__ __forceinline__ int rec_slot(const SysDesc& d, const MoveSet& M, int j) {
+    const int a = d.n_a_before[j] - M.a_lo;
+    return d.seq[j] ? M.n_a + (j - M.lo - a) : a;
 }
 
 // Pair evaluations of a move between different chains (2 per pair).
@@ -445,13 +456,10 @@ __device__ __forceinline__ void sincos32(float a, float* s, float* c) {
 // FP64 mode: the exact FP64 positions (also kept in new64).  FP32 mode: the
 // FP32 relative coordinates moved by an FP32 rotation or translation built
 // from FP32 data only; the exact FP64 move is made only when it is accepted
-// (commit_move).  Returns false for a degenerate crankshaft axis.  *fast tells
-// whether every moved monomer lies within one box length of its chain origin
-// (before and after), the condition of the short minimum image.
+// (commit_move).  Returns false for a degenerate crankshaft axis.
 template <int TPW, typename PT>
 __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Proposal& P, const MoveSet& M,
-                                   Slot<PT>& s, const Group<TPW>& g, bool* fast) {
-    *fast = false;
+                                   Slot<PT>& s, const Group<TPW>& g) {
     const int m = M.hi - M.lo + 1;
     const int c = P.chain, o = d.chain_off[c], n = d.chain_off[c + 1] - o;
     if constexpr (sizeof(PT) == 8) {
@@ -472,17 +480,15 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
         g.sync();
         return true;
     } else {
-        float big = 0.0f;
         float4* mv = reinterpret_cast<float4*>(s.newr);
         if (P.type == PHAST_TRANS) {
             const float dx = P.disp32.x, dy = P.disp32.y, dz = P.disp32.z;
             for (int q = g.lane; q < m; q += TPW) {
                 const P4<PT> w = s.r[M.lo + q];
                 const float nx = w.x + dx, ny = w.y + dy, nz = w.z + dz;
-                big = fmaxf(big, fmaxf(fmaxf(fabsf(w.x), fmaxf(fabsf(w.y), fabsf(w.z))),
-                                       fmaxf(fabsf(nx), fmaxf(fabsf(ny), fabsf(nz)))));
-                mv[2 * q] = make_float4(w.x, nx, w.y, ny);
-                mv[2 * q + 1] = make_float4(w.z, nz, __int_as_float(w.tag), 0.0f);
+                const int k = rec_slot(d, M, M.lo + q);
+                mv[2 * k] = make_float4(w.x, nx, w.y, ny);
+                mv[2 * k + 1] = make_float4(w.z, nz, __int_as_float(w.tag), 0.0f);
             }
         } else {
             float kx = P.axis32.x, ky = P.axis32.y, kz = P.axis32.z, cx, cy, cz;
@@ -523,15 +529,11 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
                 const float nx = cx + (r0 * vx + r1 * vy + r2 * vz);
                 const float ny = cy + (r3 * vx + r4 * vy + r5 * vz);
                 const float nz = cz + (r6 * vx + r7 * vy + r8 * vz);
-                big = fmaxf(big, fmaxf(fmaxf(fabsf(w.x), fmaxf(fabsf(w.y), fabsf(w.z))),
-                                       fmaxf(fabsf(nx), fmaxf(fabsf(ny), fabsf(nz)))));
-                mv[2 * q] = make_float4(w.x, nx, w.y, ny);
-                mv[2 * q + 1] = make_float4(w.z, nz, __int_as_float(w.tag), 0.0f);
+                const int k = rec_slot(d, M, M.lo + q);
+                mv[2 * k] = make_float4(w.x, nx, w.y, ny);
+                mv[2 * k + 1] = make_float4(w.z, nz, __int_as_float(w.tag), 0.0f);
             }
         }
-#pragma unroll
-        for (int w = TPW / 2; w > 0; w >>= 1) big = fmaxf(big, __shfl_xor_sync(g.mask, big, w, TPW));
-        *fast = d.box_L == 0.0 || big < d.L32;
         g.sync();
         return true;
     }
@@ -571,7 +573,8 @@ __device__ void accept_move32(const SysDesc& d, const Proposal& P, uint64_t t, c
     const int m = M.hi - M.lo + 1;
     const float4* mv = reinterpret_cast<const float4*>(s.newr);
     for (int q = g.lane; q < m; q += TPW) {
-        const float4 A = mv[2 * q], B = mv[2 * q + 1];
+        const int k = rec_slot(d, M, M.lo + q);
+        const float4 A = mv[2 * k], B = mv[2 * k + 1];
         P4<float> w = s.r[M.lo + q];
         w.x = A.y;
         w.y = A.w;
@@ -584,7 +587,8 @@ __device__ void accept_move32(const SysDesc& d, const Proposal& P, uint64_t t, c
 // coordinates.  The state-independent part of each rotation (the winning
 // Marsaglia axis, sin/cos, Rodrigues' matrix) is built for all queued moves at
 // once, one move per lane; centres are read from the coordinates as each move
-// is made.  Then the working copy is refreshed from the exact coordinates.
+// is made.  Then the working copy of the chains they moved is refreshed from
+// the exact coordinates.
 template <int TPW>
 __device__ __noinline__ void flush_queue(const SysDesc& d, double* x64, uint64_t seed, Slot<float>& s, const Group<TPW>& g,
                             int count) {
@@ -651,8 +655,11 @@ __device__ __noinline__ void flush_queue(const SysDesc& d, double* x64, uint64_t
         }
         g.sync();
     }
+    uint32_t touched = 0;   // only the chains the replayed moves changed
+    for (int k = 0; k < count; ++k) touched |= 1u << ((s.queue[k].packed >> 2) & 63);
     for (int j = g.lane; j < d.N; j += TPW) {
         const int c = d.chain_of[j];
+        if (!((touched >> c) & 1)) continue;
         P4<float> w = s.r[j];
         w.x = (float)(x64[3 * j + 0] - s.orig[3 * c + 0]);
         w.y = (float)(x64[3 * j + 1] - s.orig[3 * c + 1]);
@@ -708,7 +715,7 @@ __device__ PT local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M,
         auto pos = [&](int j) -> P4<PT> {
             if (after && j >= M.lo && j <= M.hi) {
                 if constexpr (sizeof(PT) == 4) {
-                    const float4* mv = reinterpret_cast<const float4*>(s.newr) + 2 * (j - M.lo);
+                    const float4* mv = reinterpret_cast<const float4*>(s.newr) + 2 * rec_slot(d, M, j);
                     const float4 a = mv[0], b = mv[1];
                     P4<PT> w;
                     w.x = a.y; w.y = a.w; w.z = b.y; w.tag = __float_as_int(b.z);
@@ -757,30 +764,25 @@ __device__ __forceinline__ PT lj_pair(PT dx, PT dy, PT dz, PT Lj, PT iLj, PT C) 
     return ir6 * (ir6 - C);
 }
 
-// Shortest image distance component for |dx| < 1.5 L: min(|dx|, |L - |dx||)
-// (two FMA-pipe operations).  Lj = 1e30 leaves |dx| unchanged (same chain).
-__device__ __forceinline__ float short_image(float dx, float Lj) {
-    const float a = fabsf(dx);
-    return fminf(a, fabsf(Lj - a));
-}
-
 // FP32 pair loop.  Old and new evaluations of a pair travel together as the
 // two halves of one paired FP32 instruction (add/mul/fma .f32x2), from the
-// interleaved (old, new) records of the moved monomers.  Partners t = lane,
-// lane + TPW, ... (skipping the moved range) are held R at a time in registers;
-// the ragged tail runs one at a time so no register slot idles.  FAST: partners
-// wrapped exactly into [-L/2, L/2) around the moved chain's origin, then the
-// short image min(|d|, |L - |d||) per component (valid because every moved
-// monomer lies within L of that origin, so |d| < 1.5 L); otherwise the
-// nearest-integer image count, rounded on the FMA pipe.
-template <int RR, bool FAST>
+// interleaved (old, new) records of the moved monomers, A monomers first.
+// Partners t = lane, lane + TPW, ... (skipping the moved range) are held RR at
+// a time in registers; the ragged tail runs one at a time so no register slot
+// idles.  PBC: partners on other chains take the minimum image by the nearest
+// integer count of box lengths, rounded on the FMA pipe by the 1.5 * 2^23
+// constant (three paired instructions per component; the special-function unit
+// keeps only the reciprocal).
+template <int RR, bool PBC>
 __device__ __forceinline__ float pair_chunk32(const SysDesc& d, const MoveSet& M, int mchain, int m, int t0,
                                               int stride, const P4<float>* __restrict__ r,
-                                              const P4<float>* __restrict__ D, const float4* __restrict__ mv) {
+                                              const P4<float>* __restrict__ D, const float4* __restrict__ mv,
+                                              int sub = 0, int step = 1) {
+    // moved monomers i = sub, sub + step, ... of each type segment (step > 1: a
+    // partner shared by `step` lanes in the ragged tail)
     const int nc = d.n_chains;
-    const float L = d.L32, iL = d.iL32;
-    float2 nqx[RR], nqy[RR], nqz[RR], nC0[RR], nC1[RR], acc[RR];
-    float Lj[RR], iLj[RR], kap[RR];
+    float2 nqx[RR], nqy[RR], nqz[RR], nC0[RR], nC1[RR], nL[RR], iL[RR], acc[RR];
+    float kap[RR];
 #pragma unroll
     for (int u = 0; u < RR; ++u) {
         const int t = t0 + u * stride;
@@ -788,116 +790,106 @@ __device__ __forceinline__ float pair_chunk32(const SysDesc& d, const MoveSet& M
         const P4<float> p = r[j];
         const int cj = p.tag >> 1, tj = p.tag & 1;
         const bool ex = (j == M.ex0) | (j == M.ex1) | (j == M.ex2);
-        float qx = p.x, qy = p.y, qz = p.z;
-        Lj[u] = FAST ? 1.0e30f : 0.0f;
-        iLj[u] = 0.0f;
+        float qx = p.x, qy = p.y, qz = p.z, Lj = 0.0f, iLj = 0.0f;
         kap[u] = d.kin32;
-        if (cj != mchain) {
+        if (cj != mchain) {   // into the moved chain's frame
             const P4<float> sh = D[mchain * nc + cj];
             qx -= sh.x; qy -= sh.y; qz -= sh.z;
-            if (FAST) {   // exact: q - k L with |q| < 1.5 L loses no bits
-                qx -= L * image_count(qx, iL);
-                qy -= L * image_count(qy, iL);
-                qz -= L * image_count(qz, iL);
-                if (L > 0.0f) Lj[u] = L;
-            } else {
-                Lj[u] = L;
-                iLj[u] = iL;
-            }
+            Lj = d.L32;
+            iLj = d.iL32;
             kap[u] = d.kout32;
         }
-        if (ex) { qx = qy = qz = 1.0e4f; kap[u] = 0.0f; Lj[u] = FAST ? 1.0e30f : 0.0f; iLj[u] = 0.0f; }
+        if (ex) { qx = qy = qz = 1.0e4f; kap[u] = 0.0f; Lj = iLj = 0.0f; }
         nqx[u] = make_float2(-qx, -qx);
         nqy[u] = make_float2(-qy, -qy);
         nqz[u] = make_float2(-qz, -qz);
+        nL[u] = make_float2(-Lj, -Lj);
+        iL[u] = make_float2(iLj, iLj);
         nC0[u] = make_float2(-d.C32[tj], -d.C32[tj]);
         nC1[u] = make_float2(-d.C32[2 + tj], -d.C32[2 + tj]);
         acc[u] = make_float2(0.0f, 0.0f);
     }
+    const float2 Mg = make_float2(12582912.0f, 12582912.0f), nMg = make_float2(-12582912.0f, -12582912.0f);
+    // records [0, n_a) are A monomers, [n_a, m) B monomers
+    auto sweep = [&](int i0, int i1, const float2* nC) {
 #pragma unroll 1
-    for (int i = 0; i < m; ++i) {
-        const float4 A = mv[2 * i], B = mv[2 * i + 1];
-        const bool ib = __float_as_int(B.z) & 1;
-        const float2 x2 = make_float2(A.x, A.y), y2 = make_float2(A.z, A.w), z2 = make_float2(B.x, B.y);
-        // stage-major: each stage for all RR partners before the next, so the
-        // independent chains sit next to each other for the scheduler
-        float2 dx[RR], dy[RR], dz[RR], r2[RR];
-#pragma unroll
-        for (int u = 0; u < RR; ++u) {
-            dx[u] = __fadd2_rn(x2, nqx[u]);
-            dy[u] = __fadd2_rn(y2, nqy[u]);
-            dz[u] = __fadd2_rn(z2, nqz[u]);
-        }
-        if (FAST) {
+        for (int i = i0 + ((sub - i0) % step + step) % step; i < i1; i += step) {
+            const float4 A = mv[2 * i], B = mv[2 * i + 1];
+            const float2 x2 = make_float2(A.x, A.y), y2 = make_float2(A.z, A.w), z2 = make_float2(B.x, B.y);
+            // stage-major: each stage for all RR partners before the next, so the
+            // independent chains sit next to each other for the scheduler
+            float2 dx[RR], dy[RR], dz[RR], r2[RR];
 #pragma unroll
             for (int u = 0; u < RR; ++u) {
-                dx[u] = make_float2(short_image(dx[u].x, Lj[u]), short_image(dx[u].y, Lj[u]));
-                dy[u] = make_float2(short_image(dy[u].x, Lj[u]), short_image(dy[u].y, Lj[u]));
-                dz[u] = make_float2(short_image(dz[u].x, Lj[u]), short_image(dz[u].y, Lj[u]));
+                dx[u] = __fadd2_rn(x2, nqx[u]);
+                dy[u] = __fadd2_rn(y2, nqy[u]);
+                dz[u] = __fadd2_rn(z2, nqz[u]);
             }
-        } else {
-            const float2 Mg = make_float2(12582912.0f, 12582912.0f), nMg = make_float2(-12582912.0f, -12582912.0f);
+            if (PBC) {
+#pragma unroll
+                for (int u = 0; u < RR; ++u) {
+                    dx[u] = __ffma2_rn(nL[u], __fadd2_rn(__ffma2_rn(dx[u], iL[u], Mg), nMg), dx[u]);
+                    dy[u] = __ffma2_rn(nL[u], __fadd2_rn(__ffma2_rn(dy[u], iL[u], Mg), nMg), dy[u]);
+                    dz[u] = __ffma2_rn(nL[u], __fadd2_rn(__ffma2_rn(dz[u], iL[u], Mg), nMg), dz[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < RR; ++u) r2[u] = __fmul2_rn(dx[u], dx[u]);
+#pragma unroll
+            for (int u = 0; u < RR; ++u) r2[u] = __ffma2_rn(dy[u], dy[u], r2[u]);
+#pragma unroll
+            for (int u = 0; u < RR; ++u) r2[u] = __ffma2_rn(dz[u], dz[u], r2[u]);
+#pragma unroll
+            for (int u = 0; u < RR; ++u) r2[u] = make_float2(fast_rcp(r2[u].x), fast_rcp(r2[u].y));
 #pragma unroll
             for (int u = 0; u < RR; ++u) {
-                const float2 Ln = make_float2(-Lj[u], -Lj[u]), il = make_float2(iLj[u], iLj[u]);
-                dx[u] = __ffma2_rn(Ln, __fadd2_rn(__ffma2_rn(dx[u], il, Mg), nMg), dx[u]);
-                dy[u] = __ffma2_rn(Ln, __fadd2_rn(__ffma2_rn(dy[u], il, Mg), nMg), dy[u]);
-                dz[u] = __ffma2_rn(Ln, __fadd2_rn(__ffma2_rn(dz[u], il, Mg), nMg), dz[u]);
+                const float2 i6 = __fmul2_rn(__fmul2_rn(r2[u], r2[u]), r2[u]);
+                acc[u] = __ffma2_rn(i6, __fadd2_rn(i6, nC[u]), acc[u]);   // (old, new) sums
             }
         }
-#pragma unroll
-        for (int u = 0; u < RR; ++u) r2[u] = __fmul2_rn(dx[u], dx[u]);
-#pragma unroll
-        for (int u = 0; u < RR; ++u) r2[u] = __ffma2_rn(dy[u], dy[u], r2[u]);
-#pragma unroll
-        for (int u = 0; u < RR; ++u) r2[u] = __ffma2_rn(dz[u], dz[u], r2[u]);
-#pragma unroll
-        for (int u = 0; u < RR; ++u) r2[u] = make_float2(fast_rcp(r2[u].x), fast_rcp(r2[u].y));
-#pragma unroll
-        for (int u = 0; u < RR; ++u) {
-            const float2 i6 = __fmul2_rn(__fmul2_rn(r2[u], r2[u]), r2[u]);
-            acc[u] = __ffma2_rn(i6, __fadd2_rn(i6, ib ? nC1[u] : nC0[u]), acc[u]);   // (old, new) sums
-        }
-    }
+    };
+    sweep(0, M.n_a, nC0);
+    sweep(M.n_a, m, nC1);
     float part = 0.0f;
 #pragma unroll
     for (int u = 0; u < RR; ++u) part += kap[u] * (acc[u].y - acc[u].x);
     return part;
 }
 
-// This lane's share, summed over its partner chunks with compensation and
-// returned in FP64 (the group reduces it in FP64).
-template <int TPW, int R, bool FAST>
-__device__ double pair_delta32(const SysDesc& d, const MoveSet& M, int mchain, const Slot<float>& s,
+// This lane's share, summed over its partner chunks in double-float.
+template <int TPW, int R, bool PBC>
+__device__ DF pair_delta32(const SysDesc& d, const MoveSet& M, int mchain, const Slot<float>& s,
                                const Group<TPW>& g) {
     const int m = M.hi - M.lo + 1;
     const int U = d.N - m;
     const float4* mv = reinterpret_cast<const float4*>(s.newr);
-    const int full = U / (TPW * R) * (TPW * R);
-    float hi = 0.0f, lo = 0.0f;
-    auto add = [&](float v) {
-        const float y = v - lo;
-        const float tt = hi + y;
-        lo = (tt - hi) - y;
-        hi = tt;
-    };
+    const int full = U / (TPW * R) * (TPW * R);       // partners in chunks of R per lane
+    const int full1 = U / TPW * TPW;                    // then one per lane
+    DF sum{0.0f, 0.0f};
     int t0 = g.lane;
-    for (; t0 < full; t0 += TPW * R) add(pair_chunk32<R, FAST>(d, M, mchain, m, t0, TPW, s.r, s.D, mv));
-    for (; t0 < U; t0 += TPW) add(pair_chunk32<1, FAST>(d, M, mchain, m, t0, TPW, s.r, s.D, mv));
-    return (double)hi - (double)lo;
+    for (; t0 < full; t0 += TPW * R) sum = df_add(sum, DF{pair_chunk32<R, PBC>(d, M, mchain, m, t0, TPW, s.r, s.D, mv), 0.0f});
+    for (; t0 < full1; t0 += TPW) sum = df_add(sum, DF{pair_chunk32<1, PBC>(d, M, mchain, m, t0, TPW, s.r, s.D, mv), 0.0f});
+    // the last P < TPW partners: each shared by TPW / P' lanes (P' the power of two
+    // >= P), which split its moved monomers between them
+    const int P = U - full1;
+    if (P > 0) {
+        int Pp = 1;
+        while (Pp < P) Pp <<= 1;
+        const int p = g.lane & (Pp - 1), sub = g.lane / Pp;
+        if (p < P)
+            sum = df_add(sum, DF{pair_chunk32<1, PBC>(d, M, mchain, m, full1 + p, TPW, s.r, s.D, mv, sub, TPW / Pp), 0.0f});
+    }
+    return sum;
 }
 
-// This lane's share of the Lennard-Jones change: unmoved partners t = lane,
-// lane + TPW, ... (skipping the moved range), R of them in registers at a
-// time, each swept against every moved monomer before and after the move.
-// FAST (FP32 only): partners are wrapped exactly into [-L/2, L/2) around the
-// moved chain's origin once, and the per-pair minimum image reduces to the
-// short form above -- valid because every moved monomer lies within L of that
-// origin (checked per move), so |dx| < 1.5 L.  Otherwise each pair takes the
-// nearest-integer image count.
-template <int TPW, typename PT, int R, bool FAST>
+// This lane's share of the Lennard-Jones change in the working precision
+// (FP64 mode): unmoved partners t = lane, lane + TPW, ... (skipping the moved
+// range), R of them in registers at a time, each swept against every moved
+// monomer before and after the move, with the nearest-integer minimum image
+// between chains.
+template <int TPW, typename PT, int R>
 __device__ PT pair_delta(const SysDesc& d, const MoveSet& M, int mchain, const Slot<PT>& s,
-                             const Group<TPW>& g) {
+                         const Group<TPW>& g) {
     const int m = M.hi - M.lo + 1;
     const int U = d.N - m;
     const int nc = d.n_chains;
@@ -905,7 +897,6 @@ __device__ PT pair_delta(const SysDesc& d, const MoveSet& M, int mchain, const S
     const PT L = f.L(), iL = f.iL();
     const PT kin = f.kin(), kout = f.kout();
     const PT far = (PT)1.0e4;
-    const PT open = (PT)1.0e30;
     PT part = (PT)0;
     for (int t0 = g.lane; t0 < U; t0 += TPW * R) {
         PT qx[R], qy[R], qz[R], Lj[R], iLj[R], C0[R], C1[R], kap[R], acc[R];
@@ -913,30 +904,21 @@ __device__ PT pair_delta(const SysDesc& d, const MoveSet& M, int mchain, const S
         for (int u = 0; u < R; ++u) {
             const int t = t0 + u * TPW;
             qx[u] = qy[u] = qz[u] = far;
-            Lj[u] = FAST ? open : (PT)0;
-            iLj[u] = C0[u] = C1[u] = kap[u] = (PT)0;
+            Lj[u] = iLj[u] = C0[u] = C1[u] = kap[u] = (PT)0;
             acc[u] = (PT)0;
             if (t < U) {
                 const int j = t < M.lo ? t : t + m;
                 const P4<PT> p = s.r[j];
                 const int cj = p.tag >> 1, tj = p.tag & 1;
-                const bool same = cj == mchain;
                 const bool ex = (j == M.ex0) | (j == M.ex1) | (j == M.ex2);
                 if (!ex) {
-                    if (same) {
+                    if (cj == mchain) {
                         qx[u] = p.x; qy[u] = p.y; qz[u] = p.z;
                         kap[u] = kin;
                     } else {
                         const P4<PT> sh = s.D[mchain * nc + cj];
                         qx[u] = p.x - sh.x; qy[u] = p.y - sh.y; qz[u] = p.z - sh.z;
-                        if (FAST) {   // exact: q - k L with |q| < 1.5 L loses no bits
-                            qx[u] -= L * image_count(qx[u], iL);
-                            qy[u] -= L * image_count(qy[u], iL);
-                            qz[u] -= L * image_count(qz[u], iL);
-                            if (L > (PT)0) Lj[u] = L;
-                        } else {
-                            Lj[u] = L; iLj[u] = iL;
-                        }
+                        Lj[u] = L; iLj[u] = iL;
                         kap[u] = kout;
                     }
                     C0[u] = f.C(tj);
@@ -952,21 +934,9 @@ __device__ PT pair_delta(const SysDesc& d, const MoveSet& M, int mchain, const S
 #pragma unroll
             for (int u = 0; u < R; ++u) {
                 const PT C = ib ? C1[u] : C0[u];
-                if (FAST) {
-                    const float ox = short_image(a.x - qx[u], Lj[u]), oy = short_image(a.y - qy[u], Lj[u]),
-                                oz = short_image(a.z - qz[u], Lj[u]);
-                    const float nx = short_image(b.x - qx[u], Lj[u]), ny = short_image(b.y - qy[u], Lj[u]),
-                                nz = short_image(b.z - qz[u], Lj[u]);
-                    const float io = fast_rcp(ox * ox + oy * oy + oz * oz);
-                    const float in = fast_rcp(nx * nx + ny * ny + nz * nz);
-                    const float o6 = io * io * io, n6 = in * in * in;
-                    acc[u] = fmaf(n6, n6 - C, acc[u]);
-                    acc[u] = fmaf(-o6, o6 - C, acc[u]);
-                } else {
-                    const PT e0 = lj_pair<PT>(a.x - qx[u], a.y - qy[u], a.z - qz[u], Lj[u], iLj[u], C);
-                    const PT e1 = lj_pair<PT>(b.x - qx[u], b.y - qy[u], b.z - qz[u], Lj[u], iLj[u], C);
-                    acc[u] += e1 - e0;
-                }
+                const PT e0 = lj_pair<PT>(a.x - qx[u], a.y - qy[u], a.z - qz[u], Lj[u], iLj[u], C);
+                const PT e1 = lj_pair<PT>(b.x - qx[u], b.y - qy[u], b.z - qz[u], Lj[u], iLj[u], C);
+                acc[u] += e1 - e0;
             }
         }
 #pragma unroll
@@ -975,24 +945,22 @@ __device__ PT pair_delta(const SysDesc& d, const MoveSet& M, int mchain, const S
     return part;
 }
 
-// Bin of E.  FP32 mode: the FP32 estimate of (E - e_min) / w decides unless it
-// lies within its error bound (3e-7 relative) of a bin edge; there, and in
-// FP64 mode, the FP64 division decides -- so the bin always equals bin_of's.
-template <typename PT>
-__device__ __forceinline__ int bin_fast(const SysDesc& d, double E) {
-    if constexpr (sizeof(PT) == 4) {
-        const float q = (float)(E - d.e_min);
-        if (!isfinite(q)) return -1;
-        const float x = q * d.iw32;
-        const float fl = floorf(x);
-        const float fr = x - fl;
-        const float mg = 3e-7f * (fabsf(x) + 1.0f);
-        if (fr > mg && fr < 1.0f - mg) return (fl < 0.0f || fl >= (float)d.n_bins) ? -1 : (int)fl;
-    }
-    return bin_of(d, E);
+// Bin of E + dE, the group's total dE = hi + lo (double-float) given with
+// erel = FP32 image of E - e_min.  The FP32 estimate of (E + dE - e_min) / w
+// decides unless it lies within its error bound of a bin edge: erel carries
+// half an ulp, the two FP32 additions one each, the scaling by 1/w two more,
+// all within 4e-7 (|erel| + |hi| + |lo|) / w.  Near an edge, bin_of decides on
+// the FP64 sum E + (hi + lo) -- so the bin always equals bin_of's.
+__device__ __forceinline__ int bin_after(const SysDesc& d, double E, float erel, DF dE) {
+    const float x = ((erel + dE.hi) + dE.lo) * d.iw32;
+    const float fl = floorf(x);
+    const float fr = x - fl;
+    const float mg = 4e-7f * (fabsf(erel) + fabsf(dE.hi) + fabsf(dE.lo)) * d.iw32 + 1e-6f;
+    if (fr > mg && fr < 1.0f - mg) return (fl < 0.0f || fl >= (float)d.n_bins) ? -1 : (int)fl;
+    return bin_of(d, E + ((double)dE.hi + (double)dE.lo));
 }
 
-// Lane 0's acceptance test for dlnW < 0: u < exp(dlnW), decided exactly as in
+// The acceptance test for dlnW < 0: u < exp(dlnW), decided exactly as in
 // FP64.  FP32 mode settles it with an FP32 exponential and the top 24 bits of
 // u whenever they are further apart than their error bounds (|u - u24| <=
 // 2^-24; expf within 2 ulp; the FP32 rounding of dlnW adds |dlnW| 2^-24

@@ -52,7 +52,7 @@ struct SweepArgs {
     int64_t n_sweeps;
     int order[PHAST_MAX_SYSTEMS];
     int tile_start[PHAST_MAX_SYSTEMS + 1];
-    int tpb[PHAST_MAX_SYSTEMS];          // tiles per jackknife block, by enumeration position
+    int tiles[PHAST_MAX_SYSTEMS];        // tiles of each system, by enumeration position
     int64_t hs_off[PHAST_MAX_SYSTEMS];   // hist_sum offset of each system id
     double* xyz;
     double* E;
@@ -108,7 +108,9 @@ __global__ void init_energy_kernel(const SysDesc* __restrict__ descs, int n_sys,
 // ---------------------------------------------------------------------------
 template <int TPW, typename PT>
 __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int w_local, Slot<PT>& slot,
-                           uint32_t* hist, const Group<TPW>& g) {
+                           uint32_t* hist, unsigned long long* hist_g, const Group<TPW>& g) {
+    // hist: the tile's shared histogram; hist_g (non-null): this walker's jackknife
+    // block differs from the tile's, so its visits go straight to the global sums
     const int gw = sd.walker_off + w_local;
     double* x64 = a.xyz + sd.xyz_off + (int64_t)w_local * sd.N * 3;
     const double* lnW = a.lnW + sd.lnw_off;
@@ -116,8 +118,8 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
     int bin = a.bin[gw];
     uint64_t t = a.t[gw];
     const uint64_t seed = a.seed[gw];
-    uint64_t att[4] = {0, 0, 0, 0}, acc_n[4] = {0, 0, 0, 0}, pev = 0, pevx = 0, nrec = 0;
-    double drift_max = 0.0;
+    phast_walker_stats* ls = slot.st;   // counters of this launch, in shared memory
+    if (g.lane == 0) memset(ls, 0, sizeof(*ls));
     uint32_t* hw = a.hist_walker ? a.hist_walker + sd.hw_off + (int64_t)w_local * sd.n_bins : nullptr;
     const bool tracing = a.trace && s_id == 0 && w_local < a.trace_walkers;
     const int64_t n_moves = a.n_sweeps * sd.N;
@@ -126,48 +128,63 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
     build_working<TPW, PT>(sd, x64, slot, g);
     int queued = 0;                                         // accepted moves awaiting their FP64 replay
     const int qcap = TPW < kQueue ? TPW : kQueue;
+    // Every lane holds the walker's scalar state and takes the same decision
+    // from the same broadcast values; lane 0 alone writes histograms and counters.
+    double lnw_here = __ldg(lnW + bin);
+    float erel = (float)(E - sd.e_min);                     // FP32 image of E - e_min (FP32 mode)
+    uint4 blk = stream_block(seed, t, (uint32_t)g.lane);    // this lane's block of the current move
     for (int64_t it = 0; it < n_moves; ++it) {
-        const double lnw_here = (g.lane == 0) ? __ldg(lnW + bin) : 0.0;   // issued early, used at the decision
-        const Proposal P = propose_group<TPW, PT>(sd, seed, t, g);
+        const Proposal P = propose_group<TPW, PT>(sd, seed, t, blk, g);
         const MoveSet M = move_set(sd, P.type, P.chain, P.index);
-        bool fast;
-        const bool ok = make_new_positions<TPW, PT>(sd, x64, P, M, slot, g, &fast);
-        double part = 0.0;   // this lane's share of dE, reduced over the group in FP64
-        if (ok) {
-            part = (double)local_delta<TPW, PT>(sd, P, M, slot, g);
-            if constexpr (sizeof(PT) == 4) {
-                if (fast) part += pair_delta32<TPW, 3, true>(sd, M, P.chain, slot, g);
-                else part += pair_delta32<TPW, 3, false>(sd, M, P.chain, slot, g);
-            } else {
-                part += pair_delta<TPW, PT, 4, false>(sd, M, P.chain, slot, g);
+        const bool ok = make_new_positions<TPW, PT>(sd, x64, P, M, slot, g);
+        DF dE32{0.0f, 0.0f};
+        double dE64 = 0.0;
+        if constexpr (sizeof(PT) == 4) {   // this lane's share in double-float, the group total on every lane
+            DF part{0.0f, 0.0f};
+            if (ok) {
+                part = sd.box_L > 0.0 ? pair_delta32<TPW, 3, true>(sd, M, P.chain, slot, g)
+                                      : pair_delta32<TPW, 3, false>(sd, M, P.chain, slot, g);
+                part = df_add(part, DF{local_delta<TPW, PT>(sd, P, M, slot, g), 0.0f});
             }
+            dE32 = group_sum_df<TPW>(part, g);
+        } else {
+            double part = 0.0;
+            if (ok) part = local_delta<TPW, PT>(sd, P, M, slot, g) + pair_delta<TPW, PT, 4>(sd, M, P.chain, slot, g);
+            dE64 = g.sum(part);
         }
-        const double dsum = g.sum0(part);
-        uint32_t acc = 0;
-        if (g.lane == 0) {   // decision, histogram and bookkeeping on one lane
-            const double dE = ok ? dsum : __longlong_as_double(0x7ff8000000000000ll);
-            const double E_new = E + dE;
-            const int b_new = bin_fast<PT>(sd, E_new);
-            if (b_new >= 0) {
-                const double dl = __ldg(lnW + b_new) - lnw_here;
-                acc = (dl >= 0.0) || accept_below<PT>(dl, P);
-            }
-            if (acc) { E = E_new; bin = b_new; }
-            atomicAdd(hist + bin, 1u);
+        const bool finite = ok && (sizeof(PT) == 4 ? (isfinite(dE32.hi) && isfinite(dE32.lo)) : isfinite(dE64));
+        int b_new = -1;
+        if (finite) b_new = sizeof(PT) == 4 ? bin_after(sd, E, erel, dE32) : bin_of(sd, E + dE64);
+        const double lnw_new = __ldg(lnW + (b_new >= 0 ? b_new : bin));
+        blk = stream_block(seed, t + 1, (uint32_t)g.lane);   // next move's block, while the load is in flight
+        bool acc = false;
+        if (b_new >= 0) {
+            const double dl = lnw_new - lnw_here;
+            acc = (dl >= 0.0) || accept_below<PT>(dl, P);
+        }
+        if (acc) {
+            E = E + (sizeof(PT) == 4 ? (double)dE32.hi + (double)dE32.lo : dE64);
+            bin = b_new;
+            lnw_here = lnw_new;
+            erel = (float)(E - sd.e_min);
+        }
+        if (g.lane == 0) {   // histogram and bookkeeping on one lane
+            if (hist_g) atomicAdd(hist_g + bin, 1ull);
+            else atomicAdd(hist + bin, 1u);
             if (hw) atomicAdd(hw + bin, 1u);
-            att[P.type]++;
-            acc_n[P.type] += acc;
-            pev += move_pair_evals(sd, P.type, M);
-            pevx += move_pair_evals_inter(sd, P.type, P.chain, M);
+            ls->attempts[P.type]++;
+            ls->accepts[P.type] += acc;
+            ls->pair_evals += move_pair_evals(sd, P.type, M);
+            ls->pair_evals_inter += move_pair_evals_inter(sd, P.type, P.chain, M);
             if (tracing) {
                 phast_trace tr;
-                tr.dE = dE;
+                tr.dE = !ok ? __longlong_as_double(0x7ff8000000000000ll)
+                            : (sizeof(PT) == 4 ? (double)dE32.hi + (double)dE32.lo : dE64);
                 tr.bin_after = bin;
                 tr.accepted = (int32_t)acc;
                 a.trace[(int64_t)w_local * n_moves + it] = tr;
             }
         }
-        acc = g.bcast(acc, 0);
         if (acc) {
             if constexpr (sizeof(PT) == 4) {
                 accept_move32<TPW>(sd, P, t, M, slot, g, queued);
@@ -188,10 +205,15 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
             }
             const double Ef = full_energy64<TPW>(sd, x64, g);
             if (g.lane == 0) {
-                drift_max = fmax(drift_max, fabs(E - Ef));
-                const int bf = bin_of(sd, Ef);
-                if (bf >= 0) { E = Ef; bin = bf; }
-                ++nrec;
+                ls->drift_max = fmax(ls->drift_max, fabs(E - Ef));
+                ls->recomputes++;
+            }
+            const int bf = bin_of(sd, Ef);
+            if (bf >= 0) {
+                E = Ef;
+                bin = bf;
+                lnw_here = __ldg(lnW + bin);
+                erel = (float)(E - sd.e_min);
             }
             g.sync();
             build_working<TPW, PT>(sd, x64, slot, g);
@@ -203,11 +225,11 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         a.bin[gw] = bin;
         a.t[gw] = t;
         phast_walker_stats* st = a.stats + gw;
-        for (int i = 0; i < 4; ++i) { st->attempts[i] += att[i]; st->accepts[i] += acc_n[i]; }
-        st->pair_evals += pev;
-        st->pair_evals_inter += pevx;
-        st->recomputes += nrec;
-        st->drift_max = fmax(st->drift_max, drift_max);
+        for (int i = 0; i < 4; ++i) { st->attempts[i] += ls->attempts[i]; st->accepts[i] += ls->accepts[i]; }
+        st->pair_evals += ls->pair_evals;
+        st->pair_evals_inter += ls->pair_evals_inter;
+        st->recomputes += ls->recomputes;
+        st->drift_max = fmax(st->drift_max, ls->drift_max);
     }
 }
 
@@ -236,13 +258,20 @@ sweep_batched_kernel(const SweepArgs a) {
         copy_desc(&sd, a.descs + s_id);
         __syncthreads();
         for (int k = threadIdx.x; k < sd.n_bins; k += blockDim.x) hist[k] = 0u;
-        const int lt = tile - a.tile_start[pos];
-        const int blk = lt / a.tpb[pos], jt = lt % a.tpb[pos];
+        // tile k of this system: walkers [k W / nt, (k + 1) W / nt), at most wpc of them;
+        // the shared histogram collects the jackknife block of the first one
+        const int k = tile - a.tile_start[pos], nt = a.tiles[pos];
         const int W = sd.n_walkers;
-        const int b_lo = (int)((int64_t)blk * W / a.n_jk), b_hi = (int)((int64_t)(blk + 1) * W / a.n_jk);
-        const int w_local = b_lo + jt * a.wpc + slot_id;
+        const int w_a = (int)((int64_t)k * W / nt), w_b = (int)((int64_t)(k + 1) * W / nt);
+        const int w_local = w_a + slot_id;
+        const int blk = jk_block(w_a, W, a.n_jk);
         __syncthreads();
-        if (w_local < b_hi) run_walker<TPW, PT>(sd, a, s_id, w_local, slot, hist, g);
+        if (w_local < w_b) {
+            const int mine = jk_block(w_local, W, a.n_jk);
+            unsigned long long* hg =
+                (a.hist_sum && mine != blk) ? a.hist_sum + a.hs_off[s_id] + (int64_t)mine * sd.n_bins : nullptr;
+            run_walker<TPW, PT>(sd, a, s_id, w_local, slot, hist, hg, g);
+        }
         __syncthreads();
         if (a.hist_sum) {
             unsigned long long* hs = a.hist_sum + a.hs_off[s_id] + (int64_t)blk * sd.n_bins;
@@ -306,8 +335,9 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
     int bin = a.bin[gw];
     uint64_t t = a.t[gw];
     const uint64_t seed = a.seed[gw];
-    uint64_t att[4] = {0, 0, 0, 0}, acc_n[4] = {0, 0, 0, 0}, pev = 0, pevx = 0, nrec = 0;
-    double drift_max = 0.0;
+    __shared__ phast_walker_stats s_st;   // counters of this launch
+    phast_walker_stats* ls = &s_st;
+    if (threadIdx.x == 0) memset(ls, 0, sizeof(*ls));
     unsigned long long* hs = a.hist_sum
         ? a.hist_sum + a.hs_off[s_id] + (int64_t)jk_block(w_local, sd.n_walkers, a.n_jk) * sd.n_bins : nullptr;
     uint32_t* hw = a.hist_walker ? a.hist_walker + sd.hw_off + (int64_t)w_local * sd.n_bins : nullptr;
@@ -418,10 +448,10 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
             if (acc) { E = E_new; bin = b_new; }
             if (hs) atomicAdd(hs + bin, 1ull);
             if (hw) atomicAdd(hw + bin, 1u);
-            att[P.type]++;
-            acc_n[P.type] += acc;
-            pev += move_pair_evals(sd, P.type, M);
-            pevx += move_pair_evals_inter(sd, P.type, P.chain, M);
+            ls->attempts[P.type]++;
+            ls->accepts[P.type] += acc;
+            ls->pair_evals += move_pair_evals(sd, P.type, M);
+            ls->pair_evals_inter += move_pair_evals_inter(sd, P.type, P.chain, M);
             if (tracing) {
                 phast_trace tr;
                 tr.dE = dE;
@@ -438,10 +468,10 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
         if (period && (t % period) == 0) {
             const double Ef = block_full_energy64(sd, x64, red);
             if (threadIdx.x == 0) {
-                drift_max = fmax(drift_max, fabs(E - Ef));
+                ls->drift_max = fmax(ls->drift_max, fabs(E - Ef));
                 const int bf = bin_of(sd, Ef);
                 if (bf >= 0) { E = Ef; bin = bf; }
-                ++nrec;
+                ls->recomputes++;
             }
         }
     }
@@ -450,11 +480,11 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
         a.bin[gw] = bin;
         a.t[gw] = t;
         phast_walker_stats* st = a.stats + gw;
-        for (int i = 0; i < 4; ++i) { st->attempts[i] += att[i]; st->accepts[i] += acc_n[i]; }
-        st->pair_evals += pev;
-        st->pair_evals_inter += pevx;
-        st->recomputes += nrec;
-        st->drift_max = fmax(st->drift_max, drift_max);
+        for (int i = 0; i < 4; ++i) { st->attempts[i] += ls->attempts[i]; st->accepts[i] += ls->accepts[i]; }
+        st->pair_evals += ls->pair_evals;
+        st->pair_evals_inter += ls->pair_evals_inter;
+        st->recomputes += ls->recomputes;
+        st->drift_max = fmax(st->drift_max, ls->drift_max);
     }
 }
 
@@ -500,18 +530,7 @@ int fill_args(const phast_ctx* c, int64_t n_sweeps, const double* lnW, int n_jk,
     a->n_sweeps = n_sweeps;
     int64_t hs = 0;
     for (int s = 0; s < c->n_sys; ++s) { a->hs_off[s] = hs; hs += (int64_t)n_jk * c->desc[s].n_bins; }
-    int tiles = 0;
-    for (int p = 0; p < c->n_sys; ++p) {
-        const int s = c->order[p];
-        const int W = c->desc[s].n_walkers;
-        const int maxblk = (W + n_jk - 1) / n_jk;
-        a->order[p] = s;
-        a->tile_start[p] = tiles;
-        a->tpb[p] = (maxblk + wpc - 1) / wpc;
-        tiles += a->tpb[p] * n_jk;
-    }
-    a->tile_start[c->n_sys] = tiles;
-    a->n_tiles = tiles;
+    for (int p = 0; p < c->n_sys; ++p) a->order[p] = c->order[p];
     a->xyz = c->xyz;
     a->E = c->E;
     a->bin = c->bin;
@@ -528,6 +547,31 @@ int fill_args(const phast_ctx* c, int64_t n_sweeps, const double* lnW, int n_jk,
     a->scratch_stride = 3 * c->max_chain;
     a->hist_bins = c->max_bins;
     return PHAST_OK;
+}
+
+// Tiles of at most wpc walkers, as many as make whole rounds of the grid: the
+// last system in the order (the cheapest) is cut into smaller tiles so that no
+// CTA idles through the final round while others finish theirs.
+void layout_tiles(const phast_ctx* c, int wpc, int grid, SweepArgs* a) {
+    int nt[PHAST_MAX_SYSTEMS], total = 0;
+    for (int p = 0; p < c->n_sys; ++p) {
+        nt[p] = (c->desc[a->order[p]].n_walkers + wpc - 1) / wpc;
+        total += nt[p];
+    }
+    const int want = (total + grid - 1) / grid * grid;
+    for (int p = c->n_sys - 1; p >= 0 && total < want; --p) {
+        const int add = std::min(want - total, c->desc[a->order[p]].n_walkers - nt[p]);
+        nt[p] += add;
+        total += add;
+    }
+    int start = 0;
+    for (int p = 0; p < c->n_sys; ++p) {
+        a->tile_start[p] = start;
+        a->tiles[p] = nt[p];
+        start += nt[p];
+    }
+    a->tile_start[c->n_sys] = start;
+    a->n_tiles = start;
 }
 
 int launch_batched(phast_ctx* c, const SweepArgs& a0, int tpw, int wpc, bool fp32, cudaStream_t st) {
@@ -551,6 +595,7 @@ int launch_batched(phast_ctx* c, const SweepArgs& a0, int tpw, int wpc, bool fp3
     PHAST_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
     if (per_sm < 1) return phast_set_error(PHAST_EINVAL, "tile of %d x %d does not fit on an SM", tpw, wpc);
     int grid = per_sm * n_sm;
+    layout_tiles(c, wpc, grid, &a);
     if (grid > a.n_tiles) grid = a.n_tiles;
     PHAST_CUDA_TRY(cudaMemsetAsync(c->tile_counter, 0, sizeof(int32_t), st));
     fn<<<grid, threads, sm, st>>>(a);
