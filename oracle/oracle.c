@@ -67,7 +67,9 @@ static double orc_u52(uint32_t a, uint32_t b) {
 /* Move geometry (Sec. 3.2, UPDATE_ENGINE: pivots, Galilean updates; plus the  */
 /* crankshaft).  sin and cos by their Taylor series (|a| <= 1), coefficients   */
 /* (-1)^i/(2i+1)! and (-1)^i/(2i)! as correctly rounded quotients of exact     */
-/* factorials; evaluated by Horner in a^2 with separately rounded operations.  */
+/* factorials; evaluated by Horner in a^2, each step one fused multiply-add    */
+/* (C99 fma: a single rounding).  The paper fixes no evaluation order; this    */
+/* one, written out below, is the one both implementations follow.           */
 /* ------------------------------------------------------------------------- */
 static double orc_factorial(int n) {
     double f = 1.0;
@@ -81,38 +83,39 @@ static void orc_sincos(double a, double* s, double* c) {
     /* sin a = a * sum_{i=0..8} (-1)^i a^{2i}/(2i+1)! */
     for (int i = 8; i >= 0; --i) {
         double coef = (i % 2 ? -1.0 : 1.0) / orc_factorial(2 * i + 1);
-        ps = (i == 8) ? coef : ps * x2 + coef;
+        ps = (i == 8) ? coef : fma(ps, x2, coef);
     }
     /* cos a = sum_{i=0..9} (-1)^i a^{2i}/(2i)! */
     for (int i = 9; i >= 0; --i) {
         double coef = (i % 2 ? -1.0 : 1.0) / orc_factorial(2 * i);
-        pc = (i == 9) ? coef : pc * x2 + coef;
+        pc = (i == 9) ? coef : fma(pc, x2, coef);
     }
     *s = a * ps;
     *c = pc;
 }
 
-/* Rodrigues' rotation matrix about unit axis k by the angle with sine s and cosine c. */
+/* Rodrigues' rotation matrix about unit axis k by the angle with sine s and
+ * cosine c: R = c I + s [k]x + (1 - c) k k^T, entry (i, j) as
+ * fma((1 - c) k_i, k_j, d_ij) with d_ij = c on the diagonal and +-s k_l off it. */
 static void orc_rotation(const double k[3], double s, double c, double R[3][3]) {
     double t = 1.0 - c;
-    R[0][0] = (t * k[0]) * k[0] + c;
-    R[0][1] = (t * k[0]) * k[1] - s * k[2];
-    R[0][2] = (t * k[0]) * k[2] + s * k[1];
-    R[1][0] = (t * k[1]) * k[0] + s * k[2];
-    R[1][1] = (t * k[1]) * k[1] + c;
-    R[1][2] = (t * k[1]) * k[2] - s * k[0];
-    R[2][0] = (t * k[2]) * k[0] - s * k[1];
-    R[2][1] = (t * k[2]) * k[1] + s * k[0];
-    R[2][2] = (t * k[2]) * k[2] + c;
+    double tk[3] = {t * k[0], t * k[1], t * k[2]};
+    double sk[3] = {s * k[0], s * k[1], s * k[2]};
+    R[0][0] = fma(tk[0], k[0], c);
+    R[0][1] = fma(tk[0], k[1], -sk[2]);
+    R[0][2] = fma(tk[0], k[2], sk[1]);
+    R[1][0] = fma(tk[1], k[0], sk[2]);
+    R[1][1] = fma(tk[1], k[1], c);
+    R[1][2] = fma(tk[1], k[2], -sk[0]);
+    R[2][0] = fma(tk[2], k[0], -sk[1]);
+    R[2][1] = fma(tk[2], k[1], sk[0]);
+    R[2][2] = fma(tk[2], k[2], c);
 }
 
-/* x' = p + R (x - p). */
+/* x' = p + R (x - p): v = x - p, then x'_i = fma(R_i2, v_2, fma(R_i1, v_1, fma(R_i0, v_0, p_i))). */
 static void orc_rotate_about(const double R[3][3], const double p[3], const double x[3], double out[3]) {
     double v[3] = {x[0] - p[0], x[1] - p[1], x[2] - p[2]};
-    for (int i = 0; i < 3; ++i) {
-        double w = (R[i][0] * v[0] + R[i][1] * v[1]) + R[i][2] * v[2];
-        out[i] = p[i] + w;
-    }
+    for (int i = 0; i < 3; ++i) out[i] = fma(R[i][2], v[2], fma(R[i][1], v[1], fma(R[i][0], v[0], p[i])));
 }
 
 /* Isotropic unit axis by Marsaglia (1972): (v1, v2) uniform in the unit disc,

@@ -58,14 +58,16 @@ int phast_build_desc(const phast_system* sys, const phast_ff* ff, const phast_mu
 
 // ---------------------------------------------------------------------------
 // Explicitly rounded FP64 arithmetic: the geometry below must round exactly
-// as the specification states (no contraction into FMA), so that coordinates
-// are reproducible bit for bit by any IEEE-754 implementation of it.
+// as the specification states (fused multiply-adds only where written, no
+// other contraction), so that coordinates are reproducible bit for bit by any
+// IEEE-754 implementation of it.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double xadd(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double xsub(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double xdiv(double a, double b) { return __ddiv_rn(a, b); }
 __device__ __forceinline__ double xsqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ double xfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
@@ -115,39 +117,40 @@ __device__ __forceinline__ void taylor_sincos(double a, double* s, double* c) {
     double x2 = xmul(a, a);
     double ps = S[8];
 #pragma unroll
-    for (int i = 7; i >= 0; --i) ps = xadd(xmul(ps, x2), S[i]);
+    for (int i = 7; i >= 0; --i) ps = xfma(ps, x2, S[i]);
     double pc = Cc[9];
 #pragma unroll
-    for (int i = 8; i >= 0; --i) pc = xadd(xmul(pc, x2), Cc[i]);
+    for (int i = 8; i >= 0; --i) pc = xfma(pc, x2, Cc[i]);
     *s = xmul(a, ps);
     *c = pc;
 }
 
-// Rodrigues' matrix about unit axis k, angle with sine s and cosine c.
+// Rodrigues' matrix about unit axis k, angle with sine s and cosine c:
+// entry (i, j) = fma((1 - c) k_i, k_j, d_ij), d_ij = c on the diagonal, +-s k_l off it.
 struct Rot3 { double m[9]; };
 __device__ __forceinline__ Rot3 rodrigues(double kx, double ky, double kz, double s, double c) {
     double t = xsub(1.0, c);
     double tx = xmul(t, kx), ty = xmul(t, ky), tz = xmul(t, kz);
+    double sx = xmul(s, kx), sy = xmul(s, ky), sz = xmul(s, kz);
     Rot3 R;
-    R.m[0] = xadd(xmul(tx, kx), c);
-    R.m[1] = xsub(xmul(tx, ky), xmul(s, kz));
-    R.m[2] = xadd(xmul(tx, kz), xmul(s, ky));
-    R.m[3] = xadd(xmul(ty, kx), xmul(s, kz));
-    R.m[4] = xadd(xmul(ty, ky), c);
-    R.m[5] = xsub(xmul(ty, kz), xmul(s, kx));
-    R.m[6] = xsub(xmul(tz, kx), xmul(s, ky));
-    R.m[7] = xadd(xmul(tz, ky), xmul(s, kx));
-    R.m[8] = xadd(xmul(tz, kz), c);
+    R.m[0] = xfma(tx, kx, c);
+    R.m[1] = xfma(tx, ky, -sz);
+    R.m[2] = xfma(tx, kz, sy);
+    R.m[3] = xfma(ty, kx, sz);
+    R.m[4] = xfma(ty, ky, c);
+    R.m[5] = xfma(ty, kz, -sx);
+    R.m[6] = xfma(tz, kx, -sy);
+    R.m[7] = xfma(tz, ky, sx);
+    R.m[8] = xfma(tz, kz, c);
     return R;
 }
 
-// x' = p + R (x - p), rows summed left to right.
+// x' = p + R (x - p): v = x - p, x'_i = fma(R_i2, v_2, fma(R_i1, v_1, fma(R_i0, v_0, p_i))).
 __device__ __forceinline__ double3 rotate_about(const Rot3& R, double3 p, double3 x) {
     double v0 = xsub(x.x, p.x), v1 = xsub(x.y, p.y), v2 = xsub(x.z, p.z);
-    double w0 = xadd(xadd(xmul(R.m[0], v0), xmul(R.m[1], v1)), xmul(R.m[2], v2));
-    double w1 = xadd(xadd(xmul(R.m[3], v0), xmul(R.m[4], v1)), xmul(R.m[5], v2));
-    double w2 = xadd(xadd(xmul(R.m[6], v0), xmul(R.m[7], v1)), xmul(R.m[8], v2));
-    return make_double3(xadd(p.x, w0), xadd(p.y, w1), xadd(p.z, w2));
+    return make_double3(xfma(R.m[2], v2, xfma(R.m[1], v1, xfma(R.m[0], v0, p.x))),
+                        xfma(R.m[5], v2, xfma(R.m[4], v1, xfma(R.m[3], v0, p.y))),
+                        xfma(R.m[8], v2, xfma(R.m[7], v1, xfma(R.m[6], v0, p.z))));
 }
 
 // One Marsaglia (1972) attempt from block r: (v1, v2) uniform in the square,
