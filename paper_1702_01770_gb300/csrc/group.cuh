@@ -81,7 +81,7 @@ struct QEntry {
     uint64_t t;          // move index (the walker stream's counter)
 };
 static_assert(sizeof(QEntry) == 16, "QEntry layout");
-constexpr int kQueue = 16;   // accepted moves replayed per batch (at most the group's lanes)
+constexpr int kQueue = 32;   // accepted moves replayed per batch (at most the group's lanes)
 
 struct SlotLayout {
     int r_off, d_off, newr_off, orig_off, new64_off, geo_off, q_off, st_off, bytes;
