@@ -211,6 +211,32 @@ int phast_weight_update(int32_t K, double bin_width, const uint64_t* hist, int32
                         double* lnW, double* g_acc, double* beta_out, double* flat_out,
                         void* stream);
 
+/* ---- One multicanonical iteration as a CUDA graph (Sec. 2.2, Fig. 2) --- */
+
+/* Captures on `stream` one iteration of the multicanonical loop of Sec. 2.2
+ * for every system type of ctx: clear hist_sum, n_sweeps sweeps of the
+ * batched form (as phast_muca_sweep with the context's tile), then one step of
+ * Berg's recursion per type on its rows of hist_sum (as phast_weight_update).
+ * Nothing runs at capture time; each phast_graph_launch runs one more
+ * iteration on the same buffers, the walkers' state carried in ctx.
+ *  lnW: dev [sum_s K_s] (type s at its lnw offset, phast_ctx_info), read by the
+ *       sweeps and rewritten by the step; g_acc: dev [sum_s K_s], type s at the
+ *       same offset as its lnW (its last entry unused);
+ *  hist_sum: dev uint64 [sum_s n_jk K_s], jackknife layout of phast_muca_sweep;
+ *  flat_out: dev [n_types][4] or NULL (phast_weight_update's flatness row);
+ *  stream: a created stream (the legacy default stream cannot be captured).
+ * The pointers are baked into the graph: it must not outlive ctx or the
+ * buffers, and must not run concurrently with other sweeps of ctx.  *out is
+ * owned by the caller (phast_graph_destroy).  PHAST_EINVAL for a bad argument,
+ * PHAST_ECUDA if capture or instantiation fails (*out = NULL). */
+typedef struct phast_graph phast_graph;
+int phast_ctx_capture_iteration(phast_ctx* ctx, int64_t n_sweeps, double* lnW, int32_t n_jk,
+                                uint64_t* hist_sum, double* g_acc, double* flat_out,
+                                phast_graph** out, void* stream);
+/* Replays the captured iteration on `stream` (any stream, default included). */
+int phast_graph_launch(phast_graph* graph, void* stream);
+void phast_graph_destroy(phast_graph* graph);
+
 /* ---- microcanonical analysis (Eq. 4-6, Sec. 3.3) ------------------------ */
 
 /* Outputs of phast_micro_analysis (all dev pointers; any may be NULL).

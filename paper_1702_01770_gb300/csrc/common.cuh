@@ -53,6 +53,11 @@ struct SysDesc {
 static_assert(sizeof(SysDesc) % 16 == 0, "SysDesc must be 16-byte sized for vector copies");
 
 // Validates the ABI structs and fills a descriptor (offsets left at 0).
+// Berg step on stream st (weights.cu); set_attr: set the kernel's shared-memory
+// limit first (not allowed while a stream is being captured).
+int phast_launch_berg(int32_t K, double bin_width, const uint64_t* hist, int32_t n_blocks, double* lnW,
+                      double* g_acc, double* beta_out, double* flat_out, cudaStream_t st, bool set_attr);
+
 int phast_build_desc(const phast_system* sys, const phast_ff* ff, const phast_muca_params* mp,
                      SysDesc* d, const char* what);
 

@@ -574,33 +574,54 @@ void layout_tiles(const phast_ctx* c, int wpc, int grid, SweepArgs* a) {
     a->n_tiles = start;
 }
 
-int launch_batched(phast_ctx* c, const SweepArgs& a0, int tpw, int wpc, bool fp32, cudaStream_t st) {
-    SweepArgs a = a0;
-    SlotLayout L;
-    size_t sm = batched_smem(c, fp32, wpc, &L);
-    a.L = L;
-    batched_fn fn = pick_batched(tpw, fp32);
-    if (!fn) return phast_set_error(PHAST_EINVAL, "threads per walker %d not in {4, 8, 16, 32}", tpw);
-    const int threads = tpw * wpc;
-    if (threads < 32 || threads > kMaxTileThreads || threads % 32)
+struct BatchedLaunch {
+    batched_fn fn;
+    int grid, threads;
+    size_t smem;
+    SweepArgs a;
+};
+
+// Host-side part of a batched launch: kernel choice, shared-memory limit,
+// occupancy and tile layout (nothing is queued on a stream).
+int prepare_batched(phast_ctx* c, const SweepArgs& a0, int tpw, int wpc, bool fp32, BatchedLaunch* L) {
+    L->a = a0;
+    SlotLayout SL;
+    L->smem = batched_smem(c, fp32, wpc, &SL);
+    L->a.L = SL;
+    L->fn = pick_batched(tpw, fp32);
+    if (!L->fn) return phast_set_error(PHAST_EINVAL, "threads per walker %d not in {4, 8, 16, 32}", tpw);
+    L->threads = tpw * wpc;
+    if (L->threads < 32 || L->threads > kMaxTileThreads || L->threads % 32)
         return phast_set_error(PHAST_EINVAL, "tile of %d x %d threads is not a whole number of warps <= %d", tpw, wpc,
                                kMaxTileThreads);
     int max_sm = 0;
     PHAST_CUDA_TRY(cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    if (sm + 64 > (size_t)max_sm)
-        return phast_set_error(PHAST_EINVAL, "tile needs %zu bytes of shared memory (> %d)", sm, max_sm);
-    PHAST_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (L->smem + 64 > (size_t)max_sm)
+        return phast_set_error(PHAST_EINVAL, "tile needs %zu bytes of shared memory (> %d)", L->smem, max_sm);
+    PHAST_CUDA_TRY(cudaFuncSetAttribute(L->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem));
     int per_sm = 0, n_sm = 0;
-    PHAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, sm));
+    PHAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L->fn, L->threads, L->smem));
     PHAST_CUDA_TRY(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
     if (per_sm < 1) return phast_set_error(PHAST_EINVAL, "tile of %d x %d does not fit on an SM", tpw, wpc);
-    int grid = per_sm * n_sm;
-    layout_tiles(c, wpc, grid, &a);
-    if (grid > a.n_tiles) grid = a.n_tiles;
+    L->grid = per_sm * n_sm;
+    layout_tiles(c, wpc, L->grid, &L->a);
+    if (L->grid > L->a.n_tiles) L->grid = L->a.n_tiles;
+    return PHAST_OK;
+}
+
+// Stream part: reset the tile counter, launch.
+int enqueue_batched(phast_ctx* c, const BatchedLaunch& L, cudaStream_t st) {
     PHAST_CUDA_TRY(cudaMemsetAsync(c->tile_counter, 0, sizeof(int32_t), st));
-    fn<<<grid, threads, sm, st>>>(a);
+    L.fn<<<L.grid, L.threads, L.smem, st>>>(L.a);
     PHAST_CUDA_TRY(cudaGetLastError());
     return PHAST_OK;
+}
+
+int launch_batched(phast_ctx* c, const SweepArgs& a0, int tpw, int wpc, bool fp32, cudaStream_t st) {
+    BatchedLaunch L;
+    const int rc = prepare_batched(c, a0, tpw, wpc, fp32, &L);
+    if (rc != PHAST_OK) return rc;
+    return enqueue_batched(c, L, st);
 }
 
 void default_tile(const phast_ctx* c, int* tpw, int* wpc) {
@@ -949,4 +970,91 @@ extern "C" int phast_ctx_restore(phast_ctx* c, const void* buf, size_t len, void
     if (rc) return rc;
     PHAST_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
     return PHAST_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One multicanonical iteration (sweeps, then Berg's step per system type) as a
+// CUDA graph, replayed by phast_graph_launch.
+// ---------------------------------------------------------------------------
+struct phast_graph {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" int phast_ctx_capture_iteration(phast_ctx* c, int64_t n_sweeps, double* lnW, int32_t n_jk,
+                                           uint64_t* hist_sum, double* g_acc, double* flat_out, phast_graph** out,
+                                           void* stream) {
+    if (out) *out = nullptr;
+    if (!c || !lnW || !hist_sum || !g_acc || !out)
+        return phast_set_error(PHAST_EINVAL, "phast_ctx_capture_iteration: NULL argument");
+    if (!stream)
+        return phast_set_error(PHAST_EINVAL, "phast_ctx_capture_iteration: the legacy default stream cannot be captured");
+    if (n_sweeps < 1) return phast_set_error(PHAST_EINVAL, "phast_ctx_capture_iteration: n_sweeps < 1");
+    if (n_jk < 1) return phast_set_error(PHAST_EINVAL, "phast_ctx_capture_iteration: n_jk < 1");
+    const bool fp32 = c->desc[0].pair_precision == 32;
+    int max_bins = 1;
+    size_t hs_bytes = 0;
+    for (int s = 0; s < c->n_sys; ++s) {
+        if (n_jk > c->desc[s].n_walkers)
+            return phast_set_error(PHAST_EINVAL, "phast_ctx_capture_iteration: n_jk %d > walkers of system %d", n_jk, s);
+        if ((c->desc[s].pair_precision == 32) != fp32)
+            return phast_set_error(PHAST_EINVAL, "phast_ctx_capture_iteration: system types mix pair precisions");
+        max_bins = std::max(max_bins, (int)c->desc[s].n_bins);
+        hs_bytes += sizeof(uint64_t) * (size_t)n_jk * (size_t)c->desc[s].n_bins;
+    }
+    SweepArgs a;
+    fill_args(c, n_sweeps, lnW, n_jk, hist_sum, nullptr, nullptr, 0, c->wpc, &a);
+    BatchedLaunch L;
+    int rc = prepare_batched(c, a, c->tpw, c->wpc, fp32, &L);
+    if (rc != PHAST_OK) return rc;
+    // the Berg kernel's shared-memory limit is set outside the capture
+    rc = phast_launch_berg(max_bins, 1.0, nullptr, 1, nullptr, nullptr, nullptr, nullptr, nullptr, true);
+    if (rc != PHAST_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return phast_set_error(PHAST_ECUDA, "phast_ctx_capture_iteration: %s", cudaGetErrorString(e));
+    rc = PHAST_OK;
+    if (cudaMemsetAsync(hist_sum, 0, hs_bytes, st) != cudaSuccess) rc = PHAST_ECUDA;
+    if (rc == PHAST_OK) rc = enqueue_batched(c, L, st);
+    for (int s = 0; s < c->n_sys && rc == PHAST_OK; ++s) {
+        const SysDesc& d = c->desc[s];
+        rc = phast_launch_berg(d.n_bins, d.bin_width, hist_sum + a.hs_off[s], n_jk, lnW + d.lnw_off, g_acc + d.lnw_off,
+                               nullptr, flat_out ? flat_out + 4 * s : nullptr, st, false);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(st, &graph);
+    if (rc != PHAST_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rc != PHAST_OK ? rc : phast_set_error(PHAST_ECUDA, "phast_ctx_capture_iteration: %s", cudaGetErrorString(e));
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return phast_set_error(PHAST_ECUDA, "phast_ctx_capture_iteration: instantiate: %s", cudaGetErrorString(e));
+    }
+    phast_graph* g = (phast_graph*)malloc(sizeof(phast_graph));
+    if (!g) {
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        return phast_set_error(PHAST_ENOMEM, "phast_ctx_capture_iteration: out of host memory");
+    }
+    g->graph = graph;
+    g->exec = exec;
+    *out = g;
+    return PHAST_OK;
+}
+
+extern "C" int phast_graph_launch(phast_graph* g, void* stream) {
+    if (!g) return phast_set_error(PHAST_EINVAL, "phast_graph_launch: NULL graph");
+    PHAST_CUDA_TRY(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+    return PHAST_OK;
+}
+
+extern "C" void phast_graph_destroy(phast_graph* g) {
+    if (!g) return;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    free(g);
 }

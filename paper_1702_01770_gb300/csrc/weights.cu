@@ -105,16 +105,24 @@ berg_kernel(int K, double w, const unsigned long long* __restrict__ hist, int n_
 
 }  // namespace
 
+int phast_launch_berg(int32_t K, double bin_width, const uint64_t* hist, int32_t n_blocks, double* lnW,
+                      double* g_acc, double* beta_out, double* flat_out, cudaStream_t st, bool set_attr) {
+    size_t sm = sizeof(double) * (size_t)(K > 1 ? K - 1 : 1);
+    if (set_attr)   // always the largest K, so that a captured launch never meets a lower limit
+        PHAST_CUDA_TRY(cudaFuncSetAttribute(berg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)(sizeof(double) * (PHAST_MAX_BINS - 1))));
+    if (!hist) return PHAST_OK;   // limit only
+    berg_kernel<<<1, kThreads, sm, st>>>(K, bin_width, reinterpret_cast<const unsigned long long*>(hist), n_blocks, lnW,
+                                         g_acc, beta_out, flat_out);
+    PHAST_CUDA_TRY(cudaGetLastError());
+    return PHAST_OK;
+}
+
 extern "C" int phast_weight_update(int32_t K, double bin_width, const uint64_t* hist, int32_t n_blocks,
                                    double* lnW, double* g_acc, double* beta_out, double* flat_out, void* stream) {
     if (K < 1 || K > PHAST_MAX_BINS) return phast_set_error(PHAST_EINVAL, "phast_weight_update: K %d outside [1, %d]", K, PHAST_MAX_BINS);
     if (!(bin_width > 0.0)) return phast_set_error(PHAST_EINVAL, "phast_weight_update: bin_width must be > 0");
     if (n_blocks < 1) return phast_set_error(PHAST_EINVAL, "phast_weight_update: n_blocks < 1");
     if (!hist || !lnW || (K > 1 && !g_acc)) return phast_set_error(PHAST_EINVAL, "phast_weight_update: NULL argument");
-    size_t sm = sizeof(double) * (size_t)(K > 1 ? K - 1 : 1);
-    PHAST_CUDA_TRY(cudaFuncSetAttribute(berg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    berg_kernel<<<1, kThreads, sm, (cudaStream_t)stream>>>(K, bin_width, reinterpret_cast<const unsigned long long*>(hist),
-                                                           n_blocks, lnW, g_acc, beta_out, flat_out);
-    PHAST_CUDA_TRY(cudaGetLastError());
-    return PHAST_OK;
+    return phast_launch_berg(K, bin_width, hist, n_blocks, lnW, g_acc, beta_out, flat_out, (cudaStream_t)stream, true);
 }

@@ -27,7 +27,8 @@ SYMBOLS = ["phast_energy", "phast_delta_energy", "phast_ctx_create", "phast_ctx_
            "phast_ctx_get_state", "phast_ctx_set_state", "phast_ctx_set_tile", "phast_ctx_get_tile",
            "phast_ctx_autotune", "phast_muca_sweep", "phast_weight_update", "phast_micro_workspace_size",
            "phast_micro_analysis", "phast_micro_analysis_noalloc", "phast_ctx_checkpoint", "phast_ctx_restore", "phast_last_error",
-           "phast_version"]
+           "phast_version", "phast_ctx_capture_iteration", "phast_graph_launch",
+           "phast_graph_destroy"]
 
 
 class PhastError(RuntimeError):
@@ -93,6 +94,10 @@ def lib():
                                            C.c_size_t, vp]
         L.phast_micro_analysis_noalloc.argtypes = [i32, dbl, dbl, vp, vp, i32, i32, i32, i32, vp, P(_MicroOut),
                                                    vp]
+        L.phast_ctx_capture_iteration.argtypes = [vp, i64, vp, i32, vp, vp, vp, P(vp), vp]
+        L.phast_graph_launch.argtypes = [vp, vp]
+        L.phast_graph_destroy.argtypes = [vp]
+        L.phast_graph_destroy.restype = None
         L.phast_ctx_checkpoint.argtypes = [vp, vp, P(C.c_size_t), vp]
         L.phast_ctx_restore.argtypes = [vp, vp, C.c_size_t, vp]
         L.phast_last_error.restype = C.c_char_p
@@ -291,6 +296,18 @@ class Context:
         _check(lib().phast_muca_sweep(self.h, int(n_sweeps), _ptr(lnW), form, n_jk, _ptr(hist_sum),
                                       _ptr(hist_walker), _ptr(trace), trace_walkers, _stream(stream)))
 
+    def capture_iteration(self, n_sweeps: int, lnW: torch.Tensor, hist_sum: torch.Tensor, g_acc: torch.Tensor,
+                          n_jk: int = 1, flat_out: torch.Tensor | None = None, stream=None) -> "IterationGraph":
+        """One multicanonical iteration (clear hist_sum, n_sweeps batched sweeps, Berg's step per
+        system type) captured as a CUDA graph; g_acc is laid out like lnW.  Captured on `stream`
+        (a side stream by default), replayed by IterationGraph.launch."""
+        cap = stream if stream is not None else torch.cuda.Stream()
+        cap.wait_stream(torch.cuda.current_stream())
+        h = C.c_void_p()
+        _check(lib().phast_ctx_capture_iteration(self.h, int(n_sweeps), _ptr(lnW), n_jk, _ptr(hist_sum), _ptr(g_acc),
+                                                 _ptr(flat_out), C.byref(h), _stream(cap)))
+        return IterationGraph(h, keep=(self, lnW, hist_sum, g_acc, flat_out))
+
     def trace_buffer(self, n_sweeps: int, walkers: int, device="cuda") -> torch.Tensor:
         n = walkers * n_sweeps * self.N[0]
         return torch.zeros(n * TRACE_DTYPE.itemsize, dtype=torch.uint8, device=device)
@@ -306,6 +323,26 @@ class Context:
     def restore(self, blob: bytes, stream=None):
         buf = C.create_string_buffer(blob, len(blob))
         _check(lib().phast_ctx_restore(self.h, buf, len(blob), _stream(stream)))
+
+
+class IterationGraph:
+    """A captured multicanonical iteration (phast_ctx_capture_iteration); holds the
+    context and buffers it was captured with."""
+
+    def __init__(self, handle, keep):
+        self.h = handle
+        self._keep = keep
+
+    def launch(self, stream=None):
+        _check(lib().phast_graph_launch(self.h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().phast_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
 
 
 def phast_weight_update(hist: torch.Tensor, lnW: torch.Tensor, g_acc: torch.Tensor, bin_width: float,
