@@ -78,6 +78,12 @@ def lib():
         L.orc_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
         L.orc_energy.argtypes = [P(_Model), P(C.c_double), P(C.c_double)]
         L.orc_energy.restype = C.c_double
+        L.orc_energy_grad.argtypes = [P(_Model), P(C.c_double), P(C.c_double), P(C.c_double)]
+        L.orc_energy_grad.restype = C.c_double
+        L.orc_reweight_sensitivity.argtypes = [C.c_int64, P(C.c_double), P(C.c_double), P(C.c_double), C.c_int32,
+                                               C.c_int32, P(C.c_double), P(C.c_double), P(C.c_double),
+                                               P(C.c_double), P(C.c_double)]
+        L.orc_reweight_sensitivity.restype = None
         L.orc_propose.argtypes = [P(_Model), P(_Muca), C.c_uint64, C.c_uint64, P(Move), P(C.c_double)]
         L.orc_apply_move.argtypes = [P(_Model), P(Move), P(C.c_double), P(C.c_double)]
         L.orc_apply_move.restype = C.c_int
@@ -174,6 +180,31 @@ def energy(model: Model, xyz, terms: bool = False):
     m = model.c_struct()
     e = lib().orc_energy(C.byref(m), _ptr(x, C.c_double), _ptr(t, C.c_double))
     return (e, t) if terms else e
+
+
+def energy_grad(model: Model, xyz):
+    """(E, dE/dxyz [N, 3], dE/d(C_AA, C_BB, C_AB, kappa, kappa_C) [5]) of one conformation."""
+    x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
+    assert x.size == 3 * model.n_total
+    gx, gp = np.zeros(x.size), np.zeros(5)
+    m = model.c_struct()
+    e = lib().orc_energy_grad(C.byref(m), _ptr(x, C.c_double), _ptr(gx, C.c_double), _ptr(gp, C.c_double))
+    return e, gx.reshape(-1, 3), gp
+
+
+def reweight_sensitivity(E, D, lnW, n_monomers: int, T):
+    """<E>_T, c_V(T) per monomer and their derivatives in a parameter from
+    multicanonical samples (energies E, derivatives D, sampling log-weights lnW)."""
+    E = np.ascontiguousarray(E, dtype=np.float64)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    lnW = np.ascontiguousarray(lnW, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    assert E.size == D.size == lnW.size
+    out = [np.zeros(max(T.size, 1)) for _ in range(4)]
+    lib().orc_reweight_sensitivity(C.c_int64(E.size), _ptr(E, C.c_double), _ptr(D, C.c_double),
+                                   _ptr(lnW, C.c_double), C.c_int32(n_monomers), C.c_int32(T.size),
+                                   _ptr(T, C.c_double), *[_ptr(o, C.c_double) for o in out])
+    return dict(E_T=out[0][: T.size], cV_T=out[1][: T.size], dE_T=out[2][: T.size], dcV_T=out[3][: T.size])
 
 
 def propose(model: Model, muca: Muca, seed: int, t: int):

@@ -678,3 +678,167 @@ void orc_micro_analysis(int32_t K, double e_min, double bin_width, const double*
         }
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Derivatives of the energy of Eq. 2/3 (with the torsion term), for the      */
+/* force-field sensitivities: every term differentiated by hand, in the same  */
+/* loops as orc_energy.  Parameters p = (C_AA, C_BB, C_AB, kappa, kappa_C):   */
+/* the energy is linear in each, so dE/dp is the sum of the terms it          */
+/* multiplies.  Between different chains of a periodic system the minimum     */
+/* image d - L rint(d / L) has derivative 1 in d (rint is piecewise constant).*/
+/* ------------------------------------------------------------------------- */
+static void orc_cross(const double a[3], const double b[3], double out[3]) {
+    out[0] = a[1] * b[2] - a[2] * b[1];
+    out[1] = a[2] * b[0] - a[0] * b[2];
+    out[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double orc_dot(const double a[3], const double b[3]) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+double orc_energy_grad(const orc_model* m, const double* xyz, double* gx, double* gp) {
+    int N = orc_total(m);
+    double g_local[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    double E = 0.0;
+    if (gx) for (int q = 0; q < 3 * N; ++q) gx[q] = 0.0;
+    for (int c = 0, o = 0; c < m->n_chains; o += m->chain_len[c], ++c) {
+        int n = m->chain_len[c];
+        /* bending: kappa_C (1 - cos theta), cos theta = a.b / (|a| |b|), a = x1 - x0, b = x2 - x1 */
+        for (int k = 1; k <= n - 2; ++k) {
+            int i0 = o + k - 1, i1 = o + k, i2 = o + k + 1;
+            double a[3], b[3];
+            for (int d = 0; d < 3; ++d) {
+                a[d] = xyz[3 * i1 + d] - xyz[3 * i0 + d];
+                b[d] = xyz[3 * i2 + d] - xyz[3 * i1 + d];
+            }
+            double la = sqrt(orc_dot(a, a)), lb = sqrt(orc_dot(b, b));
+            double cs = orc_dot(a, b) / (la * lb);
+            E = E + m->k_bend * (1.0 - cs);
+            g_local[4] = g_local[4] + (1.0 - cs);
+            if (!gx) continue;
+            for (int d = 0; d < 3; ++d) {
+                double dca = b[d] / (la * lb) - cs * a[d] / (la * la);   /* d cos / d a */
+                double dcb = a[d] / (la * lb) - cs * b[d] / (lb * lb);   /* d cos / d b */
+                /* E = kappa_C (1 - cos): dE/da = -kappa_C dca, a = x1 - x0, b = x2 - x1 */
+                gx[3 * i0 + d] = gx[3 * i0 + d] + m->k_bend * dca;
+                gx[3 * i1 + d] = gx[3 * i1 + d] - m->k_bend * (dca - dcb);
+                gx[3 * i2 + d] = gx[3 * i2 + d] - m->k_bend * dcb;
+            }
+        }
+        /* torsion: -kappa cos tau, cos tau = n1.n2 / (|n1| |n2|), n1 = u x v, n2 = v x w */
+        for (int j = 0; j <= n - 4; ++j) {
+            int i0 = o + j;
+            double u[3], v[3], w[3], n1[3], n2[3];
+            for (int d = 0; d < 3; ++d) {
+                u[d] = xyz[3 * (i0 + 1) + d] - xyz[3 * i0 + d];
+                v[d] = xyz[3 * (i0 + 2) + d] - xyz[3 * (i0 + 1) + d];
+                w[d] = xyz[3 * (i0 + 3) + d] - xyz[3 * (i0 + 2) + d];
+            }
+            orc_cross(u, v, n1);
+            orc_cross(v, w, n2);
+            double n11 = orc_dot(n1, n1), n22 = orc_dot(n2, n2);
+            if (n11 * n22 < 1e-20) continue;   /* degenerate dihedral: no term, no derivative */
+            double l1 = sqrt(n11), l2 = sqrt(n22);
+            double cs = orc_dot(n1, n2) / (l1 * l2);
+            E = E - m->k_tors * cs;
+            g_local[3] = g_local[3] - cs;
+            if (!gx) continue;
+            double g1[3], g2[3];   /* d cos / d n1, d cos / d n2 */
+            for (int d = 0; d < 3; ++d) {
+                g1[d] = n2[d] / (l1 * l2) - cs * n1[d] / n11;
+                g2[d] = n1[d] / (l1 * l2) - cs * n2[d] / n22;
+            }
+            /* d(g1.(u x v))/du = v x g1, /dv = g1 x u; d(g2.(v x w))/dv = w x g2, /dw = g2 x v */
+            double du[3], dv1[3], dv2[3], dw[3];
+            orc_cross(v, g1, du);
+            orc_cross(g1, u, dv1);
+            orc_cross(w, g2, dv2);
+            orc_cross(g2, v, dw);
+            for (int d = 0; d < 3; ++d) {
+                double eu = -m->k_tors * du[d], ev = -m->k_tors * (dv1[d] + dv2[d]), ew = -m->k_tors * dw[d];
+                gx[3 * i0 + d] = gx[3 * i0 + d] - eu;
+                gx[3 * (i0 + 1) + d] = gx[3 * (i0 + 1) + d] + eu - ev;
+                gx[3 * (i0 + 2) + d] = gx[3 * (i0 + 2) + d] + ev - ew;
+                gx[3 * (i0 + 3) + d] = gx[3 * (i0 + 3) + d] + ew;
+            }
+        }
+    }
+    /* Lennard-Jones pairs (Eq. 2: i < j - 1 of one chain; Eq. 3: all pairs of different chains):
+     * phi = k (s^6 - C s^3), s = 1 / r^2, dphi / d(r^2) = k s (3 C s^3 - 6 s^6), dphi/dC = -k s^3 */
+    for (int i = 0; i < N; ++i) {
+        int ci = orc_chain_of(m, i);
+        for (int j = i + 1; j < N; ++j) {
+            int cj = orc_chain_of(m, j);
+            if (ci == cj && j < i + 2) continue;
+            double dv[3], r2 = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                double x = xyz[3 * i + d] - xyz[3 * j + d];
+                if (ci != cj && m->box_L > 0.0) x = x - m->box_L * rint(x / m->box_L);
+                dv[d] = x;
+                r2 = r2 + x * x;
+            }
+            int si = m->seq[i], sj = m->seq[j];
+            double C = m->C[2 * si + sj];
+            double k = (ci == cj) ? m->k_lj_intra : m->k_lj_inter;
+            double s = 1.0 / r2, s3 = s * s * s, s6 = s3 * s3;
+            E = E + k * (s6 - C * s3);
+            int pidx = (si == sj) ? (si == 0 ? 0 : 1) : 2;
+            g_local[pidx] = g_local[pidx] - k * s3;
+            if (!gx) continue;
+            double f = 2.0 * k * s * (3.0 * C * s3 - 6.0 * s6);   /* 2 dphi/d(r^2) */
+            for (int d = 0; d < 3; ++d) {
+                gx[3 * i + d] = gx[3 * i + d] + f * dv[d];
+                gx[3 * j + d] = gx[3 * j + d] - f * dv[d];
+            }
+        }
+    }
+    if (gp) for (int q = 0; q < 5; ++q) gp[q] = g_local[q];
+    return E;
+}
+
+/* Canonical averages and their parameter derivatives from multicanonical
+ * samples (Sec. 2.2: reweighting the multicanonical ensemble to temperature T).
+ * Sample n has energy E_n, derivative D_n = dE/dlambda and was drawn with
+ * log-weight lnW_n, so its canonical weight at T is w_n ~ exp(-E_n / T - lnW_n)
+ * (the sampling weights do not depend on lambda).  With beta = 1 / T and
+ * centred moments over the w_n:
+ *   <E>, c_V = <(E - <E>)^2> / (N T^2),
+ *   d<E>/dlambda = <D> - beta <(E - <E>)(D - <D>)>,
+ *   d c_V/dlambda = [2 <(E - <E>)(D - <D>)> - beta <(E - <E>)^2 (D - <D>)>] / (N T^2),
+ * the last from d<O>/dlambda = <dO/dlambda> - beta Cov(O, D) for O = E and E^2. */
+void orc_reweight_sensitivity(int64_t n, const double* E, const double* D, const double* lnW, int32_t n_monomers,
+                              int32_t n_T, const double* T, double* E_T, double* cV_T, double* dE_T, double* dcV_T) {
+    for (int i = 0; i < n_T; ++i) {
+        double beta = 1.0 / T[i];
+        double amax = -INFINITY;
+        for (int64_t q = 0; q < n; ++q) {
+            double a = -beta * E[q] - lnW[q];
+            if (a > amax) amax = a;
+        }
+        double Z = 0.0, sE = 0.0, sD = 0.0;
+        for (int64_t q = 0; q < n; ++q) {
+            double w = exp(-beta * E[q] - lnW[q] - amax);
+            Z = Z + w;
+            sE = sE + w * E[q];
+            sD = sD + w * D[q];
+        }
+        double mE = sE / Z, mD = sD / Z;
+        double vE = 0.0, cED = 0.0, m3 = 0.0;
+        for (int64_t q = 0; q < n; ++q) {
+            double w = exp(-beta * E[q] - lnW[q] - amax);
+            double e = E[q] - mE, dd = D[q] - mD;
+            vE = vE + w * e * e;
+            cED = cED + w * e * dd;
+            m3 = m3 + w * e * e * dd;
+        }
+        vE = vE / Z;
+        cED = cED / Z;
+        m3 = m3 / Z;
+        double nT2 = (double)n_monomers * T[i] * T[i];
+        E_T[i] = mE;
+        cV_T[i] = vE / nT2;
+        dE_T[i] = mD - beta * cED;
+        dcV_T[i] = (2.0 * cED - beta * m3) / nT2;
+    }
+}

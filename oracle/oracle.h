@@ -125,6 +125,17 @@ void orc_micro_analysis(int32_t K, double e_min, double bin_width, const double*
                         double* S, double* beta, double* CV,
                         double* E_T, double* cV_T, double* peak);
 
+/* Energy (returned) and its derivatives: gx [N*3] (nullable) with respect to
+ * the coordinates, gp [5] (nullable) with respect to (C_AA, C_BB, C_AB, kappa,
+ * kappa_C), each term of Eq. 2/3 and the torsion term differentiated by hand. */
+double orc_energy_grad(const orc_model* m, const double* xyz, double* gx, double* gp);
+
+/* Canonical <E>, c_V (per monomer) and their derivatives in a parameter lambda
+ * at temperatures T[n_T], reweighted from n multicanonical samples with
+ * energies E, derivatives D = dE/dlambda and sampling log-weights lnW. */
+void orc_reweight_sensitivity(int64_t n, const double* E, const double* D, const double* lnW, int32_t n_monomers,
+                              int32_t n_T, const double* T, double* E_T, double* cV_T, double* dE_T, double* dcV_T);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,39 @@ def random_saw(n: int, d_min: float, rng: np.random.Generator, max_tries: int = 
             return x
 
 
+def random_saws(B: int, n: int, d_min: float, rng: np.random.Generator, max_tries: int = 200) -> np.ndarray:
+    """B independent random self-avoiding walks grown together (unit bonds,
+    non-bonded distances >= d_min), (B, n, 3); a walk whose monomer finds no
+    place in max_tries draws restarts from scratch."""
+    out = np.empty((B, n, 3))
+    todo = np.arange(B)
+    while todo.size:
+        m = todo.size
+        x = np.zeros((m, n, 3))
+        alive = np.ones(m, bool)
+        for i in range(1, n):
+            placed = np.zeros(m, bool)
+            placed[~alive] = True
+            for _ in range(max_tries):
+                idx = np.nonzero(~placed)[0]
+                if idx.size == 0:
+                    break
+                v = rng.normal(size=(idx.size, 3))
+                v /= np.linalg.norm(v, axis=1, keepdims=True)
+                cand = x[idx, i - 1] + v
+                if i >= 2:
+                    d2 = np.sum((x[idx, : i - 1] - cand[:, None, :]) ** 2, axis=2)
+                    ok = np.min(d2, axis=1) >= d_min * d_min
+                else:
+                    ok = np.ones(idx.size, bool)
+                x[idx[ok], i] = cand[ok]
+                placed[idx[ok]] = True
+            alive &= placed
+        out[todo[alive]] = x[alive]
+        todo = todo[~alive]
+    return out
+
+
 def _min_image_d2(a: np.ndarray, b: np.ndarray, L: float) -> float:
     d = a[:, None, :] - b[None, :, :]
     if L > 0:
@@ -191,6 +224,17 @@ def config2(walkers_each: int = 1024) -> list:
         s.seed_base = base
         base += s.walkers
     return [s13, s21, s2x34, s8x9]
+
+
+def config3(batch: int = 65536, seed: int = 3):
+    """Differentiation workload: one Fibonacci 55-mer (open boundaries, torsion
+    kappa = -0.5) and a batch of seed-3 random self-avoiding walks of it (unit
+    bonds, non-bonded distances >= 0.8).  Returns (System, xyz [batch, 55, 3])."""
+    s = System("fib55", np.array([55], np.int32), fibonacci_sequence(55), 0.0, k_tors=-0.5,
+               e_min=-100.0, bin_width=0.1, n_bins=_bins(-100.0, 100.0, 0.1), p=(1, 0, 0, 0),
+               recompute_every=100, walkers=1, xyz0=straight_chain(55))
+    rng = np.random.Generator(np.random.Philox(seed))
+    return s, random_saws(batch, 55, 0.8, rng)
 
 
 def config4(walkers: int = 16384) -> System:
