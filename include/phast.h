@@ -211,6 +211,38 @@ int phast_weight_update(int32_t K, double bin_width, const uint64_t* hist, int32
                         double* lnW, double* g_acc, double* beta_out, double* flat_out,
                         void* stream);
 
+/* ---- Force-field derivatives (Eq. 2/3 and the torsion term) ---------- */
+
+/* Energy and its derivatives for a batch of B conformations of one system:
+ * xyz dev FP64 [B][N][3]; E_out dev FP64 [B] or NULL; grad_xyz dev FP64
+ * [B][N][3] or NULL (dE/dx, the minimum image between chains of a periodic
+ * system); grad_ff dev FP64 [B][5] or NULL: dE/d(C_AA, C_BB, C_AB, kappa,
+ * kappa_C) -- the Lennard-Jones coefficients of Eq. 1, the torsion weight and
+ * the bending weight kappa_C of Eq. 2.  pair_precision 32: FP32 terms on
+ * coordinates relative to chain centroids, FP64 sums of the energy and the
+ * parameter derivatives; 64: FP64 throughout.  One warp per conformation;
+ * nothing is kept between calls (a backward pass recomputes the forward one).
+ * PHAST_EINVAL for bad arguments. */
+int phast_energy_grad(const phast_system* sys, const phast_ff* ff, int32_t B, const double* xyz,
+                      int32_t pair_precision, double* E_out, double* grad_xyz, double* grad_ff,
+                      void* stream);
+
+/* Canonical averages from multicanonical samples (Sec. 2.2 reweighting) and
+ * their derivatives in a force-field parameter lambda.  Sample q (of n) has
+ * energy E[q], D[q] = dE/dlambda (e.g. a column of grad_ff) and was drawn with
+ * log-weight lnW[q] (the weight of its bin), so at temperature T its
+ * canonical weight is exp(-E/T - lnW) (normalised by log-sum-exp).  With
+ * beta = 1/T and centred moments over those weights, per T[i]:
+ *   E_T = <E>, cV_T = <(E-<E>)^2> / (N T^2)  (N = n_monomers),
+ *   dE_T = d<E>/dlambda = <D> - beta <(E-<E>)(D-<D>)>,
+ *   dcV_T = [2 <(E-<E>)(D-<D>)> - beta <(E-<E>)^2 (D-<D>)>] / (N T^2),
+ * from d<O>/dlambda = <dO/dlambda> - beta Cov(O, D) for O = E and E^2.
+ * All arrays on the device, FP64: E, D, lnW [n]; T, E_T, cV_T, dE_T, dcV_T [n_T].
+ * One CTA per temperature.  PHAST_EINVAL for bad arguments. */
+int phast_reweight_sensitivity(int64_t n, const double* E, const double* D, const double* lnW,
+                               int32_t n_monomers, int32_t n_T, const double* T, double* E_T,
+                               double* cV_T, double* dE_T, double* dcV_T, void* stream);
+
 /* ---- One multicanonical iteration as a CUDA graph (Sec. 2.2, Fig. 2) --- */
 
 /* Captures on `stream` one iteration of the multicanonical loop of Sec. 2.2

@@ -28,7 +28,8 @@ SYMBOLS = ["phast_energy", "phast_delta_energy", "phast_ctx_create", "phast_ctx_
            "phast_ctx_autotune", "phast_muca_sweep", "phast_weight_update", "phast_micro_workspace_size",
            "phast_micro_analysis", "phast_micro_analysis_noalloc", "phast_ctx_checkpoint", "phast_ctx_restore", "phast_last_error",
            "phast_version", "phast_ctx_capture_iteration", "phast_graph_launch",
-           "phast_graph_destroy"]
+           "phast_graph_destroy", "phast_energy_grad",
+           "phast_reweight_sensitivity"]
 
 
 class PhastError(RuntimeError):
@@ -94,6 +95,8 @@ def lib():
                                            C.c_size_t, vp]
         L.phast_micro_analysis_noalloc.argtypes = [i32, dbl, dbl, vp, vp, i32, i32, i32, i32, vp, P(_MicroOut),
                                                    vp]
+        L.phast_energy_grad.argtypes = [P(_System), P(_FF), i32, vp, i32, vp, vp, vp, vp]
+        L.phast_reweight_sensitivity.argtypes = [i64, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
         L.phast_ctx_capture_iteration.argtypes = [vp, i64, vp, i32, vp, vp, vp, P(vp), vp]
         L.phast_graph_launch.argtypes = [vp, vp]
         L.phast_graph_destroy.argtypes = [vp]
@@ -167,6 +170,78 @@ def phast_energy(system, xyz: torch.Tensor, pair_precision: int = 64, stream=Non
     E = torch.empty(B, dtype=torch.float64, device=xyz.device)
     _check(lib().phast_energy(st.sys, st.ff, B, _ptr(xyz), pair_precision, _ptr(E), _stream(stream)))
     return E
+
+
+FF_PARAMS = ("C_AA", "C_BB", "C_AB", "kappa", "kappa_C")
+
+
+def ff_params(system) -> list:
+    """(C_AA, C_BB, C_AB, kappa, kappa_C) of a system: the Lennard-Jones coefficients of
+    Eq. 1, the torsion weight (E_tors = -kappa sum cos tau) and the bending weight."""
+    return [float(system.C[0]), float(system.C[3]), float(system.C[1]), float(system.k_tors), float(system.k_bend)]
+
+
+def with_ff_params(system, params):
+    """Copy of system with the five force-field parameters set."""
+    import dataclasses
+    caa, cbb, cab, kappa, kappa_c = [float(x) for x in params]
+    return dataclasses.replace(system, C=(caa, cab, cab, cbb), k_tors=kappa, k_bend=kappa_c)
+
+
+def phast_energy_grad(system, xyz: torch.Tensor, pair_precision: int = 32, want_xyz: bool = True,
+                      want_ff: bool = True, stream=None):
+    """(E [B], dE/dxyz [B, N, 3] or None, dE/d(C_AA, C_BB, C_AB, kappa, kappa_C) [B, 5] or None),
+    FP64 on the device, of xyz [B, N, 3] FP64 on the device."""
+    st = _Structs([system])
+    xyz = xyz.contiguous()
+    B = xyz.shape[0] if xyz.numel() else 0
+    E = torch.empty(B, dtype=torch.float64, device=xyz.device)
+    gx = torch.empty_like(xyz) if want_xyz else None
+    gf = torch.empty(B, 5, dtype=torch.float64, device=xyz.device) if want_ff else None
+    _check(lib().phast_energy_grad(st.sys, st.ff, B, _ptr(xyz), pair_precision, _ptr(E), _ptr(gx), _ptr(gf),
+                                   _stream(stream)))
+    return E, gx, gf
+
+
+class EnergyFunction(torch.autograd.Function):
+    """E(xyz, params) for a batch of conformations of one system; params are the five
+    force-field parameters (ff_params order).  The backward pass recomputes the forward
+    one in the same kernel (nothing is kept but the inputs)."""
+
+    @staticmethod
+    def forward(ctx, xyz, params, system, pair_precision):
+        s = with_ff_params(system, params.detach().cpu().tolist())
+        E, _, _ = phast_energy_grad(s, xyz.detach().to(torch.float64), pair_precision, want_xyz=False, want_ff=False)
+        ctx.save_for_backward(xyz, params)
+        ctx.system, ctx.pair_precision = system, pair_precision
+        return E
+
+    @staticmethod
+    def backward(ctx, gE):
+        xyz, params = ctx.saved_tensors
+        s = with_ff_params(ctx.system, params.detach().cpu().tolist())
+        _, gx, gf = phast_energy_grad(s, xyz.detach().to(torch.float64), ctx.pair_precision)
+        gE = gE.to(torch.float64)
+        g_xyz = (gE.view(-1, 1, 1) * gx).to(xyz.dtype) if ctx.needs_input_grad[0] else None
+        g_par = (gE.view(-1, 1) * gf).sum(0).to(params.device, params.dtype) if ctx.needs_input_grad[1] else None
+        return g_xyz, g_par, None, None
+
+
+def energy(xyz: torch.Tensor, params: torch.Tensor, system, pair_precision: int = 32) -> torch.Tensor:
+    """Differentiable energies [B] of xyz [B, N, 3] (device) under params [5] (ff_params order)."""
+    return EnergyFunction.apply(xyz, params, system, pair_precision)
+
+
+def reweight_sensitivity(E: torch.Tensor, D: torch.Tensor, lnW: torch.Tensor, n_monomers: int,
+                         T: torch.Tensor, stream=None) -> dict:
+    """<E>_T, c_V(T) and their derivatives in a parameter from multicanonical samples
+    (energies E, derivatives D = dE/dlambda, sampling log-weights lnW), device FP64."""
+    E, D, lnW, T = (x.to(torch.float64).contiguous() for x in (E, D, lnW, T))
+    out = {k: torch.empty(T.numel(), dtype=torch.float64, device=E.device) for k in ("E_T", "cV_T", "dE_T", "dcV_T")}
+    _check(lib().phast_reweight_sensitivity(E.numel(), _ptr(E), _ptr(D), _ptr(lnW), n_monomers, T.numel(), _ptr(T),
+                                            _ptr(out["E_T"]), _ptr(out["cV_T"]), _ptr(out["dE_T"]),
+                                            _ptr(out["dcV_T"]), _stream(stream)))
+    return out
 
 
 def moves_tensor(moves, device) -> torch.Tensor:
