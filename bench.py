@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-grad", action="store_true")
     return ap.parse_args()
 
 
@@ -311,6 +312,30 @@ def run_ours(args):
                         "walkers": 2432, "sweeps": 1, "dtype": "f64"}
         out["batched_over_plain"] = out["pair_evals_per_s"] / world / out["plain"]["pair_evals_per_s"]
         pctx.close()
+
+    # differentiation: energy, dE/dx and dE/d(force-field parameters) of the batch of
+    # 65536 random self-avoiding walks of the Fibonacci 55-mer, FP32 terms
+    if not args.no_grad and rank == 0:
+        gs, gx0 = inputs.config3()
+        gxyz = torch.from_numpy(gx0).to(dev)
+        for _ in range(2):
+            phast.phast_energy_grad(gs, gxyz, 32)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        a.record()
+        for _ in range(reps):
+            phast.phast_energy_grad(gs, gxyz, 32)
+        b.record()
+        torch.cuda.synchronize()
+        gms = a.elapsed_time(b) / reps
+        n = gs.n_total
+        pairs = n * (n - 1) // 2 - (n - 1)
+        out["differentiation"] = {"workload": "65536 random self-avoiding walks of a Fibonacci 55-mer (d_min 0.8)",
+                                  "ms_per_batch": gms, "conformations_per_s": gx0.shape[0] / (gms / 1e3),
+                                  "pair_terms_per_s": gx0.shape[0] * pairs / (gms / 1e3),
+                                  "outputs": "E, dE/dx, dE/d(C_AA, C_BB, C_AB, kappa, kappa_C)", "dtype": "f32"}
+        del gxyz
 
     # end to end through the C ABI with host buffers: state in from pinned host memory, results out
     if not args.no_e2e:
