@@ -84,6 +84,9 @@ def lib():
                                                C.c_int32, P(C.c_double), P(C.c_double), P(C.c_double),
                                                P(C.c_double), P(C.c_double)]
         L.orc_reweight_sensitivity.restype = None
+        L.orc_maxwell.argtypes = [C.c_int32, C.c_double, C.c_double, P(C.c_double), C.c_int32, C.c_int32,
+                                  C.c_double, C.c_double, C.c_double, P(C.c_double), P(C.c_double)]
+        L.orc_maxwell.restype = None
         L.orc_propose.argtypes = [P(_Model), P(_Muca), C.c_uint64, C.c_uint64, P(Move), P(C.c_double)]
         L.orc_apply_move.argtypes = [P(_Model), P(Move), P(C.c_double), P(C.c_double)]
         L.orc_apply_move.restype = C.c_int
@@ -205,6 +208,18 @@ def reweight_sensitivity(E, D, lnW, n_monomers: int, T):
                                    _ptr(lnW, C.c_double), C.c_int32(n_monomers), C.c_int32(T.size),
                                    _ptr(T, C.c_double), *[_ptr(o, C.c_double) for o in out])
     return dict(E_T=out[0][: T.size], cV_T=out[1][: T.size], dE_T=out[2][: T.size], dcV_T=out[3][: T.size])
+
+
+def maxwell(S, e_min: float, bin_width: float, n_monomers: int, fd_half_width: int = 1, beta_c: float = 0.0,
+            tol_beta: float = 0.0, tol_L: float = 0.0):
+    """Free energy per monomer f [K] and the Maxwell construction {beta_c, eps_1, eps_2,
+    latent, barrier, found} from S [K] (NaN on unvisited bins)."""
+    S = np.ascontiguousarray(S, dtype=np.float64)
+    f, res = np.zeros(S.size), np.zeros(6)
+    lib().orc_maxwell(C.c_int32(S.size), C.c_double(e_min), C.c_double(bin_width), _ptr(S, C.c_double),
+                      C.c_int32(n_monomers), C.c_int32(fd_half_width), C.c_double(beta_c), C.c_double(tol_beta),
+                      C.c_double(tol_L), _ptr(f, C.c_double), _ptr(res, C.c_double))
+    return f, dict(zip(("beta_c", "eps_1", "eps_2", "latent", "barrier", "found"), res))
 
 
 def propose(model: Model, muca: Muca, seed: int, t: int):

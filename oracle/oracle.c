@@ -842,3 +842,91 @@ void orc_reweight_sensitivity(int64_t n, const double* E, const double* D, const
         dcV_T[i] = (2.0 * cED - beta * m3) / nT2;
     }
 }
+
+/* ------------------------------------------------------------------------- */
+/* Free energy (Eq. 7) and the Maxwell construction on the caloric curve      */
+/* (Sec. 3.3, ANALYST: Tol_Beta, Tol_L).  Reading: the equal-area line on     */
+/* beta(E) is the common tangent of S(E), i.e. an edge of the upper concave   */
+/* hull of the points (E_k, S_k) over visited bins that spans bins lying      */
+/* below it (a convex intruder).  Among intruders whose latent heat           */
+/* (E_b - E_a)/N is at least tol_L and across which beta_k = (S_{k+h} -       */
+/* S_{k-h})/(2 h w) rises by at least tol_beta (the S-bend), the one with the */
+/* largest latent heat is taken: beta_c its slope, eps_1 = E_a/N,             */
+/* eps_2 = E_b/N, and the barrier of f = (E - S/beta_c)/N between the two     */
+/* coexisting states, max (hull(E_k) - S_k) / (beta_c N) over the bins inside.*/
+/* ------------------------------------------------------------------------- */
+void orc_maxwell(int32_t K, double e_min, double bin_width, const double* S, int32_t n_monomers,
+                 int32_t fd_half_width, double beta_c_in, double tol_beta, double tol_L, double* f_out,
+                 double* res) {
+    double N = (double)n_monomers;
+    int h = fd_half_width;
+    for (int q = 0; q < 6; ++q) res[q] = NAN;
+    res[5] = 0.0;
+    /* upper hull by Andrew's monotone chain over visited bins (S finite), left to right */
+    int* hull = (int*)malloc(sizeof(int) * (size_t)(K > 0 ? K : 1));
+    int nh = 0;
+    for (int k = 0; k < K; ++k) {
+        if (!isfinite(S[k])) continue;
+        double ek = e_min + ((double)k + 0.5) * bin_width;
+        while (nh >= 2) {
+            int i = hull[nh - 2], j = hull[nh - 1];
+            double ei = e_min + ((double)i + 0.5) * bin_width, ej = e_min + ((double)j + 0.5) * bin_width;
+            /* drop j if it lies on or below the chord from i to k */
+            if ((S[j] - S[i]) * (ek - ei) <= (S[k] - S[i]) * (ej - ei)) --nh;
+            else break;
+        }
+        hull[nh++] = k;
+    }
+    double best_L = -1.0;
+    int best_a = -1, best_b = -1;
+    if (beta_c_in <= 0.0) {
+        for (int q = 0; q + 1 < nh; ++q) {
+            int a = hull[q], b = hull[q + 1];
+            int inside = 0;
+            for (int k = a + 1; k < b; ++k) if (isfinite(S[k])) inside = 1;
+            if (!inside) continue;
+            double ea = e_min + ((double)a + 0.5) * bin_width, eb = e_min + ((double)b + 0.5) * bin_width;
+            double L = (eb - ea) / N;
+            /* largest rise of beta across [a, b]: max over k <= j of beta_j - beta_k */
+            double rise = 0.0, bmin = INFINITY;
+            for (int k = a; k <= b; ++k) {
+                if (k - h < 0 || k + h >= K || !isfinite(S[k - h]) || !isfinite(S[k + h])) continue;
+                double bk = (S[k + h] - S[k - h]) / (2.0 * h * bin_width);
+                if (bk - bmin > rise) rise = bk - bmin;
+                if (bk < bmin) bmin = bk;
+            }
+            if (L >= tol_L && rise >= tol_beta && L > best_L) {
+                best_L = L;
+                best_a = a;
+                best_b = b;
+            }
+        }
+    }
+    double beta_c = beta_c_in;
+    if (best_a >= 0) {
+        double ea = e_min + ((double)best_a + 0.5) * bin_width, eb = e_min + ((double)best_b + 0.5) * bin_width;
+        beta_c = (S[best_b] - S[best_a]) / (eb - ea);
+        double gap = 0.0;
+        for (int k = best_a + 1; k < best_b; ++k) {
+            if (!isfinite(S[k])) continue;
+            double ek = e_min + ((double)k + 0.5) * bin_width;
+            double line = S[best_a] + beta_c * (ek - ea);
+            if (line - S[k] > gap) gap = line - S[k];
+        }
+        res[0] = beta_c;
+        res[1] = ea / N;
+        res[2] = eb / N;
+        res[3] = (eb - ea) / N;
+        res[4] = gap / (beta_c * N);
+        res[5] = 1.0;
+    } else if (beta_c_in > 0.0) {
+        res[0] = beta_c_in;
+    }
+    if (f_out) {
+        for (int k = 0; k < K; ++k) {
+            double ek = e_min + ((double)k + 0.5) * bin_width;
+            f_out[k] = (isfinite(S[k]) && beta_c > 0.0) ? (ek - S[k] / beta_c) / N : NAN;
+        }
+    }
+    free(hull);
+}

@@ -136,6 +136,15 @@ double orc_energy_grad(const orc_model* m, const double* xyz, double* gx, double
 void orc_reweight_sensitivity(int64_t n, const double* E, const double* D, const double* lnW, int32_t n_monomers,
                               int32_t n_T, const double* T, double* E_T, double* cV_T, double* dE_T, double* dcV_T);
 
+/* Free energy f_k = (E_k - S_k / beta_c) / N (Eq. 7, per monomer) and the
+ * Maxwell construction on the caloric curve (see orc_maxwell in the .c for the
+ * reading).  S [K] with NaN on unvisited bins; beta_c_in > 0 fixes beta_c (no
+ * construction), 0 asks for it.  res[6] = {beta_c, eps_1, eps_2, latent heat,
+ * barrier, found}; f_out [K] nullable. */
+void orc_maxwell(int32_t K, double e_min, double bin_width, const double* S, int32_t n_monomers,
+                 int32_t fd_half_width, double beta_c_in, double tol_beta, double tol_L, double* f_out,
+                 double* res);
+
 #ifdef __cplusplus
 }
 #endif
