@@ -297,6 +297,29 @@ int phast_micro_analysis(int32_t K, double e_min, double bin_width, const double
                          const phast_micro_out* out, void* workspace, size_t workspace_bytes,
                          void* stream);
 
+/* Free energy (Eq. 7) and the Maxwell construction on the caloric curve
+ * (Sec. 3.3, ANALYST with Tol_Beta and Tol_L).  S_k from lnW and hist as in
+ * phast_micro_analysis (shifted to max S = 0, unvisited bins skipped).  The
+ * equal-area line on beta(E) is the common tangent of S(E): an edge of the
+ * upper concave hull of (E_k, S_k) spanning bins below it.  Among those with
+ * latent heat (E_b - E_a)/N >= tol_L across which beta_k = (S_{k+h} -
+ * S_{k-h})/(2 h w) rises by >= tol_beta, the widest gives beta_c (its slope),
+ * eps_1 = E_a/N, eps_2 = E_b/N, the latent heat, and the barrier
+ * max (hull - S) / (beta_c N) of f between the coexisting states.  beta_c > 0
+ * fixes beta_c instead (no construction); 0 asks for it.
+ *  f_out: dev [K] or NULL, f_k = (E_k - S_k / beta_c) / N from all blocks (NaN
+ *         where S is undefined or no beta_c was found);
+ *  rep: dev [(1 + R) * 6], R = n_blocks if n_blocks >= 2 (else 0): row 0 from
+ *       all blocks, row r from all but block r-1; each row {beta_c, eps_1,
+ *       eps_2, latent, barrier, found (1/0)};
+ *  err: dev [6] or NULL: jackknife errors of row 0 over the R rows (NaN unless
+ *       every row found a transition); err[5] = the number of rows that did.
+ * K <= PHAST_MAX_BINS (up to 192 KB of shared memory per CTA).  PHAST_EINVAL
+ * for bad arguments. */
+int phast_maxwell(int32_t K, double e_min, double bin_width, const double* lnW, const uint64_t* hist,
+                  int32_t n_blocks, int32_t fd_half_width, int32_t n_monomers, double beta_c,
+                  double tol_beta, double tol_L, double* f_out, double* rep, double* err, void* stream);
+
 /* Allocation-free variant of phast_micro_analysis, for callers that cannot
  * allocate device memory when they run the analysis (a plug-in working inside
  * another program's CUDA context under a fixed memory budget, or code between

@@ -181,6 +181,131 @@ finish_kernel(int K, const double* __restrict__ T, int n_T, int R, int n_jk, Wor
     if (threadIdx.x < 2) jackknife(wk.peak + threadIdx.x, 2, n_jk, o.peak, o.peak_err, threadIdx.x);
 }
 
+// ---------------------------------------------------------------------------
+// Free energy (Eq. 7) and the Maxwell construction on the caloric curve
+// (ANALYST's Tol_Beta / Tol_L): the equal-area line on beta(E) is the common
+// tangent of S(E), an edge of the upper concave hull of (E_k, S_k) over the
+// visited bins that spans bins below it.  Among those whose latent heat is at
+// least tol_L and across which beta_k = (S_{k+h} - S_{k-h}) / (2 h w) rises by
+// at least tol_beta, the widest is taken.  One CTA per replicate: S in shared
+// memory, the hull and the selection on one thread (O(K)), f on all threads.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads)
+maxwell_kernel(int K, double e_min, double w, const double* __restrict__ lnW,
+               const unsigned long long* __restrict__ hist, int n_blocks, int h, int n_monomers, double beta_c_in,
+               double tol_beta, double tol_L, double* __restrict__ f_out, double* __restrict__ rep) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* S = reinterpret_cast<double*>(smem_raw);                 // [K]
+    int* hull = reinterpret_cast<int*>(smem_raw + sizeof(double) * (size_t)K);   // [K]
+    __shared__ double red[32];
+    __shared__ double s_beta_c;
+    const int r = blockIdx.x;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    double mx = -INFINITY;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const double H = rep_hist(hist, n_blocks, K, r, k);
+        double s = nan;
+        if (H < 0.0) s = -lnW[k];
+        else if (H > 0.0) s = -lnW[k] + log(H);
+        S[k] = s;
+        if (!isnan(s)) mx = fmax(mx, s);
+    }
+    mx = block_max(mx, red);
+    for (int k = threadIdx.x; k < K; k += blockDim.x)
+        if (!isnan(S[k])) S[k] -= mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double N = (double)n_monomers;
+        auto Ek = [&](int k) { return e_min + ((double)k + 0.5) * w; };
+        double out[6] = {nan, nan, nan, nan, nan, 0.0};
+        int nh = 0;
+        for (int k = 0; k < K; ++k) {   // monotone chain, upper hull
+            if (!isfinite(S[k])) continue;
+            while (nh >= 2) {
+                const int i = hull[nh - 2], j = hull[nh - 1];
+                if ((S[j] - S[i]) * (Ek(k) - Ek(i)) <= (S[k] - S[i]) * (Ek(j) - Ek(i))) --nh;
+                else break;
+            }
+            hull[nh++] = k;
+        }
+        int best_a = -1, best_b = -1;
+        double best_L = -1.0;
+        if (beta_c_in <= 0.0) {
+            for (int q = 0; q + 1 < nh; ++q) {
+                const int a = hull[q], b = hull[q + 1];
+                bool inside = false;
+                for (int k = a + 1; k < b; ++k) inside |= (bool)isfinite(S[k]);
+                if (!inside) continue;
+                const double L = (Ek(b) - Ek(a)) / N;
+                double rise = 0.0, bmin = INFINITY;
+                for (int k = a; k <= b; ++k) {
+                    if (k - h < 0 || k + h >= K || !isfinite(S[k - h]) || !isfinite(S[k + h])) continue;
+                    const double bk = (S[k + h] - S[k - h]) / (2.0 * h * w);
+                    if (bk - bmin > rise) rise = bk - bmin;
+                    if (bk < bmin) bmin = bk;
+                }
+                if (L >= tol_L && rise >= tol_beta && L > best_L) {
+                    best_L = L;
+                    best_a = a;
+                    best_b = b;
+                }
+            }
+        }
+        double bc = beta_c_in;
+        if (best_a >= 0) {
+            const double ea = Ek(best_a), eb = Ek(best_b);
+            bc = (S[best_b] - S[best_a]) / (eb - ea);
+            double gap = 0.0;
+            for (int k = best_a + 1; k < best_b; ++k) {
+                if (!isfinite(S[k])) continue;
+                const double line = S[best_a] + bc * (Ek(k) - ea);
+                if (line - S[k] > gap) gap = line - S[k];
+            }
+            out[0] = bc;
+            out[1] = ea / N;
+            out[2] = eb / N;
+            out[3] = (eb - ea) / N;
+            out[4] = gap / (bc * N);
+            out[5] = 1.0;
+        } else if (beta_c_in > 0.0) {
+            out[0] = beta_c_in;
+        }
+        for (int q = 0; q < 6; ++q) rep[(size_t)r * 6 + q] = out[q];
+        s_beta_c = bc;
+    }
+    __syncthreads();
+    if (r == 0 && f_out) {
+        const double bc = s_beta_c;
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            const double ek = e_min + ((double)k + 0.5) * w;
+            f_out[k] = (isfinite(S[k]) && bc > 0.0) ? (ek - S[k] / bc) / (double)n_monomers : nan;
+        }
+    }
+}
+
+// Jackknife errors of replicate 0's results over the leave-one-block-out rows;
+// NaN when a replicate found no transition; err[5] counts the rows that did.
+__global__ void maxwell_err_kernel(int R, const double* __restrict__ rep, double* __restrict__ err) {
+    const int q = threadIdx.x;
+    if (q >= 6) return;
+    const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    int found = 0;
+    double mean = 0.0;
+    for (int r = 1; r <= R; ++r) {
+        found += rep[(size_t)r * 6 + 5] != 0.0;
+        mean += rep[(size_t)r * 6 + q];
+    }
+    if (q == 5) { err[5] = (double)found; return; }
+    if (R < 2 || found < R) { err[q] = nan; return; }
+    mean /= R;
+    double ss = 0.0;
+    for (int r = 1; r <= R; ++r) {
+        const double d = rep[(size_t)r * 6 + q] - mean;
+        ss += d * d;
+    }
+    err[q] = sqrt((double)(R - 1) / R * ss);
+}
+
 }  // namespace
 
 extern "C" size_t phast_micro_workspace_size(int32_t K, int32_t n_T, int32_t n_blocks) {
@@ -269,4 +394,31 @@ extern "C" int phast_micro_analysis_noalloc(int32_t K, double e_min, double bin_
     }
     return phast_micro_analysis(K, e_min, bin_width, lnW, hist, n_blocks, h, n_monomers, n_T, T, out, scratch,
                                 sizeof(double) * (size_t)PHAST_MICRO_NOALLOC_DOUBLES, stream);
+}
+
+extern "C" int phast_maxwell(int32_t K, double e_min, double bin_width, const double* lnW, const uint64_t* hist,
+                             int32_t n_blocks, int32_t fd_half_width, int32_t n_monomers, double beta_c,
+                             double tol_beta, double tol_L, double* f_out, double* rep, double* err, void* stream) {
+    if (K < 1 || K > PHAST_MAX_BINS) return phast_set_error(PHAST_EINVAL, "phast_maxwell: K %d outside [1, %d]", K, PHAST_MAX_BINS);
+    if (!(bin_width > 0.0)) return phast_set_error(PHAST_EINVAL, "phast_maxwell: bin_width must be > 0");
+    if (!lnW || !rep) return phast_set_error(PHAST_EINVAL, "phast_maxwell: NULL lnW or rep");
+    if (hist && n_blocks < 1) return phast_set_error(PHAST_EINVAL, "phast_maxwell: n_blocks < 1");
+    if (fd_half_width < 1) return phast_set_error(PHAST_EINVAL, "phast_maxwell: fd_half_width < 1");
+    if (n_monomers < 1) return phast_set_error(PHAST_EINVAL, "phast_maxwell: n_monomers < 1");
+    if (!(beta_c >= 0.0) || !(tol_beta >= 0.0) || !(tol_L >= 0.0))
+        return phast_set_error(PHAST_EINVAL, "phast_maxwell: beta_c, tol_beta, tol_L must be >= 0");
+    const int R = (hist && n_blocks >= 2) ? n_blocks : 0;
+    const size_t sm = (sizeof(double) + sizeof(int)) * (size_t)K;
+    cudaStream_t st = (cudaStream_t)stream;
+    PHAST_CUDA_TRY(cudaFuncSetAttribute(maxwell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)((sizeof(double) + sizeof(int)) * PHAST_MAX_BINS)));
+    maxwell_kernel<<<1 + R, kThreads, sm, st>>>(K, e_min, bin_width, lnW, reinterpret_cast<const unsigned long long*>(hist),
+                                                hist ? n_blocks : 0, fd_half_width, n_monomers, beta_c, tol_beta,
+                                                tol_L, f_out, rep);
+    PHAST_CUDA_TRY(cudaGetLastError());
+    if (err) {
+        maxwell_err_kernel<<<1, 32, 0, st>>>(R, rep, err);
+        PHAST_CUDA_TRY(cudaGetLastError());
+    }
+    return PHAST_OK;
 }

@@ -29,7 +29,7 @@ SYMBOLS = ["phast_energy", "phast_delta_energy", "phast_ctx_create", "phast_ctx_
            "phast_micro_analysis", "phast_micro_analysis_noalloc", "phast_ctx_checkpoint", "phast_ctx_restore", "phast_last_error",
            "phast_version", "phast_ctx_capture_iteration", "phast_graph_launch",
            "phast_graph_destroy", "phast_energy_grad",
-           "phast_reweight_sensitivity"]
+           "phast_reweight_sensitivity", "phast_maxwell"]
 
 
 class PhastError(RuntimeError):
@@ -95,6 +95,7 @@ def lib():
                                            C.c_size_t, vp]
         L.phast_micro_analysis_noalloc.argtypes = [i32, dbl, dbl, vp, vp, i32, i32, i32, i32, vp, P(_MicroOut),
                                                    vp]
+        L.phast_maxwell.argtypes = [i32, dbl, dbl, vp, vp, i32, i32, i32, dbl, dbl, dbl, vp, vp, vp, vp]
         L.phast_energy_grad.argtypes = [P(_System), P(_FF), i32, vp, i32, vp, vp, vp, vp]
         L.phast_reweight_sensitivity.argtypes = [i64, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
         L.phast_ctx_capture_iteration.argtypes = [vp, i64, vp, i32, vp, vp, vp, P(vp), vp]
@@ -398,6 +399,27 @@ class Context:
     def restore(self, blob: bytes, stream=None):
         buf = C.create_string_buffer(blob, len(blob))
         _check(lib().phast_ctx_restore(self.h, buf, len(blob), _stream(stream)))
+
+
+MAXWELL_FIELDS = ("beta_c", "eps_1", "eps_2", "latent", "barrier", "found")
+
+
+def phast_maxwell(lnW: torch.Tensor, hist: torch.Tensor | None, e_min: float, bin_width: float, n_monomers: int,
+                  fd_half_width: int = 1, beta_c: float = 0.0, tol_beta: float = 0.0, tol_L: float = 0.0,
+                  stream=None):
+    """Free energy per monomer f [K] and the Maxwell construction: rows [(1 + R), 6] of
+    (MAXWELL_FIELDS) for all blocks and each leave-one-block-out replicate, and their
+    jackknife errors [6]; hist int64 [n_blocks, K] (or [K], or None for S = -lnW)."""
+    K = lnW.numel()
+    n_blocks = 0 if hist is None else hist.numel() // K
+    R = n_blocks if n_blocks >= 2 else 0
+    f = torch.empty(K, dtype=torch.float64, device=lnW.device)
+    rep = torch.empty(1 + R, 6, dtype=torch.float64, device=lnW.device)
+    err = torch.empty(6, dtype=torch.float64, device=lnW.device)
+    _check(lib().phast_maxwell(K, float(e_min), float(bin_width), _ptr(lnW), _ptr(hist), n_blocks, fd_half_width,
+                               n_monomers, float(beta_c), float(tol_beta), float(tol_L), _ptr(f), _ptr(rep),
+                               _ptr(err), _stream(stream)))
+    return f, rep, err
 
 
 class IterationGraph:
