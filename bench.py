@@ -123,7 +123,7 @@ def oracle_walker_moves_per_s(s, seconds: float, threads: int):
     def one(w):
         wk = oracle.new_walker(m, mu, s.xyz0, int(w))
         _, st, _ = oracle.sweep_walker(m, mu, lnW, wk, N)
-        return st[8]
+        return st[oracle.ST_PAIR_EVALS]
 
     t0 = time.perf_counter()
     one(0)

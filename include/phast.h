@@ -32,7 +32,7 @@
 extern "C" {
 #endif
 
-#define PHAST_VERSION 1
+#define PHAST_VERSION 2
 
 /* Hard limits of this build. */
 #define PHAST_MAX_SYSTEMS 8      /* system types in one context */
@@ -52,40 +52,55 @@ enum {
     PHAST_ENONFINITE = -7  /* non-finite coordinates or energy */
 };
 
-enum { PHAST_PIVOT = 0, PHAST_TRANS = 1, PHAST_ROT = 2, PHAST_CRANK = 3 };
+/* Move types (Sec. 3.2, UPDATE_ENGINE): pivot, Galilean translation and
+ * rotation of a chain, crankshaft, bond-length change, spherical cap. */
+enum { PHAST_PIVOT = 0, PHAST_TRANS = 1, PHAST_ROT = 2, PHAST_CRANK = 3, PHAST_BOND = 4, PHAST_CAP = 5 };
+#define PHAST_N_MOVES 6
 
 /* A system type: M chains (each >= 3 monomers), their AB sequence and the box.
  * box_L > 0: periodic cube of side box_L with the minimum image between
  * different chains (chains are never wrapped, so distances within a chain are
- * direct); box_L = 0: open space.  All pointers are host pointers. */
+ * direct); box_L = 0: open space.  sphere_R > 0 (with box_L = 0): the steric
+ * spherical container of Sec. 3.2 (box_size.h), a hard wall at |x| = sphere_R
+ * about the origin -- a configuration with a monomer at |x|^2 > sphere_R^2 has
+ * infinite energy; 0: none.  All pointers are host pointers. */
 typedef struct {
     int32_t n_chains;
     const int32_t* chain_len;   /* host [n_chains] */
     const uint8_t* seq;         /* host [N], N = sum chain_len */
     double box_L;
+    double sphere_R;
 } phast_system;
 
-/* Force field, Eq. 2/3 in the AB limit (kappa_F = 0) plus torsion:
- * E = k_bend sum_k (1 - cos theta_k) - k_tors sum_j cos tau_j
+/* Force field, Eq. 2/3 plus torsion:
+ * E = k_fene R^2 sum_l C_F[2 s_l + s_{l+1}] ln(1 - ((r_{l,l+1} - r0) / R)^2)
+ *   + k_bend sum_k (1 - cos theta_k) - k_tors sum_j cos tau_j
  *   + k_lj_intra sum_{i < j-1} (r^-12 - C r^-6) + k_lj_inter sum_{inter} (...).
- * C[2*s_i + s_j] is C_LJ of Eq. 1 (AA = 1, AB = BA = -1/2, BB = 1/2). */
+ * C[2*s_i + s_j] is C_LJ of Eq. 1 (AA = 1, AB = BA = -1/2, BB = 1/2).  The
+ * FENE bond term is the printed first term of Eq. 2 (r0 = fene_r0, R =
+ * fene_R); it confines bonds when k_fene C_F < 0, and a bond with
+ * |r - r0| >= R has infinite energy.  k_fene = 0 is the AB limit of Sec. 4:
+ * bonds stay at their length and no bond term is evaluated. */
 typedef struct {
     double k_bend, k_tors, k_lj_intra, k_lj_inter;
     double C[4];
+    double k_fene, fene_r0, fene_R;
+    double C_F[4];
 } phast_ff;
 
 /* Multicanonical set-up of one system type (Sec. 2.2, Eq. 8): bins
- * [e_min + k w, e_min + (k+1) w), k < n_bins; move mix p[] over pivot,
- * translation, rotation, crankshaft (sums to 1); amplitudes amax[] (angles in
- * rad <= PHAST_MAX_ANGLE, translation step per component); an FP64 full-energy
+ * [e_min + k w, e_min + (k+1) w), k < n_bins; move mix p[] over the
+ * PHAST_N_MOVES types (sums to 1; bond-length and spherical-cap moves need
+ * k_fene != 0); amplitudes amax[] (angles in rad <= PHAST_MAX_ANGLE,
+ * translation step per component, bond-length step); an FP64 full-energy
  * recompute every `recompute_every` sweeps (0 = never); pair arithmetic of the
  * batched sweep in FP32 (32) or FP64 (64). */
 typedef struct {
     double e_min, bin_width;
     int32_t n_bins;
     int32_t recompute_every;
-    double p[4];
-    double amax[4];
+    double p[PHAST_N_MOVES];
+    double amax[PHAST_N_MOVES];
     int32_t pair_precision;
     int32_t pad;
 } phast_muca_params;
@@ -93,7 +108,10 @@ typedef struct {
 /* An explicit move (64 bytes): pivot about monomer `index` of `chain` by
  * `angle` around unit `axis`; translation by `disp`; rotation of the chain
  * about its centroid; crankshaft of monomer `index` about its neighbours' axis
- * (axis ignored). */
+ * (axis ignored); bond-length change of bond `index` (monomers index and
+ * index+1) by `angle` (the shorter side slides along the bond); spherical cap:
+ * monomer `index` alone rotated by `angle` around `axis` through its bonded
+ * neighbour index-1 (monomer 1 for index 0). */
 typedef struct {
     int32_t type, chain, index, pad;
     double axis[3];
@@ -103,8 +121,8 @@ typedef struct {
 
 /* Per-walker counters, accumulated over sweeps (dev arrays of these). */
 typedef struct {
-    uint64_t attempts[4];
-    uint64_t accepts[4];
+    uint64_t attempts[PHAST_N_MOVES];
+    uint64_t accepts[PHAST_N_MOVES];
     uint64_t pair_evals;   /* 2 per (moved, unmoved) Lennard-Jones pair whose distance can change */
     uint64_t pair_evals_inter;  /* the part of pair_evals between different chains */
     uint64_t recomputes;

@@ -20,7 +20,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
-PIVOT, TRANS, ROT, CRANK = 0, 1, 2, 3
+PIVOT, TRANS, ROT, CRANK, BOND, CAP = 0, 1, 2, 3, 4, 5
+N_MOVES = 6
+# orc_sweep_walker statistics: attempts[6], accepts[6], then these
+ST_PAIR_EVALS, ST_RECOMPUTES, ST_DRIFT, ST_MISMATCHES = 12, 13, 14, 15
 
 
 def build(force: bool = False) -> str:
@@ -43,12 +46,13 @@ class _Model(C.Structure):
                 ("seq", C.POINTER(C.c_uint8)), ("box_L", C.c_double),
                 ("k_bend", C.c_double), ("k_tors", C.c_double),
                 ("k_lj_intra", C.c_double), ("k_lj_inter", C.c_double),
-                ("C", C.c_double * 4)]
+                ("C", C.c_double * 4), ("sphere_R", C.c_double), ("k_fene", C.c_double),
+                ("fene_r0", C.c_double), ("fene_R", C.c_double), ("C_F", C.c_double * 4)]
 
 
 class _Muca(C.Structure):
     _fields_ = [("e_min", C.c_double), ("bin_width", C.c_double), ("n_bins", C.c_int32),
-                ("p", C.c_double * 4), ("amax", C.c_double * 4),
+                ("p", C.c_double * 6), ("amax", C.c_double * 6),
                 ("recompute_every", C.c_int32)]
 
 
@@ -128,6 +132,11 @@ class Model:
     k_lj_intra: float = 4.0
     k_lj_inter: float = 4.0
     C: tuple = (1.0, -0.5, -0.5, 0.5)
+    sphere_R: float = 0.0
+    k_fene: float = 0.0
+    fene_r0: float = 1.0
+    fene_R: float = 0.5
+    C_F: tuple = (1.0, 1.0, 1.0, 1.0)
 
     def __post_init__(self):
         self.chain_len = np.ascontiguousarray(self.chain_len, dtype=np.int32)
@@ -147,6 +156,9 @@ class Model:
         s.k_bend, s.k_tors = float(self.k_bend), float(self.k_tors)
         s.k_lj_intra, s.k_lj_inter = float(self.k_lj_intra), float(self.k_lj_inter)
         s.C = (C.c_double * 4)(*[float(c) for c in self.C])
+        s.sphere_R = float(self.sphere_R)
+        s.k_fene, s.fene_r0, s.fene_R = float(self.k_fene), float(self.fene_r0), float(self.fene_R)
+        s.C_F = (C.c_double * 4)(*[float(c) for c in self.C_F])
         return s
 
 
@@ -162,8 +174,10 @@ class Muca:
     def c_struct(self) -> _Muca:
         s = _Muca()
         s.e_min, s.bin_width, s.n_bins = float(self.e_min), float(self.bin_width), int(self.n_bins)
-        s.p = (C.c_double * 4)(*[float(x) for x in self.p])
-        s.amax = (C.c_double * 4)(*[float(x) for x in self.amax])
+        p = list(self.p) + [0.0] * (6 - len(self.p))
+        a = list(self.amax) + [0.0] * (6 - len(self.amax))
+        s.p = (C.c_double * 6)(*[float(x) for x in p])
+        s.amax = (C.c_double * 6)(*[float(x) for x in a])
         s.recompute_every = int(self.recompute_every)
         return s
 
@@ -179,7 +193,7 @@ def philox(ctr, key) -> np.ndarray:
 def energy(model: Model, xyz, terms: bool = False):
     x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
     assert x.size == 3 * model.n_total
-    t = np.zeros(4)
+    t = np.zeros(5)
     m = model.c_struct()
     e = lib().orc_energy(C.byref(m), _ptr(x, C.c_double), _ptr(t, C.c_double))
     return (e, t) if terms else e
@@ -297,7 +311,7 @@ def sweep_walker(model: Model, muca: Muca, lnW, w: Walker, n_moves: int, hist=No
     E = C.c_double(w.E)
     b = C.c_int32(w.bin)
     t = C.c_uint64(w.t)
-    stats = np.zeros(12)
+    stats = np.zeros(16)
     rec = np.zeros(n_moves, RECORD_DTYPE) if record else None
     f = None
     if force is not None:

@@ -148,7 +148,8 @@ static int orc_total(const orc_model* m) { return orc_chain_offset(m, m->n_chain
 
 /* Draw move t of a walker.  Readings: the move type is chosen by comparing one
  * uniform with the running sum of the type probabilities; the chain is uniform;
- * pivot and crankshaft act on an interior monomer 1..n-2; angles and steps are
+ * pivot and crankshaft act on an interior monomer 1..n-2, a bond-length move
+ * on a bond 0..n-2, a spherical cap on any monomer; angles and steps are
  * uniform in [-max, max]; the axis is isotropic. */
 void orc_propose(const orc_model* m, const orc_muca* mu, uint64_t seed, uint64_t t,
                  orc_move* mv, double* u_acc) {
@@ -164,7 +165,7 @@ void orc_propose(const orc_model* m, const orc_muca* mu, uint64_t seed, uint64_t
 
     int type = -1, last = 0;
     double cum = 0.0;
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 6; ++i) {
         cum = cum + mu->p[i];
         if (mu->p[i] > 0.0) {
             last = i;
@@ -179,13 +180,17 @@ void orc_propose(const orc_model* m, const orc_muca* mu, uint64_t seed, uint64_t
     int n = m->chain_len[mv->chain];
     if (type == ORC_PIVOT || type == ORC_CRANK)
         mv->index = 1 + (int32_t)(((uint64_t)b0[3] * (uint64_t)(n - 2)) >> 32);
+    if (type == ORC_BOND)   /* a bond 0..n-2 */
+        mv->index = (int32_t)(((uint64_t)b0[3] * (uint64_t)(n - 1)) >> 32);
+    if (type == ORC_CAP)    /* any monomer */
+        mv->index = (int32_t)(((uint64_t)b0[3] * (uint64_t)n) >> 32);
     if (type == ORC_TRANS) {
         mv->disp[0] = (2.0 * u_a - 1.0) * mu->amax[ORC_TRANS];
         mv->disp[1] = (2.0 * u_b - 1.0) * mu->amax[ORC_TRANS];
         mv->disp[2] = (2.0 * u_c - 1.0) * mu->amax[ORC_TRANS];
     } else {
-        mv->angle = (2.0 * u_a - 1.0) * mu->amax[type];
-        if (type == ORC_PIVOT || type == ORC_ROT) orc_axis(seed, t, mv->axis);
+        mv->angle = (2.0 * u_a - 1.0) * mu->amax[type];   /* the length step for a bond move */
+        if (type == ORC_PIVOT || type == ORC_ROT || type == ORC_CAP) orc_axis(seed, t, mv->axis);
     }
 }
 
@@ -226,6 +231,25 @@ int orc_apply_move(const orc_model* m, const orc_move* mv, const double* xyz, do
             for (int d = 0; d < 3; ++d) xyz_new[3 * j + d] = xyz[3 * j + d] + mv->disp[d];
         return n;
     }
+    if (mv->type == ORC_BOND) {
+        /* bond l between monomers l and l+1 changes length by delta: the shorter
+         * side (head 0..l or tail l+1..n-1; on a tie the tail) slides along the
+         * unit bond vector u = (x_{l+1} - x_l) / |x_{l+1} - x_l|, by +delta u (tail)
+         * or -delta u (head). */
+        int l = mv->index;
+        double b[3], u[3], step[3];
+        for (int d = 0; d < 3; ++d) b[d] = xyz[3 * (o + l + 1) + d] - xyz[3 * (o + l) + d];
+        double len = sqrt((b[0] * b[0] + b[1] * b[1]) + b[2] * b[2]);
+        if (!(len > 1e-12)) return 0;
+        int head = (l + 1) < (n - 1 - l);
+        double delta = head ? -mv->angle : mv->angle;
+        for (int d = 0; d < 3; ++d) { u[d] = b[d] / len; step[d] = delta * u[d]; }
+        if (head) { lo = o; hi = o + l; }
+        else { lo = o + l + 1; hi = o + n - 1; }
+        for (int j = lo; j <= hi; ++j)
+            for (int d = 0; d < 3; ++d) xyz_new[3 * j + d] = xyz[3 * j + d] + step[d];
+        return hi - lo + 1;
+    }
     if (mv->type == ORC_PIVOT) {
         int k = mv->index;
         if (k < n - 1 - k) { lo = o; hi = o + k - 1; }
@@ -235,6 +259,13 @@ int orc_apply_move(const orc_model* m, const orc_move* mv, const double* xyz, do
         lo = o; hi = o + n - 1;
         orc_centroid(xyz, o, n, center);
         for (int d = 0; d < 3; ++d) axis[d] = mv->axis[d];
+    } else if (mv->type == ORC_CAP) {
+        /* spherical cap: monomer i rotated about an isotropic axis through its
+         * bonded neighbour i-1 (monomer 1 for i = 0), keeping that bond */
+        int i = o + mv->index;
+        int c = mv->index > 0 ? i - 1 : i + 1;
+        for (int d = 0; d < 3; ++d) { center[d] = xyz[3 * c + d]; axis[d] = mv->axis[d]; }
+        lo = hi = i;
     } else {   /* crankshaft */
         int i = o + mv->index;
         double e[3];
@@ -315,6 +346,38 @@ static void orc_chain_local(const orc_model* m, const double* xyz, int o, int n,
     *e_tors = -m->k_tors * tors;
 }
 
+/* FENE bond term of Eq. 2, as printed, for the chain at o with n monomers:
+ * k_fene R^2 sum_l C_F(s_l, s_{l+1}) ln(1 - ((r_{l,l+1} - r0) / R)^2); +inf for a
+ * bond with |r - r0| >= R (outside the potential's range); 0 in the AB limit
+ * k_fene = 0 of Sec. 4, where bonds keep their length. */
+static double orc_chain_fene(const orc_model* m, const double* xyz, int o, int n) {
+    if (m->k_fene == 0.0) return 0.0;
+    double sum = 0.0;
+    for (int l = o; l < o + n - 1; ++l) {
+        double d[3];
+        for (int q = 0; q < 3; ++q) d[q] = xyz[3 * (l + 1) + q] - xyz[3 * l + q];
+        double r = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+        double x = (r - m->fene_r0) / m->fene_R;
+        double x2 = x * x;
+        if (!(x2 < 1.0)) return INFINITY;
+        sum = sum + m->C_F[2 * m->seq[l] + m->seq[l + 1]] * log(1.0 - x2);
+    }
+    return (m->k_fene * (m->fene_R * m->fene_R)) * sum;
+}
+
+/* Steric spherical container (Sec. 3.2, box_size.h), a hard wall about the
+ * origin: 1 if every monomer lo..hi lies at (x^2 + y^2) + z^2 <= R^2 (or there
+ * is no container), else 0. */
+static int orc_inside(const orc_model* m, const double* xyz, int lo, int hi) {
+    if (!(m->sphere_R > 0.0)) return 1;
+    double R2 = m->sphere_R * m->sphere_R;
+    for (int j = lo; j <= hi; ++j) {
+        const double* x = &xyz[3 * j];
+        if ((x[0] * x[0] + x[1] * x[1]) + x[2] * x[2] > R2) return 0;
+    }
+    return 1;
+}
+
 static int orc_chain_of(const orc_model* m, int j) {
     int o = 0;
     for (int c = 0; c < m->n_chains; ++c) {
@@ -326,12 +389,13 @@ static int orc_chain_of(const orc_model* m, int j) {
 
 double orc_energy(const orc_model* m, const double* xyz, double* terms) {
     int N = orc_total(m);
-    double bend = 0.0, tors = 0.0, intra = 0.0, inter = 0.0;
+    double bend = 0.0, tors = 0.0, intra = 0.0, inter = 0.0, fene = 0.0;
     for (int c = 0, o = 0; c < m->n_chains; o += m->chain_len[c], ++c) {
         double eb, et;
         orc_chain_local(m, xyz, o, m->chain_len[c], &eb, &et);
         bend = bend + eb;
         tors = tors + et;
+        fene = fene + orc_chain_fene(m, xyz, o, m->chain_len[c]);
     }
     /* Eq. 2: pairs i < j - 1 of one chain.  Eq. 3: all pairs of different chains. */
     for (int i = 0; i < N; ++i) {
@@ -349,8 +413,10 @@ double orc_energy(const orc_model* m, const double* xyz, double* terms) {
     }
     intra = m->k_lj_intra * intra;
     inter = m->k_lj_inter * inter;
-    if (terms) { terms[0] = bend; terms[1] = tors; terms[2] = intra; terms[3] = inter; }
-    return ((bend + tors) + intra) + inter;
+    if (terms) { terms[0] = bend; terms[1] = tors; terms[2] = intra; terms[3] = inter; terms[4] = fene; }
+    if (!orc_inside(m, xyz, 0, N - 1)) return INFINITY;
+    double E = ((bend + tors) + intra) + inter;
+    return m->k_fene == 0.0 ? E : E + fene;
 }
 
 /* Moved monomer range of a move, [lo, hi] (global indices). */
@@ -358,7 +424,13 @@ static void orc_moved_range(const orc_model* m, const orc_move* mv, int* lo, int
     int o = orc_chain_offset(m, mv->chain);
     int n = m->chain_len[mv->chain];
     if (mv->type == ORC_TRANS || mv->type == ORC_ROT) { *lo = o; *hi = o + n - 1; return; }
-    if (mv->type == ORC_CRANK) { *lo = *hi = o + mv->index; return; }
+    if (mv->type == ORC_CRANK || mv->type == ORC_CAP) { *lo = *hi = o + mv->index; return; }
+    if (mv->type == ORC_BOND) {
+        int l = mv->index;
+        if ((l + 1) < (n - 1 - l)) { *lo = o; *hi = o + l; }
+        else { *lo = o + l + 1; *hi = o + n - 1; }
+        return;
+    }
     int k = mv->index;
     if (k < n - 1 - k) { *lo = o; *hi = o + k - 1; }
     else { *lo = o + k + 1; *hi = o + n - 1; }
@@ -373,8 +445,12 @@ double orc_delta_energy(const orc_model* m, const double* xyz, const orc_move* m
     double* xn = xyz_new ? xyz_new : (double*)malloc(sizeof(double) * 3 * (size_t)N);
     int moved = orc_apply_move(m, mv, xyz, xn);
     double dE;
+    int lo, hi;
+    orc_moved_range(m, mv, &lo, &hi);
     if (moved == 0) {
         dE = NAN;
+    } else if (!orc_inside(m, xn, lo, hi)) {
+        dE = INFINITY;   /* the hard wall of the container */
     } else {
         int o = orc_chain_offset(m, mv->chain);
         int n = m->chain_len[mv->chain];
@@ -382,8 +458,7 @@ double orc_delta_energy(const orc_model* m, const double* xyz, const orc_move* m
         orc_chain_local(m, xyz, o, n, &eb0, &et0);
         orc_chain_local(m, xn, o, n, &eb1, &et1);
         dE = (eb1 + et1) - (eb0 + et0);
-        int lo, hi;
-        orc_moved_range(m, mv, &lo, &hi);
+        if (m->k_fene != 0.0) dE = dE + (orc_chain_fene(m, xn, o, n) - orc_chain_fene(m, xyz, o, n));
         for (int i = lo; i <= hi; ++i) {
             int ci = orc_chain_of(m, i);
             for (int j = 0; j < N; ++j) {
@@ -421,6 +496,7 @@ double orc_delta_scale(const orc_model* m, const double* xyz, const orc_move* mv
         orc_chain_local(m, xyz, o, n, &eb0, &et0);
         orc_chain_local(m, xn, o, n, &eb1, &et1);
         scale = fabs(eb0) + fabs(et0) + fabs(eb1) + fabs(et1);
+        if (m->k_fene != 0.0) scale += fabs(orc_chain_fene(m, xyz, o, n)) + fabs(orc_chain_fene(m, xn, o, n));
         int lo, hi;
         orc_moved_range(m, mv, &lo, &hi);
         for (int i = lo; i <= hi; ++i) {
@@ -485,7 +561,7 @@ int orc_sweep_walker(const orc_model* m, const orc_muca* mu, const double* lnW,
     int N = orc_total(m);
     if (orc_bin(mu, *E) != *bin || *bin < 0) return -1;
     double* xn = (double*)malloc(sizeof(double) * 3 * (size_t)N);
-    uint64_t attempts[4] = {0, 0, 0, 0}, accepts[4] = {0, 0, 0, 0};
+    uint64_t attempts[6] = {0, 0, 0, 0, 0, 0}, accepts[6] = {0, 0, 0, 0, 0, 0};
     int64_t pair_evals = 0, n_recompute = 0, mismatches = 0;
     double drift_max = 0.0;
     uint64_t period = (uint64_t)N * (uint64_t)(mu->recompute_every > 0 ? mu->recompute_every : 0);
@@ -536,11 +612,11 @@ int orc_sweep_walker(const orc_model* m, const orc_muca* mu, const double* lnW,
     }
     free(xn);
     if (stats) {
-        for (int i = 0; i < 4; ++i) { stats[i] = (double)attempts[i]; stats[4 + i] = (double)accepts[i]; }
-        stats[8] = (double)pair_evals;
-        stats[9] = (double)n_recompute;
-        stats[10] = drift_max;
-        stats[11] = (double)mismatches;
+        for (int i = 0; i < 6; ++i) { stats[i] = (double)attempts[i]; stats[6 + i] = (double)accepts[i]; }
+        stats[12] = (double)pair_evals;
+        stats[13] = (double)n_recompute;
+        stats[14] = drift_max;
+        stats[15] = (double)mismatches;
     }
     return 0;
 }
@@ -761,6 +837,25 @@ double orc_energy_grad(const orc_model* m, const double* xyz, double* gx, double
                 gx[3 * (i0 + 1) + d] = gx[3 * (i0 + 1) + d] + eu - ev;
                 gx[3 * (i0 + 2) + d] = gx[3 * (i0 + 2) + d] + ev - ew;
                 gx[3 * (i0 + 3) + d] = gx[3 * (i0 + 3) + d] + ew;
+            }
+        }
+    }
+    /* FENE bonds: phi = k R^2 C_F ln(1 - x^2), x = (r - r0) / R, dphi/dr = -2 k R C_F x / (1 - x^2) */
+    if (m->k_fene != 0.0) {
+        for (int c = 0, o = 0; c < m->n_chains; o += m->chain_len[c], ++c) {
+            for (int l = o; l < o + m->chain_len[c] - 1; ++l) {
+                double d[3];
+                for (int q = 0; q < 3; ++q) d[q] = xyz[3 * (l + 1) + q] - xyz[3 * l + q];
+                double r = sqrt((d[0] * d[0] + d[1] * d[1]) + d[2] * d[2]);
+                double x = (r - m->fene_r0) / m->fene_R;
+                double cf = m->C_F[2 * m->seq[l] + m->seq[l + 1]];
+                E = E + (m->k_fene * (m->fene_R * m->fene_R)) * (cf * log(1.0 - x * x));
+                if (!gx) continue;
+                double dphi = -2.0 * m->k_fene * m->fene_R * cf * x / (1.0 - x * x);
+                for (int q = 0; q < 3; ++q) {
+                    gx[3 * (l + 1) + q] = gx[3 * (l + 1) + q] + dphi * d[q] / r;
+                    gx[3 * l + q] = gx[3 * l + q] - dphi * d[q] / r;
+                }
             }
         }
     }

@@ -40,18 +40,23 @@ typedef struct {
     double k_lj_intra;            /* kappa_LJ_INTRA */
     double k_lj_inter;            /* kappa_LJ_INTER */
     double C[4];                  /* C_LJ(s_i, s_j) at index 2*s_i + s_j (Eq. 1) */
+    double sphere_R;              /* > 0: steric spherical container about the origin (hard wall) */
+    double k_fene, fene_r0, fene_R;   /* FENE bond term of Eq. 2 (k_fene = 0: AB limit, rigid bonds) */
+    double C_F[4];                /* C_F(s_l, s_{l+1}) at index 2*s_l + s_{l+1} */
 } orc_model;
 
 /* Multicanonical set-up: energy bins, move mix and step sizes. */
 typedef struct {
     double e_min, bin_width;
     int32_t n_bins;
-    double p[4];                  /* probabilities of pivot, translation, rotation, crankshaft */
-    double amax[4];               /* pivot angle, translation step, rotation angle, crank angle */
+    double p[6];                  /* probabilities of pivot, translation, rotation, crankshaft,
+                                     bond-length change, spherical cap */
+    double amax[6];               /* pivot angle, translation step, rotation angle, crank angle,
+                                     bond-length step, cap angle */
     int32_t recompute_every;      /* full FP64 energy every this many sweeps (0 = never) */
 } orc_muca;
 
-enum { ORC_PIVOT = 0, ORC_TRANS = 1, ORC_ROT = 2, ORC_CRANK = 3 };
+enum { ORC_PIVOT = 0, ORC_TRANS = 1, ORC_ROT = 2, ORC_CRANK = 3, ORC_BOND = 4, ORC_CAP = 5 };
 
 typedef struct {
     int32_t type, chain, index, pad;
@@ -71,8 +76,10 @@ typedef struct {
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): out = philox(ctr, key). */
 void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
-/* Total energy, Eq. 2 summed per chain plus the inter-chain sum of Eq. 3.
- * terms (nullable) receives {bend, torsion, lj_intra, lj_inter}. */
+/* Total energy, Eq. 2 summed per chain plus the inter-chain sum of Eq. 3;
+ * +inf if a monomer is outside the spherical container or a bond outside the
+ * FENE range.  terms (nullable) receives {bend, torsion, lj_intra, lj_inter,
+ * fene}. */
 double orc_energy(const orc_model* m, const double* xyz, double* terms);
 
 /* Draw move number t of the walker with key `seed` (see orc_propose in the .c). */
@@ -101,7 +108,7 @@ int32_t orc_bin(const orc_muca* mu, double E);
  * (in/out), *E, *bin, *t.  hist[n_bins] (uint64, in/out) gets +1 per attempt.
  * force (nullable, [n_moves]): -1 = own decision, 0/1 = impose this decision
  * (used to replay another sampler's trajectory).  rec (nullable, [n_moves]).
- * stats (nullable, [12]): attempts[4], accepts[4], pair_evals, n_recompute,
+ * stats (nullable, [16]): attempts[6], accepts[6], pair_evals, n_recompute,
  * drift_max (as double bits), own_vs_forced_mismatches.
  * Returns 0, or -1 if the walker state is invalid (E out of range). */
 int orc_sweep_walker(const orc_model* m, const orc_muca* mu, const double* lnW,

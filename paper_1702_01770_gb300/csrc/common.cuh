@@ -38,17 +38,23 @@ struct SysDesc {
     double k_bend, k_tors, k_lj_intra, k_lj_inter;
     double C[4];
     double e_min, bin_width;
-    double p[4], amax[4];
-    uint64_t thr[4];      // move-type thresholds: type i if 2n+1 < thr[i] (n the 52-bit uniform), see propose_select
+    double p[PHAST_N_MOVES], amax[PHAST_N_MOVES];
+    uint64_t thr[PHAST_N_MOVES];   // move-type thresholds: type i if 2n+1 < thr[i] (n the 52-bit uniform), see propose_select
     int32_t last_type, type_mask, pad2[2];   // type_mask: bit i set when p[i] > 0
+    double sphere_R2;     // sphere_R * sphere_R of the steric container (0: none)
+    double k_fene, fene_r0, fene_R, fene_kR2;   // FENE term of Eq. 2; fene_kR2 = k_fene * (R * R)
+    double C_F[4];
     float C32[4];         // FP32 copies for the FP32 working precision
-    float L32, iL32, kin32, kout32, kbend32, ktors32, iw32, pad3;
-    float amax32[4];
+    float L32, iL32, kin32, kout32, kbend32, ktors32, iw32, sphere_R2_32;
+    float amax32[PHAST_N_MOVES], pad3[2];
+    float fene_r0_32, fene_iR32, fene_kR2_32, pad4;
+    float C_F32[4];
     int32_t chain_off[PHAST_MAX_CHAINS + 1];
     int32_t pad1[3];
     uint8_t seq[PHAST_MAX_MONOMERS];
     uint8_t chain_of[PHAST_MAX_MONOMERS];
     uint16_t n_a_before[PHAST_MAX_MONOMERS + 8];   // number of A monomers with index < j
+    int32_t pad5[2];
 };
 static_assert(sizeof(SysDesc) % 16 == 0, "SysDesc must be 16-byte sized for vector copies");
 
@@ -207,6 +213,16 @@ struct Proposal {
     uint32_t uz, uw;        // words of the acceptance uniform (block 2 z, w)
 };
 
+// Monomer or bond a move acts on, from block 0's last word: an interior
+// monomer 1..n-2 (pivot, crankshaft), a bond 0..n-2 (bond length), any
+// monomer 0..n-1 (spherical cap); 0 for whole-chain moves.
+__host__ __device__ __forceinline__ int move_index(int type, int n, uint32_t w) {
+    if (type == PHAST_PIVOT || type == PHAST_CRANK) return 1 + (int)(((uint64_t)w * (uint64_t)(n - 2)) >> 32);
+    if (type == PHAST_BOND) return (int)(((uint64_t)w * (uint64_t)(n - 1)) >> 32);
+    if (type == PHAST_CAP) return (int)(((uint64_t)w * (uint64_t)n) >> 32);
+    return 0;
+}
+
 // Selection part of move t (blocks 0-2): the type is the first one with p > 0
 // whose running probability sum exceeds the uniform (the last type with p > 0
 // catches the rounding remainder) -- compared exactly in integers, since
@@ -218,7 +234,7 @@ __device__ __forceinline__ void propose_select(const SysDesc& d, uint4 b0, uint4
     const uint64_t v = 2 * u52_bits(b0.x, b0.y) + 1;
     int type = d.last_type;
 #pragma unroll
-    for (int i = 3; i >= 0; --i)
+    for (int i = PHAST_N_MOVES - 1; i >= 0; --i)
         if (((d.type_mask >> i) & 1) && v < d.thr[i]) type = i;
     P->uz = b2.z;
     P->uw = b2.w;
@@ -226,8 +242,7 @@ __device__ __forceinline__ void propose_select(const SysDesc& d, uint4 b0, uint4
     P->type = type;
     P->chain = (int)(((uint64_t)b0.z * (uint64_t)d.n_chains) >> 32);
     int n = d.chain_off[P->chain + 1] - d.chain_off[P->chain];
-    P->index = (type == PHAST_PIVOT || type == PHAST_CRANK)
-                   ? 1 + (int)(((uint64_t)b0.w * (uint64_t)(n - 2)) >> 32) : 0;
+    P->index = move_index(type, n, b0.w);
     P->angle = 0.0;
     P->disp = make_double3(0.0, 0.0, 0.0);
     P->axis = make_double3(0.0, 0.0, 1.0);
@@ -235,7 +250,7 @@ __device__ __forceinline__ void propose_select(const SysDesc& d, uint4 b0, uint4
         double a = d.amax[PHAST_TRANS];
         P->disp = make_double3(xmul(sym_unit(b1.x, b1.y), a), xmul(sym_unit(b1.z, b1.w), a),
                                xmul(sym_unit(b2.x, b2.y), a));
-    } else {
+    } else {   // rotation angle, or the signed length step of a bond move
         P->angle = xmul(sym_unit(b1.x, b1.y), d.amax[type]);
     }
 }
@@ -247,7 +262,12 @@ __device__ __forceinline__ void moved_range(const SysDesc& d, int type, int chai
     int o = d.chain_off[chain], n = d.chain_off[chain + 1] - o;
     *fixed = -1;
     if (type == PHAST_TRANS || type == PHAST_ROT) { *lo = o; *hi = o + n - 1; return; }
-    if (type == PHAST_CRANK) { *lo = *hi = o + index; return; }
+    if (type == PHAST_CRANK || type == PHAST_CAP) { *lo = *hi = o + index; return; }
+    if (type == PHAST_BOND) {   // the shorter side of bond index (on a tie the tail)
+        if (index + 1 < n - 1 - index) { *lo = o; *hi = o + index; }
+        else { *lo = o + index + 1; *hi = o + n - 1; }
+        return;
+    }
     *fixed = o + index;
     if (index < n - 1 - index) { *lo = o; *hi = o + index - 1; }
     else { *lo = o + index + 1; *hi = o + n - 1; }
@@ -293,19 +313,56 @@ __device__ __forceinline__ double torsion_term(const Pos& pos, int o, int j) {
 // Local (bending + torsion) items a move changes.  Items 0..nb-1 are bends at
 // vertices vb0.., items nb.. are dihedrals starting at jt0..; returns the count.
 __device__ __forceinline__ void local_window(const SysDesc& d, int type, int chain, int index,
-                                             int* vb0, int* nb, int* jt0, int* nt) {
+                                             int* vb0, int* nb, int* jt0, int* nt, int* fb0, int* nf) {
     int n = d.chain_off[chain + 1] - d.chain_off[chain];
-    *nb = 0; *nt = 0; *vb0 = 0; *jt0 = 0;
+    *nb = 0; *nt = 0; *vb0 = 0; *jt0 = 0; *fb0 = 0; *nf = 0;
     if (type == PHAST_PIVOT) {
         *vb0 = index; *nb = 1;
         int a = max(index - 2, 0), b = min(index - 1, n - 4);
         *jt0 = a; *nt = max(b - a + 1, 0);
-    } else if (type == PHAST_CRANK) {
+    } else if (type == PHAST_CRANK || type == PHAST_CAP) {
         int a = max(index - 1, 1), b = min(index + 1, n - 2);
         *vb0 = a; *nb = max(b - a + 1, 0);
         int c = max(index - 3, 0), e = min(index, n - 4);
         *jt0 = c; *nt = max(e - c + 1, 0);
+        // a cap keeps the bond to its rotation centre; the other bond changes length
+        if (type == PHAST_CAP && d.k_fene != 0.0 && index >= 1 && index <= n - 2) { *fb0 = index; *nf = 1; }
+    } else if (type == PHAST_BOND) {   // bend and torsion angles keep; one bond's length changes
+        if (d.k_fene != 0.0) { *fb0 = index; *nf = 1; }
     }
+}
+
+// FENE term of bond l (monomers l, l+1 of the chain at o) without k_fene R^2:
+// C_F ln(1 - ((r - r0) / R)^2), +inf outside |r - r0| < R (FP64).
+template <class Pos>
+__device__ __forceinline__ double fene_term(const SysDesc& d, const Pos& pos, int o, int l) {
+    double3 a = pos(o + l), b = pos(o + l + 1);
+    double dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+    double r = sqrt((dx * dx + dy * dy) + dz * dz);
+    double x = (r - d.fene_r0) / d.fene_R;
+    double x2 = x * x;
+    if (!(x2 < 1.0)) return INFINITY;
+    return d.C_F[2 * d.seq[o + l] + d.seq[o + l + 1]] * log(1.0 - x2);
+}
+
+__device__ __forceinline__ double3 ld3(const double* p) { return make_double3(p[0], p[1], p[2]); }
+
+// Exact step of a bond-length move on bond l of the chain at o (n monomers):
+// the shorter side slides by +delta u (tail) or -delta u (head), u the unit
+// bond vector (x_{l+1} - x_l) / |x_{l+1} - x_l|; false for coincident monomers.
+__device__ __forceinline__ bool bond_step(const double* x64, int o, int n, int l, double delta, double3* step) {
+    const double3 a = ld3(x64 + 3 * (o + l)), b = ld3(x64 + 3 * (o + l + 1));
+    const double bx = xsub(b.x, a.x), by = xsub(b.y, a.y), bz = xsub(b.z, a.z);
+    const double len = xsqrt(xadd(xadd(xmul(bx, bx), xmul(by, by)), xmul(bz, bz)));
+    if (!(len > 1e-12)) return false;
+    const double dl = (l + 1 < n - 1 - l) ? -delta : delta;
+    *step = make_double3(xmul(dl, xdiv(bx, len)), xmul(dl, xdiv(by, len)), xmul(dl, xdiv(bz, len)));
+    return true;
+}
+
+// Steric container (hard wall about the origin): true if (x^2 + y^2) + z^2 <= R^2.
+__device__ __forceinline__ bool inside64(const SysDesc& d, double3 x) {
+    return !(d.sphere_R2 > 0.0) || xadd(xadd(xmul(x.x, x.x), xmul(x.y, x.y)), xmul(x.z, x.z)) <= d.sphere_R2;
 }
 
 // Lennard-Jones pair of Eq. 2/3 without its coupling: r^-12 - C r^-6 (FP64).

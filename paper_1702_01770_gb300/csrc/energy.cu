@@ -24,6 +24,9 @@ energy_kernel(const SysDesc d, int B, const double* __restrict__ xyz, double* __
         Slot<PT> s(smem + (size_t)w * L.bytes, L);
         build_working<32, PT>(d, x64, s, g);
         E = full_energy_working<32, PT>(d, s, g);
+        bool out = false;   // a monomer beyond the container's wall: infinite energy
+        for (int j = g.lane; j < d.N; j += 32) out |= !inside64(d, ld3(x64 + 3 * j));
+        if (__any_sync(g.mask, out)) E = INFINITY;
     }
     if (g.lane == 0) E_out[b] = E;
 }
@@ -51,20 +54,24 @@ delta_kernel(const SysDesc d, int B, const double* __restrict__ xyz, const phast
     P.disp32 = make_float3((float)P.disp.x, (float)P.disp.y, (float)P.disp.z);
     // a move outside the system (type, chain, interior index, amplitude) is
     // reported as NaN instead of being applied
-    bool valid = P.type >= 0 && P.type <= 3 && P.chain >= 0 && P.chain < d.n_chains;
+    bool valid = P.type >= 0 && P.type < PHAST_N_MOVES && P.chain >= 0 && P.chain < d.n_chains;
     if (valid) {
         const int n = d.chain_off[P.chain + 1] - d.chain_off[P.chain];
         if (P.type == PHAST_PIVOT || P.type == PHAST_CRANK) valid = P.index >= 1 && P.index <= n - 2;
-        if (P.type != PHAST_TRANS) valid = valid && fabs(P.angle) <= PHAST_MAX_ANGLE;
-        else valid = isfinite(P.disp.x) && isfinite(P.disp.y) && isfinite(P.disp.z);
-        if (P.type == PHAST_PIVOT || P.type == PHAST_ROT)
+        if (P.type == PHAST_BOND) valid = P.index >= 0 && P.index <= n - 2 && isfinite(P.angle);
+        else if (P.type == PHAST_CAP) valid = P.index >= 0 && P.index <= n - 1;
+        if (P.type == PHAST_TRANS) valid = isfinite(P.disp.x) && isfinite(P.disp.y) && isfinite(P.disp.z);
+        else if (P.type != PHAST_BOND) valid = valid && fabs(P.angle) <= PHAST_MAX_ANGLE;
+        if (P.type == PHAST_PIVOT || P.type == PHAST_ROT || P.type == PHAST_CAP)
             valid = valid && isfinite(P.axis.x) && isfinite(P.axis.y) && isfinite(P.axis.z);
     }
     if (!valid) P.type = PHAST_TRANS, P.chain = 0, P.index = 0;
     const MoveSet M = move_set(d, P.type, P.chain, P.index);
     double dE = __longlong_as_double(0x7ff8000000000000ll);   // NaN for a degenerate or invalid move
     const bool ok = valid && make_new_positions<32, PT>(d, x64, P, M, s, g);
-    if (ok) {
+    const bool wall = ok && !container_ok<32, PT>(d, x64, P, M, s, g, true, 0ull, 0ull);
+    if (wall) dE = INFINITY;   // beyond the container's wall
+    if (ok && !wall) {
         double part = (double)local_delta<32, PT>(d, P, M, s, g);
         if constexpr (sizeof(PT) == 4) {
             const DF q = d.box_L > 0.0 ? pair_delta32<32, 3, true>(d, M, P.chain, s, g)

@@ -112,7 +112,11 @@ energy_grad_kernel(const SysDesc d, int B, const double* __restrict__ xyz, doubl
             gp[3] -= t;
             E -= d.k_tors * t;
         }
+        if (d.k_fene != 0.0)
+            for (int l = g.lane; l <= n - 2; l += 32) E += d.fene_kR2 * (double)fene_w<PT>(d, pos, o, l);
     }
+    bool out = false;   // a monomer beyond the container's wall: infinite energy
+    for (int j = g.lane; j < d.N; j += 32) out |= !inside64(d, ld3(x64 + 3 * j));
     // each lane's monomers: Lennard-Jones partners, then its local terms
     for (int i = g.lane; i < d.N; i += 32) {
         const P4<PT> a = s.r[i];
@@ -171,6 +175,21 @@ energy_grad_kernel(const SysDesc d, int B, const double* __restrict__ xyz, doubl
                 gy -= f.ktors() * t.y;
                 gz -= f.ktors() * t.z;
             }
+            if (d.k_fene != 0.0) {   // bonds of i: d/dr [k R^2 C_F ln(1 - x^2)] = -2 k R C_F x / (1 - x^2)
+                for (int l = li - 1; l <= li; ++l) {
+                    if (l < 0 || l > n - 2) continue;
+                    const V3<PT> b = sub3(s.r[o + l + 1], s.r[o + l]);
+                    const PT r = sqrt(dot3(b, b));
+                    const PT R = (PT)d.fene_R;
+                    const PT x = (r - (PT)d.fene_r0) / R;
+                    const PT cf = (PT)d.C_F[2 * d.seq[o + l] + d.seq[o + l + 1]];
+                    const PT dphi = (PT)(-2.0 * d.k_fene) * R * cf * x / ((PT)1 - x * x);
+                    const PT sg = (l == li) ? (PT)-1 : (PT)1;   // i is the bond's first or second monomer
+                    gx += sg * dphi * b.x / r;
+                    gy += sg * dphi * b.y / r;
+                    gz += sg * dphi * b.z / r;
+                }
+            }
             double* out = grad_xyz + ((size_t)b * d.N + i) * 3;
             out[0] = (double)gx;
             out[1] = (double)gy;
@@ -178,6 +197,7 @@ energy_grad_kernel(const SysDesc d, int B, const double* __restrict__ xyz, doubl
         }
     }
     E = g.sum(E);
+    if (__any_sync(g.mask, out)) E = INFINITY;
     for (int q = 0; q < 5; ++q) gp[q] = g.sum(gp[q]);
     if (g.lane == 0) {
         if (E_out) E_out[b] = E;

@@ -76,7 +76,7 @@ __device__ __forceinline__ DF group_sum_df(DF v, const Group<TPW>& g) {
 // An accepted move waiting for its exact FP64 replay (FP32 mode).
 // Its exact amplitude and step are regenerated from the counter-based stream.
 struct QEntry {
-    int32_t packed;      // type | chain << 2 | index << 8
+    int32_t packed;      // type | chain << 3 | index << 9
     int32_t attempt;     // winning Marsaglia attempt
     uint64_t t;          // move index (the walker stream's counter)
 };
@@ -121,7 +121,6 @@ struct Slot {
           queue((QEntry*)(p + L.q_off)), st((phast_walker_stats*)(p + L.st_off)) {}
 };
 
-__device__ __forceinline__ double3 ld3(const double* p) { return make_double3(p[0], p[1], p[2]); }
 
 // Force-field constants in the working precision (FP32 copies live in the descriptor).
 template <typename PT> struct FF;
@@ -134,6 +133,7 @@ template <> struct FF<float> {
     __device__ __forceinline__ float kout() const { return d.kout32; }
     __device__ __forceinline__ float kbend() const { return d.kbend32; }
     __device__ __forceinline__ float ktors() const { return d.ktors32; }
+    __device__ __forceinline__ float kfene() const { return d.fene_kR2_32; }
 };
 template <> struct FF<double> {
     const SysDesc& d;
@@ -144,6 +144,7 @@ template <> struct FF<double> {
     __device__ __forceinline__ double kout() const { return d.k_lj_inter; }
     __device__ __forceinline__ double kbend() const { return d.k_bend; }
     __device__ __forceinline__ double ktors() const { return d.k_tors; }
+    __device__ __forceinline__ double kfene() const { return d.fene_kR2; }
 };
 
 // Minimum-imaged difference of the origins of chains a and b, in the working precision.
@@ -258,20 +259,19 @@ __device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, u
         const uint64_t v = 2 * u52_bits(w0x, w0y) + 1;
         int type = d.last_type;
 #pragma unroll
-        for (int i = 3; i >= 0; --i)
+        for (int i = PHAST_N_MOVES - 1; i >= 0; --i)
             if (((d.type_mask >> i) & 1) && v < d.thr[i]) type = i;
         P.type = type;
         P.chain = (int)(((uint64_t)w0z * (uint64_t)d.n_chains) >> 32);
         const int n = d.chain_off[P.chain + 1] - d.chain_off[P.chain];
-        P.index = (type == PHAST_PIVOT || type == PHAST_CRANK) ? 1 + (int)(((uint64_t)w0w * (uint64_t)(n - 2)) >> 32)
-                                                               : 0;
+        P.index = move_index(type, n, w0w);
         const float am = d.amax32[type];
         const float a0 = sym_unit32(w1x) * am;
         if (type == PHAST_TRANS) P.disp32 = make_float3(a0, sym_unit32(w1z) * am, sym_unit32(w2x) * am);
         else P.angle32 = a0;
     }
     P.attempt = -1;
-    if (P.type == PHAST_PIVOT || P.type == PHAST_ROT) {
+    if (P.type == PHAST_PIVOT || P.type == PHAST_ROT || P.type == PHAST_CAP) {
         const unsigned gm = TPW == 32 ? 0xffffffffu : ((1u << TPW) - 1u);
         uint4 mine = blk;
         int round = 0;
@@ -353,9 +353,12 @@ __device__ __forceinline__ MoveSet move_set(const SysDesc& d, int type, int chai
     MoveSet M;
     int fixed;
     moved_range(d, type, chain, index, &M.lo, &M.hi, &fixed);
+    // partners left out: the pivot (its distances to the rotated side keep) and
+    // the bonded neighbours of the moved range inside the chain
+    const int o = d.chain_off[chain], e = d.chain_off[chain + 1] - 1;
     M.ex0 = fixed;
-    M.ex1 = (type == PHAST_CRANK) ? M.lo - 1 : -1;
-    M.ex2 = (type == PHAST_CRANK) ? M.hi + 1 : -1;
+    M.ex1 = (type != PHAST_PIVOT && M.lo - 1 >= o) ? M.lo - 1 : -1;
+    M.ex2 = (type != PHAST_PIVOT && M.hi + 1 <= e) ? M.hi + 1 : -1;
     M.a_lo = d.n_a_before[M.lo];
     M.n_a = d.n_a_before[M.hi + 1] - M.a_lo;
     return M;
@@ -372,16 +375,15 @@ __device__ __forceinline__ int rec_slot(const SysDesc& d, const MoveSet& M, int 
 // Pair evaluations of a move between different chains (2 per pair).
 __device__ __forceinline__ uint64_t move_pair_evals_inter(const SysDesc& d, int type, int chain, const MoveSet& M) {
     const int nc = d.chain_off[chain + 1] - d.chain_off[chain];
-    const int m = (type == PHAST_CRANK) ? 1 : M.hi - M.lo + 1;
+    const int m = M.hi - M.lo + 1;
     return 2ull * m * (d.N - nc);
 }
 
 // Pair evaluations a move costs (2 per changed Lennard-Jones pair).
 __device__ __forceinline__ uint64_t move_pair_evals(const SysDesc& d, int type, const MoveSet& M) {
-    int m = M.hi - M.lo + 1;
-    if (type == PHAST_PIVOT) return 2ull * m * (d.N - m - 1);
-    if (type == PHAST_CRANK) return 2ull * (d.N - 3);
-    return 2ull * m * (d.N - m);
+    const int m = M.hi - M.lo + 1;
+    const int excluded = (M.ex0 >= 0) + (M.ex1 >= 0) + (M.ex2 >= 0);
+    return 2ull * m * (d.N - m - excluded);
 }
 
 // Lane 0 builds the move's exact centre and rotation (FP64, bit-reproducible)
@@ -394,11 +396,19 @@ __device__ bool prepare_exact(const SysDesc& d, const double* x64, const Proposa
     const int c = P.chain, o = d.chain_off[c], n = d.chain_off[c + 1] - o;
     double3 rot_center = make_double3(0.0, 0.0, 0.0);
     if (P.type == PHAST_ROT) rot_center = centroid_tree<TPW>(x64, o, n, g);
-    if (P.type != PHAST_TRANS && g.lane == 0) {
+    if (P.type == PHAST_BOND && g.lane == 0) {   // the slide of the moved side
+        double3 step = make_double3(0.0, 0.0, 0.0);
+        s.geo[12] = bond_step(x64, o, n, P.index, P.angle, &step) ? 1.0 : 0.0;
+        s.geo[13] = step.x;
+        s.geo[14] = step.y;
+        s.geo[15] = step.z;
+    } else if (P.type != PHAST_TRANS && g.lane == 0) {
         double3 axis = axis64, center;
         double ok = 1.0;
         if (P.type == PHAST_PIVOT) {
             center = ld3(x64 + 3 * (o + P.index));
+        } else if (P.type == PHAST_CAP) {   // about the bonded neighbour i-1 (monomer 1 for i = 0)
+            center = ld3(x64 + 3 * (o + (P.index > 0 ? P.index - 1 : 1)));
         } else if (P.type == PHAST_ROT) {
             center = rot_center;
         } else {   // crankshaft about the axis through monomers i-1 and i+1
@@ -429,6 +439,8 @@ __device__ bool prepare_exact(const SysDesc& d, const double* x64, const Proposa
 __device__ __forceinline__ double3 exact_position(const Proposal& P, const double* geo, double3 x) {
     if (P.type == PHAST_TRANS)
         return make_double3(xadd(x.x, P.disp.x), xadd(x.y, P.disp.y), xadd(x.z, P.disp.z));
+    if (P.type == PHAST_BOND)
+        return make_double3(xadd(x.x, geo[13]), xadd(x.y, geo[14]), xadd(x.z, geo[15]));
     Rot3 R;
 #pragma unroll
     for (int k = 0; k < 9; ++k) R.m[k] = geo[k];
@@ -481,8 +493,18 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
         return true;
     } else {
         float4* mv = reinterpret_cast<float4*>(s.newr);
-        if (P.type == PHAST_TRANS) {
-            const float dx = P.disp32.x, dy = P.disp32.y, dz = P.disp32.z;
+        if (P.type == PHAST_TRANS || P.type == PHAST_BOND) {
+            float dx = P.disp32.x, dy = P.disp32.y, dz = P.disp32.z;
+            if (P.type == PHAST_BOND) {   // slide along the FP32 unit bond vector
+                const P4<PT> a = s.r[o + P.index], b = s.r[o + P.index + 1];
+                const float bx = b.x - a.x, by = b.y - a.y, bz = b.z - a.z;
+                const float len = sqrtf(bx * bx + by * by + bz * bz);
+                if (!(len > 1e-12f)) return false;
+                const float dl = (P.index + 1 < n - 1 - P.index) ? -P.angle32 : P.angle32;
+                dx = dl * (bx / len);
+                dy = dl * (by / len);
+                dz = dl * (bz / len);
+            }
             for (int q = g.lane; q < m; q += TPW) {
                 const P4<PT> w = s.r[M.lo + q];
                 const float nx = w.x + dx, ny = w.y + dy, nz = w.z + dz;
@@ -492,8 +514,8 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
             }
         } else {
             float kx = P.axis32.x, ky = P.axis32.y, kz = P.axis32.z, cx, cy, cz;
-            if (P.type == PHAST_PIVOT) {
-                const P4<PT> p = s.r[o + P.index];
+            if (P.type == PHAST_PIVOT || P.type == PHAST_CAP) {
+                const P4<PT> p = s.r[o + (P.type == PHAST_PIVOT ? P.index : (P.index > 0 ? P.index - 1 : 1))];
                 cx = p.x; cy = p.y; cz = p.z;
             } else if (P.type == PHAST_ROT) {
                 cx = cy = cz = 0.0f;
@@ -539,6 +561,52 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
     }
 }
 
+// Steric container: every moved monomer's trial position inside the sphere,
+// decided as the FP64 test (x^2 + y^2) + z^2 <= R^2 on the exact position.
+// FP32 mode estimates |origin + r|^2 from the trial record (error far below
+// 1e-5 R^2) and builds the exact positions only when a monomer is that close
+// to the wall.  The same value on every lane of the group.
+// exact: P carries the exact FP64 move (else it is regenerated from the
+// walker's stream, key seed and move index t, as the replay does).
+template <int TPW, typename PT>
+__device__ bool container_ok(const SysDesc& d, const double* x64, const Proposal& P, const MoveSet& M, Slot<PT>& s,
+                             const Group<TPW>& g, bool exact, uint64_t seed, uint64_t t) {
+    if (!(d.sphere_R2 > 0.0)) return true;
+    const int m = M.hi - M.lo + 1;
+    const unsigned gm = TPW == 32 ? 0xffffffffu : ((1u << TPW) - 1u);
+    bool out = false, unsure = false;
+    if constexpr (sizeof(PT) == 8) {
+        for (int q = g.lane; q < m; q += TPW)
+            out |= !inside64(d, make_double3(s.new64[3 * q], s.new64[3 * q + 1], s.new64[3 * q + 2]));
+    } else {
+        const float4* mv = reinterpret_cast<const float4*>(s.newr);
+        const int c = P.chain;
+        const float ox = (float)s.orig[3 * c], oy = (float)s.orig[3 * c + 1], oz = (float)s.orig[3 * c + 2];
+        const float R2 = d.sphere_R2_32, band = 1e-5f * R2;
+        for (int q = g.lane; q < m; q += TPW) {
+            const int k = rec_slot(d, M, M.lo + q);
+            const float4 A = mv[2 * k], B = mv[2 * k + 1];
+            const float x = ox + A.y, y = oy + A.w, z = oz + B.y;
+            const float r2 = x * x + y * y + z * z;
+            out |= r2 > R2 + band;
+            unsure |= fabsf(r2 - R2) <= band;
+        }
+        if ((__ballot_sync(g.mask, unsure) >> g.base) & gm) {   // near the wall: the exact positions decide
+            Proposal E = P;
+            if (!exact) {
+                propose_select(d, stream_block(seed, t, 0u), stream_block(seed, t, 1u), stream_block(seed, t, 2u), &E);
+                if (E.type == PHAST_PIVOT || E.type == PHAST_ROT || E.type == PHAST_CAP)
+                    E.axis = exact_axis(seed, t, P.attempt);
+            }
+            const bool ok_geo = prepare_exact<TPW, PT>(d, x64, E, E.axis, s, g);
+            if (ok_geo)
+                for (int q = g.lane; q < m; q += TPW)
+                    out |= !inside64(d, exact_position(E, s.geo, ld3(x64 + 3 * (M.lo + q))));
+        }
+    }
+    return ((__ballot_sync(g.mask, out) >> g.base) & gm) == 0u;
+}
+
 // Commit an accepted move in FP64 mode: the exact positions computed for the
 // trial become the master coordinates and the working copy.
 template <int TPW>
@@ -561,7 +629,7 @@ __device__ void accept_move32(const SysDesc& d, const Proposal& P, uint64_t t, c
                               const Group<TPW>& g, int count) {
     if (g.lane == 0) {
         QEntry e;
-        e.packed = P.type | (P.chain << 2) | (P.index << 8);
+        e.packed = P.type | (P.chain << 3) | (P.index << 9);
         e.attempt = P.attempt;
         e.t = t;
         s.queue[count] = e;
@@ -600,52 +668,55 @@ __device__ __noinline__ void flush_queue(const SysDesc& d, double* x64, uint64_t
         const QEntry e = s.queue[g.lane];
         Proposal Q;
         propose_select(d, stream_block(seed, e.t, 0u), stream_block(seed, e.t, 1u), stream_block(seed, e.t, 2u), &Q);
-        if (Q.type == PHAST_PIVOT || Q.type == PHAST_ROT) {
+        if (Q.type == PHAST_PIVOT || Q.type == PHAST_ROT || Q.type == PHAST_CAP) {
             const double3 ax = exact_axis(seed, e.t, e.attempt);
             double sn, cs;
             taylor_sincos(Q.angle, &sn, &cs);
             Rl = rodrigues(ax.x, ax.y, ax.z, sn, cs);
         } else if (Q.type == PHAST_TRANS) {
             dl = Q.disp;
-        } else {
+        } else {   // crankshaft angle, bond-length step
             dl.x = Q.angle;
         }
     }
     for (int k = 0; k < count; ++k) {
         const QEntry e = s.queue[k];
         Proposal P;
-        P.type = e.packed & 3;
-        P.chain = (e.packed >> 2) & 63;
-        P.index = e.packed >> 8;
+        P.type = e.packed & 7;
+        P.chain = (e.packed >> 3) & 63;
+        P.index = e.packed >> 9;
         P.attempt = e.attempt;
         P.angle = 0.0;
         P.disp = make_double3(0.0, 0.0, 0.0);
         P.axis = make_double3(0.0, 0.0, 1.0);
         if (P.type == PHAST_TRANS) P.disp = make_double3(g.bcastd(dl.x, k), g.bcastd(dl.y, k), g.bcastd(dl.z, k));
-        if (P.type == PHAST_CRANK) P.angle = g.bcastd(dl.x, k);
+        if (P.type == PHAST_CRANK || P.type == PHAST_BOND) P.angle = g.bcastd(dl.x, k);
         const MoveSet M = move_set(d, P.type, P.chain, P.index);
         const int m = M.hi - M.lo + 1;
         const int o = d.chain_off[P.chain], n = d.chain_off[P.chain + 1] - o;
         Rot3 R;
         double3 center = make_double3(0.0, 0.0, 0.0);
         bool ok = true;
-        if (P.type == PHAST_PIVOT || P.type == PHAST_ROT) {
+        double3 step = P.disp;
+        if (P.type == PHAST_PIVOT || P.type == PHAST_ROT || P.type == PHAST_CAP) {
 #pragma unroll
             for (int q = 0; q < 9; ++q) R.m[q] = g.bcastd(Rl.m[q], k);
-            center = (P.type == PHAST_PIVOT) ? ld3(x64 + 3 * (o + P.index)) : centroid_tree<TPW>(x64, o, n, g);
-        } else if (P.type == PHAST_CRANK) {   // its axis depends on the coordinates: built now
+            if (P.type == PHAST_ROT) center = centroid_tree<TPW>(x64, o, n, g);
+            else center = ld3(x64 + 3 * (o + (P.type == PHAST_PIVOT ? P.index : (P.index > 0 ? P.index - 1 : 1))));
+        } else if (P.type == PHAST_CRANK || P.type == PHAST_BOND) {   // axis / slide depend on the coordinates
             ok = prepare_exact<TPW, float>(d, x64, P, P.axis, s, g);
 #pragma unroll
             for (int q = 0; q < 9; ++q) R.m[q] = s.geo[q];
             center = make_double3(s.geo[9], s.geo[10], s.geo[11]);
+            step = make_double3(s.geo[13], s.geo[14], s.geo[15]);
         }
         if (ok) {
             for (int q = g.lane; q < m; q += TPW) {
                 const int j = M.lo + q;
                 const double3 x = ld3(x64 + 3 * j);
                 double3 y;
-                if (P.type == PHAST_TRANS)
-                    y = make_double3(xadd(x.x, P.disp.x), xadd(x.y, P.disp.y), xadd(x.z, P.disp.z));
+                if (P.type == PHAST_TRANS || P.type == PHAST_BOND)
+                    y = make_double3(xadd(x.x, step.x), xadd(x.y, step.y), xadd(x.z, step.z));
                 else
                     y = rotate_about(R, center, x);
                 x64[3 * j + 0] = y.x;
@@ -656,7 +727,7 @@ __device__ __noinline__ void flush_queue(const SysDesc& d, double* x64, uint64_t
         g.sync();
     }
     uint32_t touched = 0;   // only the chains the replayed moves changed
-    for (int k = 0; k < count; ++k) touched |= 1u << ((s.queue[k].packed >> 2) & 63);
+    for (int k = 0; k < count; ++k) touched |= 1u << ((s.queue[k].packed >> 3) & 63);
     for (int j = g.lane; j < d.N; j += TPW) {
         const int c = d.chain_of[j];
         if (!((touched >> c) & 1)) continue;
@@ -700,14 +771,34 @@ __device__ __forceinline__ PT torsion_w(const Pos& pos, int o, int j) {
     return n12 * rsqrt_w(n11 * n22);
 }
 
+// FENE term of bond l in the working precision without k_fene R^2:
+// C_F ln(1 - ((r - r0) / R)^2), +inf outside |r - r0| < R.
+template <typename PT, class Pos>
+__device__ __forceinline__ PT fene_w(const SysDesc& d, const Pos& pos, int o, int l) {
+    const P4<PT> a = pos(o + l), b = pos(o + l + 1);
+    const PT dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+    const PT r = sqrt(dx * dx + dy * dy + dz * dz);
+    if constexpr (sizeof(PT) == 8) {
+        const double x = (r - d.fene_r0) / d.fene_R;
+        const double x2 = x * x;
+        if (!(x2 < 1.0)) return INFINITY;
+        return d.C_F[2 * d.seq[o + l] + d.seq[o + l + 1]] * log(1.0 - x2);
+    } else {
+        const float x = (r - d.fene_r0_32) * d.fene_iR32;
+        const float x2 = x * x;
+        if (!(x2 < 1.0f)) return INFINITY;
+        return d.C_F32[2 * d.seq[o + l] + d.seq[o + l + 1]] * log1pf(-x2);
+    }
+}
+
 // This lane's share of the bending/torsion change, in the working precision.
 template <int TPW, typename PT>
 __device__ PT local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M, const Slot<PT>& s,
                               const Group<TPW>& g) {
-    int vb0, nb, jt0, nt;
-    local_window(d, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt);
+    int vb0, nb, jt0, nt, fb0, nf;
+    local_window(d, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt, &fb0, &nf);
     const int o = d.chain_off[P.chain];
-    const int items = 2 * (nb + nt);
+    const int items = 2 * (nb + nt + nf);
     PT part = (PT)0;
     for (int it = g.lane; it < items; it += TPW) {
         const bool after = it & 1;
@@ -728,7 +819,8 @@ __device__ PT local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M,
         };
         const FF<PT> f{d};
         const PT term = (k < nb) ? f.kbend() * bend_w<PT>(pos, o, vb0 + k)
-                                 : -f.ktors() * torsion_w<PT>(pos, o, jt0 + (k - nb));
+                      : (k < nb + nt) ? -f.ktors() * torsion_w<PT>(pos, o, jt0 + (k - nb))
+                                      : f.kfene() * fene_w<PT>(d, pos, o, fb0 + (k - nb - nt));
         part += after ? term : -term;
     }
     return part;
@@ -984,11 +1076,15 @@ template <int TPW>
 __device__ double full_energy64(const SysDesc& d, const double* x64, const Group<TPW>& g) {
     double part = 0.0;
     auto pos = [&](int j) -> double3 { return ld3(x64 + 3 * j); };
+    bool out = false;   // a monomer outside the steric container: infinite energy
     for (int c = 0; c < d.n_chains; ++c) {
         int o = d.chain_off[c], n = d.chain_off[c + 1] - o;
         for (int k = 1 + g.lane; k <= n - 2; k += TPW) part += d.k_bend * bend_term(pos, o, k);
         for (int j = g.lane; j <= n - 4; j += TPW) part -= d.k_tors * torsion_term(pos, o, j);
+        if (d.k_fene != 0.0)
+            for (int l = g.lane; l <= n - 2; l += TPW) part += d.fene_kR2 * fene_term(d, pos, o, l);
     }
+    for (int j = g.lane; j < d.N; j += TPW) out |= !inside64(d, pos(j));
     for (int i = 0; i < d.N; ++i) {
         const double3 xi = pos(i);
         const int ci = d.chain_of[i], si = d.seq[i];
@@ -1006,7 +1102,8 @@ __device__ double full_energy64(const SysDesc& d, const double* x64, const Group
             part += (ci == cj ? d.k_lj_intra : d.k_lj_inter) * e;
         }
     }
-    return g.sum(part);
+    const double E = g.sum(part);
+    return __any_sync(g.mask, out) ? INFINITY : E;
 }
 
 // Full energy with the Lennard-Jones pairs in the working precision (from the
@@ -1019,6 +1116,8 @@ __device__ double full_energy_working(const SysDesc& d, const Slot<PT>& s, const
         int o = d.chain_off[c], n = d.chain_off[c + 1] - o;
         for (int k = 1 + g.lane; k <= n - 2; k += TPW) part += (double)((PT)d.k_bend * bend_w<PT>(pos, o, k));
         for (int j = g.lane; j <= n - 4; j += TPW) part -= (double)((PT)d.k_tors * torsion_w<PT>(pos, o, j));
+        if (d.k_fene != 0.0)
+            for (int l = g.lane; l <= n - 2; l += TPW) part += d.fene_kR2 * (double)fene_w<PT>(d, pos, o, l);
     }
     const PT L = (PT)d.box_L, iL = (PT)d.inv_L;
     for (int i = 0; i < d.N; ++i) {

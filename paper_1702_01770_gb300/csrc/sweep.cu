@@ -137,11 +137,14 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         const Proposal P = propose_group<TPW, PT>(sd, seed, t, blk, g);
         const MoveSet M = move_set(sd, P.type, P.chain, P.index);
         const bool ok = make_new_positions<TPW, PT>(sd, x64, P, M, slot, g);
+        // a trial position beyond the container's wall: infinite energy, not evaluated
+        const bool wall = ok && !container_ok<TPW, PT>(sd, x64, P, M, slot, g, sizeof(PT) == 8, seed, t);
+        const bool eval = ok && !wall;
         DF dE32{0.0f, 0.0f};
         double dE64 = 0.0;
         if constexpr (sizeof(PT) == 4) {   // this lane's share in double-float, the group total on every lane
             DF part{0.0f, 0.0f};
-            if (ok) {
+            if (eval) {
                 part = sd.box_L > 0.0 ? pair_delta32<TPW, 3, true>(sd, M, P.chain, slot, g)
                                       : pair_delta32<TPW, 3, false>(sd, M, P.chain, slot, g);
                 part = df_add(part, DF{local_delta<TPW, PT>(sd, P, M, slot, g), 0.0f});
@@ -149,10 +152,10 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
             dE32 = group_sum_df<TPW>(part, g);
         } else {
             double part = 0.0;
-            if (ok) part = local_delta<TPW, PT>(sd, P, M, slot, g) + pair_delta<TPW, PT, 4>(sd, M, P.chain, slot, g);
+            if (eval) part = local_delta<TPW, PT>(sd, P, M, slot, g) + pair_delta<TPW, PT, 4>(sd, M, P.chain, slot, g);
             dE64 = g.sum(part);
         }
-        const bool finite = ok && (sizeof(PT) == 4 ? (isfinite(dE32.hi) && isfinite(dE32.lo)) : isfinite(dE64));
+        const bool finite = eval && (sizeof(PT) == 4 ? (isfinite(dE32.hi) && isfinite(dE32.lo)) : isfinite(dE64));
         int b_new = -1;
         if (finite) b_new = sizeof(PT) == 4 ? bin_after(sd, E, erel, dE32) : bin_of(sd, E + dE64);
         const double lnw_new = __ldg(lnW + (b_new >= 0 ? b_new : bin));
@@ -179,7 +182,8 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
             if (tracing) {
                 phast_trace tr;
                 tr.dE = !ok ? __longlong_as_double(0x7ff8000000000000ll)
-                            : (sizeof(PT) == 4 ? (double)dE32.hi + (double)dE32.lo : dE64);
+                      : wall ? INFINITY
+                             : (sizeof(PT) == 4 ? (double)dE32.hi + (double)dE32.lo : dE64);
                 tr.bin_after = bin;
                 tr.accepted = (int32_t)acc;
                 a.trace[(int64_t)w_local * n_moves + it] = tr;
@@ -294,7 +298,12 @@ __device__ double block_full_energy64(const SysDesc& d, const double* x64, doubl
         int o = d.chain_off[c], n = d.chain_off[c + 1] - o;
         for (int k = 1 + threadIdx.x; k <= n - 2; k += blockDim.x) part += d.k_bend * bend_term(pos, o, k);
         for (int j = threadIdx.x; j <= n - 4; j += blockDim.x) part -= d.k_tors * torsion_term(pos, o, j);
+        if (d.k_fene != 0.0)
+            for (int l = threadIdx.x; l <= n - 2; l += blockDim.x) part += d.fene_kR2 * fene_term(d, pos, o, l);
     }
+    int out = 0;   // a monomer beyond the container's wall: infinite energy
+    for (int j = threadIdx.x; j < d.N; j += blockDim.x) out |= !inside64(d, pos(j));
+    out = __syncthreads_or(out);
     for (int i = 0; i < d.N; ++i) {
         const double3 xi = pos(i);
         const int ci = d.chain_of[i];
@@ -312,14 +321,15 @@ __device__ double block_full_energy64(const SysDesc& d, const double* x64, doubl
                     lj64(dx * dx + dy * dy + dz * dz, d.C[2 * d.seq[i] + d.seq[j]]);
         }
     }
-    return block_sum(part, red);
+    const double E = block_sum(part, red);
+    return out ? INFINITY : E;
 }
 
 __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepArgs a, int W_total) {
     __shared__ __align__(16) SysDesc sd;
     __shared__ double red[32];
     __shared__ Proposal sP;
-    __shared__ double sR[9], sC[3];
+    __shared__ double sR[9], sC[3], sD[3];
     __shared__ int s_ok, s_acc;
     const int gw = blockIdx.x;
     if (gw >= W_total) return;
@@ -349,7 +359,7 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
         if (threadIdx.x == 0) {   // proposal, serial Marsaglia, centre and rotation
             Proposal P;
             propose_select(sd, stream_block(seed, t, 0), stream_block(seed, t, 1), stream_block(seed, t, 2), &P);
-            if (P.type == PHAST_PIVOT || P.type == PHAST_ROT) {
+            if (P.type == PHAST_PIVOT || P.type == PHAST_ROT || P.type == PHAST_CAP) {
                 double3 ax = make_double3(0.0, 0.0, 1.0);
                 for (int j = 0; j < PHAST_MARSAGLIA_TRIES; ++j)
                     if (marsaglia_try(stream_block(seed, t, 3u + j), &ax)) break;
@@ -357,9 +367,13 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
             }
             const int o = sd.chain_off[P.chain], n = sd.chain_off[P.chain + 1] - o;
             int ok = 1;
-            double3 center = make_double3(0, 0, 0), axis = P.axis;
+            double3 center = make_double3(0, 0, 0), axis = P.axis, step = P.disp;
             if (P.type == PHAST_PIVOT) {
                 center = ld3(x64 + 3 * (o + P.index));
+            } else if (P.type == PHAST_CAP) {
+                center = ld3(x64 + 3 * (o + (P.index > 0 ? P.index - 1 : 1)));
+            } else if (P.type == PHAST_BOND) {
+                ok = bond_step(x64, o, n, P.index, P.angle, &step) ? 1 : 0;
             } else if (P.type == PHAST_ROT) {
                 center = centroid_serial(x64, o, n);
             } else if (P.type == PHAST_CRANK) {
@@ -371,13 +385,14 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
                 else axis = make_double3(xdiv(ex, len), xdiv(ey, len), xdiv(ez, len));
                 center = p0;
             }
-            if (P.type != PHAST_TRANS && ok) {
+            if (P.type != PHAST_TRANS && P.type != PHAST_BOND && ok) {
                 double sn, cs;
                 taylor_sincos(P.angle, &sn, &cs);
                 Rot3 R = rodrigues(axis.x, axis.y, axis.z, sn, cs);
                 for (int k = 0; k < 9; ++k) sR[k] = R.m[k];
             }
             sC[0] = center.x; sC[1] = center.y; sC[2] = center.z;
+            sD[0] = step.x; sD[1] = step.y; sD[2] = step.z;
             sP = P;
             s_ok = ok;
         }
@@ -387,24 +402,30 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
         const int m = M.hi - M.lo + 1;
         const bool ok = s_ok;
         double dE = __longlong_as_double(0x7ff8000000000000ll);
+        int wall = 0;
         if (ok) {
             Rot3 R;
             for (int k = 0; k < 9; ++k) R.m[k] = sR[k];
-            const double3 center = make_double3(sC[0], sC[1], sC[2]);
+            const double3 center = make_double3(sC[0], sC[1], sC[2]), step = make_double3(sD[0], sD[1], sD[2]);
+            int out = 0;
             for (int q = threadIdx.x; q < m; q += blockDim.x) {
                 const double3 x = ld3(x64 + 3 * (M.lo + q));
-                double3 y = (P.type == PHAST_TRANS)
-                    ? make_double3(xadd(x.x, P.disp.x), xadd(x.y, P.disp.y), xadd(x.z, P.disp.z))
+                double3 y = (P.type == PHAST_TRANS || P.type == PHAST_BOND)
+                    ? make_double3(xadd(x.x, step.x), xadd(x.y, step.y), xadd(x.z, step.z))
                     : rotate_about(R, center, x);
                 nx[3 * q] = y.x; nx[3 * q + 1] = y.y; nx[3 * q + 2] = y.z;
+                out |= !inside64(sd, y);
             }
-            __syncthreads();
+            wall = __syncthreads_or(out);
+        }
+        if (ok && wall) dE = INFINITY;   // beyond the container's wall
+        if (ok && !wall) {
             // local terms
-            int vb0, nb, jt0, nt;
-            local_window(sd, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt);
+            int vb0, nb, jt0, nt, fb0, nf;
+            local_window(sd, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt, &fb0, &nf);
             const int o = sd.chain_off[P.chain];
             double part = 0.0;
-            for (int itm = threadIdx.x; itm < 2 * (nb + nt); itm += blockDim.x) {
+            for (int itm = threadIdx.x; itm < 2 * (nb + nt + nf); itm += blockDim.x) {
                 const bool after = itm & 1;
                 const int k = itm >> 1;
                 auto pos = [&](int j) -> double3 {
@@ -412,7 +433,8 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
                     return ld3(x64 + 3 * j);
                 };
                 double term = (k < nb) ? sd.k_bend * bend_term(pos, o, vb0 + k)
-                                       : -sd.k_tors * torsion_term(pos, o, jt0 + (k - nb));
+                            : (k < nb + nt) ? -sd.k_tors * torsion_term(pos, o, jt0 + (k - nb))
+                                            : sd.fene_kR2 * fene_term(sd, pos, o, fb0 + (k - nb - nt));
                 part += after ? term : -term;
             }
             // pairs (moved i, unmoved j), before and after

@@ -145,11 +145,16 @@ class System:
     k_lj_intra: float = 4.0
     k_lj_inter: float = 4.0
     C: tuple = (1.0, -0.5, -0.5, 0.5)          # C_LJ at 2*s_i + s_j: AA, AB, BA, BB (Eq. 1)
+    sphere_R: float = 0.0                      # steric spherical container about the origin (0: none)
+    k_fene: float = 0.0                        # FENE bond term of Eq. 2 (0: AB limit, rigid bonds)
+    fene_r0: float = 1.0
+    fene_R: float = 0.5
+    C_F: tuple = (1.0, 1.0, 1.0, 1.0)          # C_F at 2*s_l + s_{l+1}
     e_min: float = -6.0
     bin_width: float = 0.05
     n_bins: int = 720
-    p: tuple = (1.0, 0.0, 0.0, 0.0)            # pivot, translation, rotation, crankshaft
-    amax: tuple = (0.5, 0.5, 0.3, 0.5)
+    p: tuple = (1.0, 0.0, 0.0, 0.0)            # pivot, translation, rotation, crankshaft[, bond, cap]
+    amax: tuple = (0.5, 0.5, 0.3, 0.5)         # angles (rad), translation step[, bond step, cap angle]
     recompute_every: int = 0
     walkers: int = 1
     xyz0: np.ndarray = field(default=None)     # (N, 3) initial conformation shared by the walkers

@@ -38,19 +38,23 @@ class PhastError(RuntimeError):
         self.code = code
 
 
+N_MOVES = 6   # pivot, translation, rotation, crankshaft, bond length, spherical cap
+
+
 class _System(C.Structure):
     _fields_ = [("n_chains", C.c_int32), ("chain_len", C.POINTER(C.c_int32)),
-                ("seq", C.POINTER(C.c_uint8)), ("box_L", C.c_double)]
+                ("seq", C.POINTER(C.c_uint8)), ("box_L", C.c_double), ("sphere_R", C.c_double)]
 
 
 class _FF(C.Structure):
     _fields_ = [("k_bend", C.c_double), ("k_tors", C.c_double), ("k_lj_intra", C.c_double),
-                ("k_lj_inter", C.c_double), ("C", C.c_double * 4)]
+                ("k_lj_inter", C.c_double), ("C", C.c_double * 4), ("k_fene", C.c_double),
+                ("fene_r0", C.c_double), ("fene_R", C.c_double), ("C_F", C.c_double * 4)]
 
 
 class _Muca(C.Structure):
     _fields_ = [("e_min", C.c_double), ("bin_width", C.c_double), ("n_bins", C.c_int32),
-                ("recompute_every", C.c_int32), ("p", C.c_double * 4), ("amax", C.c_double * 4),
+                ("recompute_every", C.c_int32), ("p", C.c_double * N_MOVES), ("amax", C.c_double * N_MOVES),
                 ("pair_precision", C.c_int32), ("pad", C.c_int32)]
 
 
@@ -61,7 +65,7 @@ class _MicroOut(C.Structure):
 
 MOVE_DTYPE = np.dtype([("type", "<i4"), ("chain", "<i4"), ("index", "<i4"), ("pad", "<i4"),
                        ("axis", "<f8", 3), ("angle", "<f8"), ("disp", "<f8", 3)])
-STATS_DTYPE = np.dtype([("attempts", "<u8", 4), ("accepts", "<u8", 4), ("pair_evals", "<u8"),
+STATS_DTYPE = np.dtype([("attempts", "<u8", N_MOVES), ("accepts", "<u8", N_MOVES), ("pair_evals", "<u8"),
                         ("pair_evals_inter", "<u8"), ("recomputes", "<u8"), ("drift_max", "<f8")])
 TRACE_DTYPE = np.dtype([("dE", "<f8"), ("bin_after", "<i4"), ("accepted", "<i4")])
 
@@ -153,13 +157,18 @@ class _Structs:
             self.sys[i].chain_len = cl.ctypes.data_as(C.POINTER(C.c_int32))
             self.sys[i].seq = sq.ctypes.data_as(C.POINTER(C.c_uint8))
             self.sys[i].box_L = float(s.box_L)
+            self.sys[i].sphere_R = float(s.sphere_R)
             self.ff[i].k_bend, self.ff[i].k_tors = float(s.k_bend), float(s.k_tors)
             self.ff[i].k_lj_intra, self.ff[i].k_lj_inter = float(s.k_lj_intra), float(s.k_lj_inter)
             self.ff[i].C = (C.c_double * 4)(*[float(c) for c in s.C])
+            self.ff[i].k_fene, self.ff[i].fene_r0, self.ff[i].fene_R = float(s.k_fene), float(s.fene_r0), float(s.fene_R)
+            self.ff[i].C_F = (C.c_double * 4)(*[float(c) for c in s.C_F])
             self.mp[i].e_min, self.mp[i].bin_width = float(s.e_min), float(s.bin_width)
             self.mp[i].n_bins, self.mp[i].recompute_every = int(s.n_bins), int(s.recompute_every)
-            self.mp[i].p = (C.c_double * 4)(*[float(x) for x in s.p])
-            self.mp[i].amax = (C.c_double * 4)(*[float(x) for x in s.amax])
+            p = list(s.p) + [0.0] * (N_MOVES - len(s.p))
+            a = list(s.amax) + [0.0] * (N_MOVES - len(s.amax))
+            self.mp[i].p = (C.c_double * N_MOVES)(*[float(x) for x in p])
+            self.mp[i].amax = (C.c_double * N_MOVES)(*[float(x) for x in a])
             self.mp[i].pair_precision = int(pair_precision or 64)
 
 

@@ -20,7 +20,8 @@ def random_conformations(s: inputs.System, B: int, seed: int, d_min: float = 0.9
 
 def oracle_model(orc, s: inputs.System):
     return orc.Model(s.chain_len, s.seq, box_L=s.box_L, k_bend=s.k_bend, k_tors=s.k_tors,
-                     k_lj_intra=s.k_lj_intra, k_lj_inter=s.k_lj_inter, C=s.C)
+                     k_lj_intra=s.k_lj_intra, k_lj_inter=s.k_lj_inter, C=s.C, sphere_R=s.sphere_R,
+                     k_fene=s.k_fene, fene_r0=s.fene_r0, fene_R=s.fene_R, C_F=s.C_F)
 
 
 def oracle_muca(orc, s: inputs.System):

@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(libphast):
 
 def test_version_and_error_string(libphast):
     L = libphast.lib()
-    assert L.phast_version() == 1
+    assert L.phast_version() == 2
     assert isinstance(L.phast_last_error(), bytes)
 
 
@@ -81,7 +81,7 @@ def test_host_side_validation(libphast):
     # context creation rejects bad move mixes before touching the device
     s3 = inputs.config0(walkers=1)
     st3 = libphast._Structs([s3])
-    st3.mp[0].p = (C.c_double * 4)(0.5, 0.2, 0.2, 0.2)
+    st3.mp[0].p = (C.c_double * libphast.N_MOVES)(0.5, 0.2, 0.2, 0.2, 0.0, 0.0)
     h = C.c_void_p()
     w = np.array([1], np.int32)
     seeds = np.zeros(1, np.uint64)
@@ -90,9 +90,19 @@ def test_host_side_validation(libphast):
                               xyz.ctypes.data, None) == -1
     assert b"probabilities" in L.phast_last_error()
     st4 = libphast._Structs([s3])
-    st4.mp[0].amax = (C.c_double * 4)(1.5, 0.5, 0.3, 0.5)
+    st4.mp[0].amax = (C.c_double * libphast.N_MOVES)(1.5, 0.5, 0.3, 0.5, 0.0, 0.0)
     assert L.phast_ctx_create(C.byref(h), 1, st4.sys, st4.ff, st4.mp, w.ctypes.data, seeds.ctypes.data,
                               xyz.ctypes.data, None) == -1
+    # bond-length / cap moves need the FENE term; a container excludes a periodic box
+    st6 = libphast._Structs([s3])
+    st6.mp[0].p = (C.c_double * libphast.N_MOVES)(0.8, 0.0, 0.0, 0.0, 0.2, 0.0)
+    assert L.phast_ctx_create(C.byref(h), 1, st6.sys, st6.ff, st6.mp, w.ctypes.data, seeds.ctypes.data,
+                              xyz.ctypes.data, None) == -1
+    assert b"k_fene" in L.phast_last_error()
+    st7 = libphast._Structs([s3])
+    st7.sys[0].sphere_R, st7.sys[0].box_L = 10.0, 20.0
+    assert L.phast_energy(st7.sys, st7.ff, 1, None, 64, None, None) == -1
+    assert b"container" in L.phast_last_error()
     xyz_nan = xyz.copy()
     xyz_nan[4] = np.nan
     st5 = libphast._Structs([s3])

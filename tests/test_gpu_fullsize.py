@@ -49,7 +49,7 @@ def test_config4_full_size(orc):
                                       force=tr[w]["accepted"].astype(np.int8), record=True)
         check_fp32_trace_dE(orc, s, lnW.cpu().numpy(), s.seeds()[w], tr[w]["dE"], rec,
                             tr[w]["accepted"].astype(np.int8), label=f"walker {w}")
-        assert so[11] <= 2                      # decisions the oracle would take differently (near-ties)
-        assert int(stats["pair_evals"][w]) == int(so[8])
+        assert so[orc.ST_MISMATCHES] <= 2                      # decisions the oracle would take differently (near-ties)
+        assert int(stats["pair_evals"][w]) == int(so[orc.ST_PAIR_EVALS])
         assert abs(wk.E - float(st["E"][w])) <= 1e-4 * max(1.0, abs(wk.E))
     ctx.close()

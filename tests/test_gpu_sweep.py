@@ -83,8 +83,8 @@ def test_fp64_decisions_and_histograms_bit_exact(phast, orc, form, tile):
             assert np.allclose(tr[w]["dE"], rec["dE"], rtol=1e-10, atol=1e-10)
     stt = ctx.stats()
     assert np.all(stt["attempts"].sum(1) == n_sweeps * s.n_total)
-    assert np.array_equal(stt["accepts"][:, 0], np.array([r[2][4] for r in res]))
-    assert np.array_equal(stt["pair_evals"], np.array([r[2][8] for r in res]).astype(np.uint64))
+    assert np.array_equal(stt["accepts"][:, 0], np.array([r[2][orc.N_MOVES] for r in res]))
+    assert np.array_equal(stt["pair_evals"], np.array([r[2][orc.ST_PAIR_EVALS] for r in res]).astype(np.uint64))
     ctx.close()
 
 
@@ -171,7 +171,7 @@ def test_fp32_lockstep_with_oracle(phast, orc, name):
                 mis += 1
                 assert _near_tie(E_prev[it], rec["dE"][it], tr[w]["dE"][it], s, lnW, 0, b_prev[it], 1e-4 * max(1.0, abs(E_new))), \
                     f"walker {w} move {it}: unexplained decision mismatch"
-        assert mis == stats[11]
+        assert mis == stats[orc.ST_MISMATCHES]
         total_mis += mis
         # the GPU's running energy tracks the oracle's within the FP32 budget
         assert abs(float(st["E"][w]) - wk.E) < 1e-3 * max(1.0, abs(wk.E))

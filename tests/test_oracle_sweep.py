@@ -111,7 +111,7 @@ def test_resume_is_bit_exact(orc):
     hb, _, _ = orc.sweep_walker(m, mu, lnW, b, 36 * 6, hist=hb)
     assert np.array_equal(ha, hb)
     assert np.array_equal(a.xyz, b.xyz) and a.E == b.E and a.bin == b.bin and a.t == b.t == 360
-    assert sa[9] == 5 and sa[10] < 1e-10      # recomputes at sweeps 2,4,...,10; tiny FP64 drift
+    assert sa[orc.ST_RECOMPUTES] == 5 and sa[orc.ST_DRIFT] < 1e-10      # recomputes at sweeps 2,4,...,10; tiny FP64 drift
     assert ha.sum() == 360
 
 
@@ -124,13 +124,13 @@ def test_forced_decisions(orc):
     ha, sa, rec = orc.sweep_walker(m, mu, lnW, a, 500, record=True)
     b = orc.new_walker(m, mu, s.xyz0, 8)
     hb, sb, recb = orc.sweep_walker(m, mu, lnW, b, 500, force=rec["accepted"].astype(np.int8), record=True)
-    assert sb[11] == 0 and np.array_equal(ha, hb) and np.array_equal(rec, recb)
+    assert sb[orc.ST_MISMATCHES] == 0 and np.array_equal(ha, hb) and np.array_equal(rec, recb)
     f = rec["accepted"].astype(np.int8).copy()
     flip = np.nonzero(f == 0)[0][:3]
     f[flip] = 1
     c = orc.new_walker(m, mu, s.xyz0, 8)
     _, sc, _ = orc.sweep_walker(m, mu, lnW, c, 500, force=f)
-    assert sc[11] >= 1
+    assert sc[orc.ST_MISMATCHES] >= 1
 
 
 def test_out_of_range_start_is_an_error(orc):
