@@ -778,11 +778,9 @@ __device__ __forceinline__ PT fene_w(const SysDesc& d, const Pos& pos, int o, in
     const P4<PT> a = pos(o + l), b = pos(o + l + 1);
     const PT dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
     const PT r = sqrt(dx * dx + dy * dy + dz * dz);
-    if constexpr (sizeof(PT) == 8) {
-        const double x = (r - d.fene_r0) / d.fene_R;
-        const double x2 = x * x;
-        if (!(x2 < 1.0)) return INFINITY;
-        return d.C_F[2 * d.seq[o + l] + d.seq[o + l + 1]] * log(1.0 - x2);
+    if constexpr (sizeof(PT) == 8) {   // one FP64 implementation for every FP64 path
+        (void)r;
+        return fene_term(d, [&](int j) { const P4<PT> p = pos(j); return make_double3(p.x, p.y, p.z); }, o, l);
     } else {
         const float x = (r - d.fene_r0_32) * d.fene_iR32;
         const float x2 = x * x;

@@ -231,6 +231,39 @@ def config2(walkers_each: int = 1024) -> list:
     return [s13, s21, s2x34, s8x9]
 
 
+def place_in_sphere(chains, sphere_R: float, d_min: float, rng: np.random.Generator) -> np.ndarray:
+    """Translate each chain (centroid) to a uniform point of the ball that keeps it
+    inside the sphere, rejecting placements closer than d_min to chains placed."""
+    placed = []
+    for c in chains:
+        c0 = c - c.mean(axis=0)
+        reach = sphere_R - np.max(np.linalg.norm(c0, axis=1)) - 0.5
+        assert reach > 0, "chain too large for the container"
+        while True:
+            v = rng.uniform(-reach, reach, 3)
+            if np.linalg.norm(v) > reach:
+                continue
+            cand = c0 + v
+            if all(np.min(np.sum((p[:, None, :] - cand[None]) ** 2, axis=2)) >= d_min * d_min for p in placed):
+                placed.append(cand)
+                break
+    return np.concatenate(placed)
+
+
+def fene_sphere(walkers: int = 64, seed: int = 7) -> System:
+    """The paper's own geometry: two Fibonacci 13-mers in the steric spherical
+    container (radius 8) with FENE bonds (k_fene = -20, i.e. -K/2 with K = 40,
+    r0 = 1, R = 0.3) and all six move types."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    chains = [random_saw(13, 1.0, rng) for _ in range(2)]
+    xyz0 = place_in_sphere(chains, 8.0, 1.0, rng)
+    seq = np.concatenate([fibonacci_sequence(13), fibonacci_sequence(13)])
+    return System("fene_sphere", np.array([13, 13], np.int32), seq, 0.0, k_tors=-0.5, sphere_R=8.0,
+                  k_fene=-20.0, fene_r0=1.0, fene_R=0.3, e_min=-30.0, bin_width=0.05, n_bins=_bins(-30.0, 60.0, 0.05),
+                  p=(0.4, 0.1, 0.1, 0.1, 0.15, 0.15), amax=(0.5, 0.3, 0.3, 0.5, 0.05, 0.5),
+                  recompute_every=10, walkers=walkers, xyz0=xyz0)
+
+
 def config3(batch: int = 65536, seed: int = 3):
     """Differentiation workload: one Fibonacci 55-mer (open boundaries, torsion
     kappa = -0.5) and a batch of seed-3 random self-avoiding walks of it (unit
