@@ -332,8 +332,8 @@ __device__ __forceinline__ void local_window(const SysDesc& d, int type, int cha
     }
 }
 
-// FENE term of bond l (monomers l, l+1 of the chain at o) without k_fene R^2:
-// C_F ln(1 - ((r - r0) / R)^2), +inf outside |r - r0| < R (FP64).
+// FENE term of bond l (monomers l, l+1 of the chain at o):
+// k_fene R^2 C_F ln(1 - ((r - r0) / R)^2), +inf outside |r - r0| < R (FP64).
 template <class Pos>
 __device__ __forceinline__ double fene_term(const SysDesc& d, const Pos& pos, int o, int l) {
     double3 a = pos(o + l), b = pos(o + l + 1);
@@ -342,7 +342,7 @@ __device__ __forceinline__ double fene_term(const SysDesc& d, const Pos& pos, in
     double x = (r - d.fene_r0) / d.fene_R;
     double x2 = x * x;
     if (!(x2 < 1.0)) return INFINITY;
-    return d.C_F[2 * d.seq[o + l] + d.seq[o + l + 1]] * log(1.0 - x2);
+    return d.fene_kR2 * (d.C_F[2 * d.seq[o + l] + d.seq[o + l + 1]] * log(1.0 - x2));
 }
 
 __device__ __forceinline__ double3 ld3(const double* p) { return make_double3(p[0], p[1], p[2]); }

@@ -113,7 +113,7 @@ energy_grad_kernel(const SysDesc d, int B, const double* __restrict__ xyz, doubl
             E -= d.k_tors * t;
         }
         if (d.k_fene != 0.0)
-            for (int l = g.lane; l <= n - 2; l += 32) E += d.fene_kR2 * (double)fene_w<PT>(d, pos, o, l);
+            for (int l = g.lane; l <= n - 2; l += 32) E += (double)fene_w<PT>(d, pos, o, l);
     }
     bool out = false;   // a monomer beyond the container's wall: infinite energy
     for (int j = g.lane; j < d.N; j += 32) out |= !inside64(d, ld3(x64 + 3 * j));

@@ -133,7 +133,6 @@ template <> struct FF<float> {
     __device__ __forceinline__ float kout() const { return d.kout32; }
     __device__ __forceinline__ float kbend() const { return d.kbend32; }
     __device__ __forceinline__ float ktors() const { return d.ktors32; }
-    __device__ __forceinline__ float kfene() const { return d.fene_kR2_32; }
 };
 template <> struct FF<double> {
     const SysDesc& d;
@@ -144,7 +143,6 @@ template <> struct FF<double> {
     __device__ __forceinline__ double kout() const { return d.k_lj_inter; }
     __device__ __forceinline__ double kbend() const { return d.k_bend; }
     __device__ __forceinline__ double ktors() const { return d.k_tors; }
-    __device__ __forceinline__ double kfene() const { return d.fene_kR2; }
 };
 
 // Minimum-imaged difference of the origins of chains a and b, in the working precision.
@@ -353,12 +351,15 @@ __device__ __forceinline__ MoveSet move_set(const SysDesc& d, int type, int chai
     MoveSet M;
     int fixed;
     moved_range(d, type, chain, index, &M.lo, &M.hi, &fixed);
-    // partners left out: the pivot (its distances to the rotated side keep) and
-    // the bonded neighbours of the moved range inside the chain
+    // partners left out: the pivot (its distances to the rotated side keep) and,
+    // for one moved monomer (crankshaft, cap), its bonded neighbours.  A
+    // bond-length move keeps every partner; its one bonded pair is taken back
+    // out in local_delta.
     const int o = d.chain_off[chain], e = d.chain_off[chain + 1] - 1;
+    const bool single = type == PHAST_CRANK || type == PHAST_CAP;
     M.ex0 = fixed;
-    M.ex1 = (type != PHAST_PIVOT && M.lo - 1 >= o) ? M.lo - 1 : -1;
-    M.ex2 = (type != PHAST_PIVOT && M.hi + 1 <= e) ? M.hi + 1 : -1;
+    M.ex1 = (single && M.lo - 1 >= o) ? M.lo - 1 : -1;
+    M.ex2 = (single && M.hi + 1 <= e) ? M.hi + 1 : -1;
     M.a_lo = d.n_a_before[M.lo];
     M.n_a = d.n_a_before[M.hi + 1] - M.a_lo;
     return M;
@@ -382,6 +383,7 @@ __device__ __forceinline__ uint64_t move_pair_evals_inter(const SysDesc& d, int 
 // Pair evaluations a move costs (2 per changed Lennard-Jones pair).
 __device__ __forceinline__ uint64_t move_pair_evals(const SysDesc& d, int type, const MoveSet& M) {
     const int m = M.hi - M.lo + 1;
+    if (type == PHAST_BOND) return 2ull * ((uint64_t)m * (d.N - m) - 1);   // all but the bonded pair
     const int excluded = (M.ex0 >= 0) + (M.ex1 >= 0) + (M.ex2 >= 0);
     return 2ull * m * (d.N - m - excluded);
 }
@@ -771,8 +773,8 @@ __device__ __forceinline__ PT torsion_w(const Pos& pos, int o, int j) {
     return n12 * rsqrt_w(n11 * n22);
 }
 
-// FENE term of bond l in the working precision without k_fene R^2:
-// C_F ln(1 - ((r - r0) / R)^2), +inf outside |r - r0| < R.
+// FENE term of bond l in the working precision:
+// k_fene R^2 C_F ln(1 - ((r - r0) / R)^2), +inf outside |r - r0| < R.
 template <typename PT, class Pos>
 __device__ __forceinline__ PT fene_w(const SysDesc& d, const Pos& pos, int o, int l) {
     const P4<PT> a = pos(o + l), b = pos(o + l + 1);
@@ -785,18 +787,22 @@ __device__ __forceinline__ PT fene_w(const SysDesc& d, const Pos& pos, int o, in
         const float x = (r - d.fene_r0_32) * d.fene_iR32;
         const float x2 = x * x;
         if (!(x2 < 1.0f)) return INFINITY;
-        return d.C_F32[2 * d.seq[o + l] + d.seq[o + l + 1]] * log1pf(-x2);
+        return d.fene_kR2_32 * (d.C_F32[2 * d.seq[o + l] + d.seq[o + l + 1]] * log1pf(-x2));
     }
 }
 
 // This lane's share of the bending/torsion change, in the working precision.
+template <typename PT>
+__device__ __forceinline__ PT lj_pair(PT dx, PT dy, PT dz, PT Lj, PT iLj, PT C);
+
 template <int TPW, typename PT>
 __device__ PT local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M, const Slot<PT>& s,
                               const Group<TPW>& g) {
     int vb0, nb, jt0, nt, fb0, nf;
     local_window(d, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt, &fb0, &nf);
     const int o = d.chain_off[P.chain];
-    const int items = 2 * (nb + nt + nf);
+    const int nc = P.type == PHAST_BOND;   // the stretched bond's pair, counted by the pair loop, taken back
+    const int items = 2 * (nb + nt + nf + nc);
     PT part = (PT)0;
     for (int it = g.lane; it < items; it += TPW) {
         const bool after = it & 1;
@@ -816,9 +822,15 @@ __device__ PT local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M,
             return s.r[j];
         };
         const FF<PT> f{d};
-        const PT term = (k < nb) ? f.kbend() * bend_w<PT>(pos, o, vb0 + k)
-                      : (k < nb + nt) ? -f.ktors() * torsion_w<PT>(pos, o, jt0 + (k - nb))
-                                      : f.kfene() * fene_w<PT>(d, pos, o, fb0 + (k - nb - nt));
+        PT term;
+        if (k < nb) term = f.kbend() * bend_w<PT>(pos, o, vb0 + k);
+        else if (k < nb + nt) term = -f.ktors() * torsion_w<PT>(pos, o, jt0 + (k - nb));
+        else if (k < nb + nt + nf) term = fene_w<PT>(d, pos, o, fb0 + (k - nb - nt));
+        else {   // minus the Lennard-Jones term of the bonded pair (index, index + 1)
+            const P4<PT> a = pos(o + P.index), b = pos(o + P.index + 1);
+            term = -f.kin() * lj_pair<PT>(a.x - b.x, a.y - b.y, a.z - b.z, (PT)0, (PT)0,
+                                          f.C(2 * d.seq[o + P.index] + d.seq[o + P.index + 1]));
+        }
         part += after ? term : -term;
     }
     return part;
@@ -1080,7 +1092,7 @@ __device__ double full_energy64(const SysDesc& d, const double* x64, const Group
         for (int k = 1 + g.lane; k <= n - 2; k += TPW) part += d.k_bend * bend_term(pos, o, k);
         for (int j = g.lane; j <= n - 4; j += TPW) part -= d.k_tors * torsion_term(pos, o, j);
         if (d.k_fene != 0.0)
-            for (int l = g.lane; l <= n - 2; l += TPW) part += d.fene_kR2 * fene_term(d, pos, o, l);
+            for (int l = g.lane; l <= n - 2; l += TPW) part += fene_term(d, pos, o, l);
     }
     for (int j = g.lane; j < d.N; j += TPW) out |= !inside64(d, pos(j));
     for (int i = 0; i < d.N; ++i) {
@@ -1115,7 +1127,7 @@ __device__ double full_energy_working(const SysDesc& d, const Slot<PT>& s, const
         for (int k = 1 + g.lane; k <= n - 2; k += TPW) part += (double)((PT)d.k_bend * bend_w<PT>(pos, o, k));
         for (int j = g.lane; j <= n - 4; j += TPW) part -= (double)((PT)d.k_tors * torsion_w<PT>(pos, o, j));
         if (d.k_fene != 0.0)
-            for (int l = g.lane; l <= n - 2; l += TPW) part += d.fene_kR2 * (double)fene_w<PT>(d, pos, o, l);
+            for (int l = g.lane; l <= n - 2; l += TPW) part += (double)fene_w<PT>(d, pos, o, l);
     }
     const PT L = (PT)d.box_L, iL = (PT)d.inv_L;
     for (int i = 0; i < d.N; ++i) {

@@ -181,9 +181,11 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
             ls->pair_evals_inter += move_pair_evals_inter(sd, P.type, P.chain, M);
             if (tracing) {
                 phast_trace tr;
+                // an infinite FP32 term leaves NaN in the double-float's low word: report hi alone
                 tr.dE = !ok ? __longlong_as_double(0x7ff8000000000000ll)
                       : wall ? INFINITY
-                             : (sizeof(PT) == 4 ? (double)dE32.hi + (double)dE32.lo : dE64);
+                             : (sizeof(PT) == 4 ? (isinf(dE32.hi) ? (double)dE32.hi : (double)dE32.hi + (double)dE32.lo)
+                                                : dE64);
                 tr.bin_after = bin;
                 tr.accepted = (int32_t)acc;
                 a.trace[(int64_t)w_local * n_moves + it] = tr;
@@ -299,7 +301,7 @@ __device__ double block_full_energy64(const SysDesc& d, const double* x64, doubl
         for (int k = 1 + threadIdx.x; k <= n - 2; k += blockDim.x) part += d.k_bend * bend_term(pos, o, k);
         for (int j = threadIdx.x; j <= n - 4; j += blockDim.x) part -= d.k_tors * torsion_term(pos, o, j);
         if (d.k_fene != 0.0)
-            for (int l = threadIdx.x; l <= n - 2; l += blockDim.x) part += d.fene_kR2 * fene_term(d, pos, o, l);
+            for (int l = threadIdx.x; l <= n - 2; l += blockDim.x) part += fene_term(d, pos, o, l);
     }
     int out = 0;   // a monomer beyond the container's wall: infinite energy
     for (int j = threadIdx.x; j < d.N; j += blockDim.x) out |= !inside64(d, pos(j));
@@ -424,17 +426,25 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
             int vb0, nb, jt0, nt, fb0, nf;
             local_window(sd, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt, &fb0, &nf);
             const int o = sd.chain_off[P.chain];
+            const int nc = P.type == PHAST_BOND;   // the stretched bond's pair, counted below, taken back
             double part = 0.0;
-            for (int itm = threadIdx.x; itm < 2 * (nb + nt + nf); itm += blockDim.x) {
+            for (int itm = threadIdx.x; itm < 2 * (nb + nt + nf + nc); itm += blockDim.x) {
                 const bool after = itm & 1;
                 const int k = itm >> 1;
                 auto pos = [&](int j) -> double3 {
                     if (after && j >= M.lo && j <= M.hi) return ld3(nx + 3 * (j - M.lo));
                     return ld3(x64 + 3 * j);
                 };
-                double term = (k < nb) ? sd.k_bend * bend_term(pos, o, vb0 + k)
-                            : (k < nb + nt) ? -sd.k_tors * torsion_term(pos, o, jt0 + (k - nb))
-                                            : sd.fene_kR2 * fene_term(sd, pos, o, fb0 + (k - nb - nt));
+                double term;
+                if (k < nb) term = sd.k_bend * bend_term(pos, o, vb0 + k);
+                else if (k < nb + nt) term = -sd.k_tors * torsion_term(pos, o, jt0 + (k - nb));
+                else if (k < nb + nt + nf) term = fene_term(sd, pos, o, fb0 + (k - nb - nt));
+                else {
+                    const double3 a = pos(o + P.index), b = pos(o + P.index + 1);
+                    const double dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+                    term = -sd.k_lj_intra * lj64(dx * dx + dy * dy + dz * dz,
+                                                 sd.C[2 * sd.seq[o + P.index] + sd.seq[o + P.index + 1]]);
+                }
                 part += after ? term : -term;
             }
             // pairs (moved i, unmoved j), before and after

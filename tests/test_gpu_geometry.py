@@ -1,0 +1,157 @@
+"""The paper's own geometry on the GPU -- steric container, FENE bonds,
+bond-length and spherical-cap moves -- against the oracle."""
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+import torch
+
+from paper_1702_01770_gb300 import inputs
+
+from helpers import check_fp32_trace_dE, oracle_model, oracle_muca
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def phast():
+    from paper_1702_01770_gb300 import phast
+    phast.lib()
+    return phast
+
+
+def _states(orc, s, n, seed):
+    """n conformations from an oracle run of the workload (inside the wall, bonds in range)."""
+    m, mu = oracle_model(orc, s), oracle_muca(orc, s)
+    wk = orc.new_walker(m, mu, s.xyz0, seed)
+    out = []
+    for _ in range(n):
+        orc.sweep_walker(m, mu, np.zeros(s.n_bins), wk, 26 * 20)
+        out.append(wk.xyz.copy())
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_energy_with_wall_and_bonds(phast, orc, precision):
+    s = inputs.fene_sphere(1)
+    x = _states(orc, s, 6, 3)
+    bad = x[0].copy()
+    bad[5] *= 8.5 / np.linalg.norm(bad[5])            # a monomer beyond the wall
+    xs = np.concatenate([x, bad[None]])
+    E = phast.phast_energy(s, torch.from_numpy(xs).cuda(), precision).cpu().numpy()
+    m = oracle_model(orc, s)
+    for b in range(x.shape[0]):
+        Eo = orc.energy(m, x[b])
+        tol = 1e-11 if precision == 64 else 1e-4
+        assert abs(E[b] - Eo) <= tol * max(1.0, abs(Eo))
+    assert E[-1] == np.inf
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_delta_energy_every_move_type(phast, orc, precision):
+    s = inputs.fene_sphere(1)
+    x = _states(orc, s, 1, 4)[0]
+    m, mu = oracle_model(orc, s), oracle_muca(orc, s)
+    mvs = [orc.propose(m, mu, 1234, t)[0] for t in range(400)]
+    arr = np.zeros(len(mvs), phast.MOVE_DTYPE)
+    for i, mv in enumerate(mvs):
+        arr[i] = (mv.type, mv.chain, mv.index, 0, tuple(mv.axis), mv.angle, tuple(mv.disp))
+    xs = torch.from_numpy(np.broadcast_to(x, (len(mvs),) + x.shape).copy()).cuda()
+    dE, xn = phast.phast_delta_energy(s, xs, arr, precision, want_xyz=True)
+    dE, xn = dE.cpu().numpy(), xn.cpu().numpy()
+    seen = set()
+    for i, mv in enumerate(mvs):
+        dEo, yo = orc.delta_energy(m, x, mv)
+        seen.add(mv.type)
+        if np.isinf(dEo):
+            assert dE[i] == np.inf, i
+            continue
+        assert np.array_equal(xn[i], yo), (i, mv.type)          # exact FP64 geometry, bit for bit
+        if precision == 64:
+            assert dE[i] == pytest.approx(dEo, rel=1e-9, abs=1e-9), (i, mv.type)
+        else:
+            A = orc.delta_scale(m, x, mv)
+            assert abs(dE[i] - dEo) <= 1e-4 * max(1.0, abs(dEo)) + 2e-5 * A, (i, mv.type)
+    assert seen == set(range(6))
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_sweep_lockstep_with_oracle(phast, orc, precision):
+    s = inputs.fene_sphere(32)
+    n_tr, n_sweeps = 4, 150
+    ctx = phast.Context(s, pair_precision=precision)
+    k = np.arange(s.n_bins)
+    lnW = -0.03 * k + 0.5 * np.sin(k / 13.0)
+    trace = ctx.trace_buffer(n_sweeps, n_tr)
+    ctx.sweep(n_sweeps, torch.from_numpy(lnW).cuda(), trace=trace, trace_walkers=n_tr)
+    st = ctx.get_state("cpu")
+    torch.cuda.synchronize()
+    tr = trace.cpu().numpy().view(phast.TRACE_DTYPE).reshape(n_tr, -1)
+    m, mu = oracle_model(orc, s), oracle_muca(orc, s)
+    n_moves = n_sweeps * s.n_total
+    seeds = s.seeds()
+
+    def one(w):
+        wk = orc.new_walker(m, mu, s.xyz0, int(seeds[w]))
+        f = tr[w]["accepted"].astype(np.int8)
+        h, stats, rec = orc.sweep_walker(m, mu, lnW, wk, n_moves, force=f, record=True)
+        return wk, stats, rec, f
+
+    with ThreadPoolExecutor(max_workers=4) as ex:
+        res = list(ex.map(one, range(n_tr)))
+    xyz = st["xyz"].numpy().reshape(s.walkers, s.n_total, 3)
+    for w, (wk, stats, rec, f) in enumerate(res):
+        dg = tr[w]["dE"].copy()
+        inf_o, inf_g = np.isinf(rec["dE"]), np.isinf(dg)
+        if precision == 64:
+            assert np.array_equal(inf_o, inf_g), w                   # the wall and the bond range agree
+        else:
+            # in FP32 a bond at the edge of its range can be infinite on one side and
+            # finite on the other, but then far above every bin: rejected by both
+            E_prev = np.concatenate([[orc.energy(m, s.xyz0)], rec["E_after"][:-1]])
+            one = inf_o != inf_g
+            fin = np.where(inf_o, dg, rec["dE"])
+            assert np.all(E_prev[one] + fin[one] >= s.e_max), w
+            assert not np.any(tr[w]["accepted"][one]), w
+            dg[one] = rec["dE"][one]
+        ok = ~inf_o & np.isfinite(rec["dE"])
+        if precision == 64:
+            assert np.allclose(dg[ok], rec["dE"][ok], rtol=1e-9, atol=1e-9)
+        else:
+            check_fp32_trace_dE(orc, s, lnW, seeds[w], dg, rec, f, label=f"walker {w}")
+        assert stats[orc.ST_MISMATCHES] <= 2                          # near-ties of the decision only
+        assert np.array_equal(xyz[w], wk.xyz), w                      # exact coordinates, bit for bit
+        assert stats[4] > 0 and stats[5] > 0 and stats[10] > 0 and stats[11] > 0
+    assert np.all(np.linalg.norm(xyz, axis=2) <= 8.0)
+    ctx.close()
+
+
+def test_plain_and_batched_fp64_agree(phast):
+    s = inputs.fene_sphere(16)
+    a = phast.Context(s, pair_precision=64)
+    b = phast.Context(s, pair_precision=64)
+    lnW = torch.zeros(s.n_bins, dtype=torch.float64, device="cuda")
+    a.sweep(40, lnW, form=phast.FORM_PLAIN)
+    b.sweep(40, lnW, form=phast.FORM_BATCHED)
+    sa, sb = a.get_state("cpu"), b.get_state("cpu")
+    torch.cuda.synchronize()
+    assert torch.equal(sa["xyz"], sb["xyz"]) and torch.equal(sa["bin"], sb["bin"])
+    assert torch.allclose(sa["E"], sb["E"], rtol=0, atol=1e-9)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_gradient_with_bonds(phast, orc, precision):
+    s = inputs.fene_sphere(1)
+    x = _states(orc, s, 4, 8)
+    E, gx, gf = phast.phast_energy_grad(s, torch.from_numpy(x).cuda(), precision)
+    E, gx, gf = E.cpu().numpy(), gx.cpu().numpy(), gf.cpu().numpy()
+    m = oracle_model(orc, s)
+    for b in range(x.shape[0]):
+        Eo, go, po = orc.energy_grad(m, x[b])
+        gmax = max(1.0, np.max(np.abs(go)))
+        tol = 1e-10 if precision == 64 else 1e-4
+        assert abs(E[b] - Eo) <= (1e-11 if precision == 64 else 1e-4) * max(1.0, abs(Eo))
+        assert np.max(np.abs(gx[b] - go)) <= tol * gmax
+        assert np.all(np.abs(gf[b] - po) <= tol * np.maximum(1.0, np.abs(po)))
