@@ -61,6 +61,7 @@ int phast_build_desc(const phast_system* sys, const phast_ff* ff, const phast_mu
     if (sys->sphere_R > 0.0 && sys->box_L > 0.0)
         return phast_set_error(PHAST_EINVAL, "%s: a spherical container and a periodic box exclude each other", what);
     d->sphere_R2 = sys->sphere_R * sys->sphere_R;
+    d->has_sphere = sys->sphere_R > 0.0;
     d->sphere_R2_32 = (float)d->sphere_R2;
     d->k_bend = ff->k_bend;
     d->k_tors = ff->k_tors;

@@ -40,7 +40,8 @@ struct SysDesc {
     double e_min, bin_width;
     double p[PHAST_N_MOVES], amax[PHAST_N_MOVES];
     uint64_t thr[PHAST_N_MOVES];   // move-type thresholds: type i if 2n+1 < thr[i] (n the 52-bit uniform), see propose_select
-    int32_t last_type, type_mask, pad2[2];   // type_mask: bit i set when p[i] > 0
+    int32_t last_type, type_mask;   // type_mask: bit i set when p[i] > 0
+    int32_t has_sphere, pad2;       // has_sphere: a steric container (sphere_R2 > 0)
     double sphere_R2;     // sphere_R * sphere_R of the steric container (0: none)
     double k_fene, fene_r0, fene_R, fene_kR2;   // FENE term of Eq. 2; fene_kR2 = k_fene * (R * R)
     double C_F[4];

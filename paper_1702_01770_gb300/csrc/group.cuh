@@ -232,7 +232,7 @@ __device__ __forceinline__ bool disc_test(uint4 r, float* v1f, float* v2f, float
 // same axis in FP32 mode (whose exact axis is rebuilt at commit from the
 // winning block).  The acceptance words uz, uw are valid on lane 0 only
 // (u = u52(uz, uw) is formed only when the acceptance test needs it).
-template <int TPW, typename PT>
+template <int TPW, typename PT, bool GEOM = true>
 __device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, uint4 blk, const Group<TPW>& g) {
     // blk: this lane's stream block (block index = lane) of move t
     Proposal P;
@@ -257,7 +257,7 @@ __device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, u
         const uint64_t v = 2 * u52_bits(w0x, w0y) + 1;
         int type = d.last_type;
 #pragma unroll
-        for (int i = PHAST_N_MOVES - 1; i >= 0; --i)
+        for (int i = (GEOM ? PHAST_N_MOVES : 4) - 1; i >= 0; --i)
             if (((d.type_mask >> i) & 1) && v < d.thr[i]) type = i;
         P.type = type;
         P.chain = (int)(((uint64_t)w0z * (uint64_t)d.n_chains) >> 32);
@@ -269,7 +269,7 @@ __device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, u
         else P.angle32 = a0;
     }
     P.attempt = -1;
-    if (P.type == PHAST_PIVOT || P.type == PHAST_ROT || P.type == PHAST_CAP) {
+    if (P.type == PHAST_PIVOT || P.type == PHAST_ROT || (GEOM && P.type == PHAST_CAP)) {
         const unsigned gm = TPW == 32 ? 0xffffffffu : ((1u << TPW) - 1u);
         uint4 mine = blk;
         int round = 0;
@@ -471,7 +471,7 @@ __device__ __forceinline__ void sincos32(float a, float* s, float* c) {
 // FP32 relative coordinates moved by an FP32 rotation or translation built
 // from FP32 data only; the exact FP64 move is made only when it is accepted
 // (commit_move).  Returns false for a degenerate crankshaft axis.
-template <int TPW, typename PT>
+template <int TPW, typename PT, bool GEOM = true>
 __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Proposal& P, const MoveSet& M,
                                    Slot<PT>& s, const Group<TPW>& g) {
     const int m = M.hi - M.lo + 1;
@@ -495,9 +495,9 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
         return true;
     } else {
         float4* mv = reinterpret_cast<float4*>(s.newr);
-        if (P.type == PHAST_TRANS || P.type == PHAST_BOND) {
+        if (P.type == PHAST_TRANS || (GEOM && P.type == PHAST_BOND)) {
             float dx = P.disp32.x, dy = P.disp32.y, dz = P.disp32.z;
-            if (P.type == PHAST_BOND) {   // slide along the FP32 unit bond vector
+            if (GEOM && P.type == PHAST_BOND) {   // slide along the FP32 unit bond vector
                 const P4<PT> a = s.r[o + P.index], b = s.r[o + P.index + 1];
                 const float bx = b.x - a.x, by = b.y - a.y, bz = b.z - a.z;
                 const float len = sqrtf(bx * bx + by * by + bz * bz);
@@ -516,7 +516,7 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
             }
         } else {
             float kx = P.axis32.x, ky = P.axis32.y, kz = P.axis32.z, cx, cy, cz;
-            if (P.type == PHAST_PIVOT || P.type == PHAST_CAP) {
+            if (P.type == PHAST_PIVOT || (GEOM && P.type == PHAST_CAP)) {
                 const P4<PT> p = s.r[o + (P.type == PHAST_PIVOT ? P.index : (P.index > 0 ? P.index - 1 : 1))];
                 cx = p.x; cy = p.y; cz = p.z;
             } else if (P.type == PHAST_ROT) {
@@ -570,10 +570,12 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
 // to the wall.  The same value on every lane of the group.
 // exact: P carries the exact FP64 move (else it is regenerated from the
 // walker's stream, key seed and move index t, as the replay does).
+// Kept out of line: the check runs only with a container, and its code stays
+// out of the instruction stream of the moves that need none.
 template <int TPW, typename PT>
-__device__ bool container_ok(const SysDesc& d, const double* x64, const Proposal& P, const MoveSet& M, Slot<PT>& s,
-                             const Group<TPW>& g, bool exact, uint64_t seed, uint64_t t) {
-    if (!(d.sphere_R2 > 0.0)) return true;
+__device__ __noinline__ bool container_ok(const SysDesc& d, const double* x64, const Proposal& P, const MoveSet& M,
+                                          Slot<PT>& s, const Group<TPW>& g, bool exact, uint64_t seed, uint64_t t) {
+    if (!d.has_sphere) return true;
     const int m = M.hi - M.lo + 1;
     const unsigned gm = TPW == 32 ? 0xffffffffu : ((1u << TPW) - 1u);
     bool out = false, unsure = false;
@@ -659,7 +661,7 @@ __device__ void accept_move32(const SysDesc& d, const Proposal& P, uint64_t t, c
 // once, one move per lane; centres are read from the coordinates as each move
 // is made.  Then the working copy of the chains they moved is refreshed from
 // the exact coordinates.
-template <int TPW>
+template <int TPW, bool GEOM = true>
 __device__ __noinline__ void flush_queue(const SysDesc& d, double* x64, uint64_t seed, Slot<float>& s, const Group<TPW>& g,
                             int count) {
     if (count == 0) return;
@@ -670,6 +672,7 @@ __device__ __noinline__ void flush_queue(const SysDesc& d, double* x64, uint64_t
         const QEntry e = s.queue[g.lane];
         Proposal Q;
         propose_select(d, stream_block(seed, e.t, 0u), stream_block(seed, e.t, 1u), stream_block(seed, e.t, 2u), &Q);
+        if constexpr (!GEOM) __builtin_assume(Q.type >= 0 && Q.type < PHAST_BOND);
         if (Q.type == PHAST_PIVOT || Q.type == PHAST_ROT || Q.type == PHAST_CAP) {
             const double3 ax = exact_axis(seed, e.t, e.attempt);
             double sn, cs;
@@ -687,6 +690,7 @@ __device__ __noinline__ void flush_queue(const SysDesc& d, double* x64, uint64_t
         P.type = e.packed & 7;
         P.chain = (e.packed >> 3) & 63;
         P.index = e.packed >> 9;
+        if constexpr (!GEOM) __builtin_assume(P.type < PHAST_BOND);
         P.attempt = e.attempt;
         P.angle = 0.0;
         P.disp = make_double3(0.0, 0.0, 0.0);
@@ -795,13 +799,26 @@ __device__ __forceinline__ PT fene_w(const SysDesc& d, const Pos& pos, int o, in
 template <typename PT>
 __device__ __forceinline__ PT lj_pair(PT dx, PT dy, PT dz, PT Lj, PT iLj, PT C);
 
-template <int TPW, typename PT>
+// A FENE bond term of monomers (l, l + 1) at positions a, b (fene), or minus
+// the Lennard-Jones term of that pair (the bonded pair of a bond move).
+template <typename PT>
+__device__ __noinline__ PT bond_item(const SysDesc& d, bool fene, P4<PT> a, P4<PT> b, int l) {
+    const FF<PT> f{d};
+    if (fene) {
+        auto pos2 = [&](int j) -> P4<PT> { return j == l ? a : b; };
+        return fene_w<PT>(d, pos2, l, 0);
+    }
+    return -f.kin() * lj_pair<PT>(a.x - b.x, a.y - b.y, a.z - b.z, (PT)0, (PT)0, f.C(2 * d.seq[l] + d.seq[l + 1]));
+}
+
+template <int TPW, typename PT, bool GEOM = true>
 __device__ PT local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M, const Slot<PT>& s,
                               const Group<TPW>& g) {
     int vb0, nb, jt0, nt, fb0, nf;
     local_window(d, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt, &fb0, &nf);
     const int o = d.chain_off[P.chain];
-    const int nc = P.type == PHAST_BOND;   // the stretched bond's pair, counted by the pair loop, taken back
+    if (!GEOM) nf = 0;
+    const int nc = GEOM && P.type == PHAST_BOND;   // the stretched bond's pair, counted by the pair loop, taken back
     const int items = 2 * (nb + nt + nf + nc);
     PT part = (PT)0;
     for (int it = g.lane; it < items; it += TPW) {
@@ -825,11 +842,10 @@ __device__ PT local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M,
         PT term;
         if (k < nb) term = f.kbend() * bend_w<PT>(pos, o, vb0 + k);
         else if (k < nb + nt) term = -f.ktors() * torsion_w<PT>(pos, o, jt0 + (k - nb));
-        else if (k < nb + nt + nf) term = fene_w<PT>(d, pos, o, fb0 + (k - nb - nt));
-        else {   // minus the Lennard-Jones term of the bonded pair (index, index + 1)
-            const P4<PT> a = pos(o + P.index), b = pos(o + P.index + 1);
-            term = -f.kin() * lj_pair<PT>(a.x - b.x, a.y - b.y, a.z - b.z, (PT)0, (PT)0,
-                                          f.C(2 * d.seq[o + P.index] + d.seq[o + P.index + 1]));
+        else {   // a FENE bond or the bond move's pair: out of line (most workloads have neither)
+            const bool fene = k < nb + nt + nf;
+            const int l = o + (fene ? fb0 + (k - nb - nt) : P.index);   // the bond's first monomer
+            term = bond_item<PT>(d, fene, pos(l), pos(l + 1), l);
         }
         part += after ? term : -term;
     }

@@ -106,7 +106,32 @@ __global__ void init_energy_kernel(const SysDesc* __restrict__ descs, int n_sys,
 // ---------------------------------------------------------------------------
 // Batched form.
 // ---------------------------------------------------------------------------
+
+// The FP64 full energy replaces the running one (when in range) and the
+// working copy is rebuilt.
 template <int TPW, typename PT>
+__device__ __forceinline__ void recompute_energy(const SysDesc& sd, const double* x64, const double* lnW, Slot<PT>& slot,
+                                              const Group<TPW>& g, phast_walker_stats* ls, double& E, int& bin,
+                                              double& lnw_here, float& erel) {
+    const double Ef = full_energy64<TPW>(sd, x64, g);
+    if (g.lane == 0) {
+        ls->drift_max = fmax(ls->drift_max, fabs(E - Ef));
+        ls->recomputes++;
+    }
+    const int bf = bin_of(sd, Ef);
+    if (bf >= 0) {
+        E = Ef;
+        bin = bf;
+        lnw_here = __ldg(lnW + bin);
+        erel = (float)(E - sd.e_min);
+    }
+    g.sync();
+    build_working<TPW, PT>(sd, x64, slot, g);
+}
+// GEOM: the system types use the paper's own geometry (FENE bonds, container,
+// bond-length or cap moves); without it those branches are compiled out, which
+// keeps the per-move loop short in the instruction cache.
+template <int TPW, typename PT, bool GEOM>
 __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int w_local, Slot<PT>& slot,
                            uint32_t* hist, unsigned long long* hist_g, const Group<TPW>& g) {
     // hist: the tile's shared histogram; hist_g (non-null): this walker's jackknife
@@ -134,11 +159,13 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
     float erel = (float)(E - sd.e_min);                     // FP32 image of E - e_min (FP32 mode)
     uint4 blk = stream_block(seed, t, (uint32_t)g.lane);    // this lane's block of the current move
     for (int64_t it = 0; it < n_moves; ++it) {
-        const Proposal P = propose_group<TPW, PT>(sd, seed, t, blk, g);
+        const Proposal P = propose_group<TPW, PT, GEOM>(sd, seed, t, blk, g);
+        if constexpr (!GEOM) __builtin_assume(P.type >= 0 && P.type < PHAST_BOND);   // no bond or cap moves
         const MoveSet M = move_set(sd, P.type, P.chain, P.index);
-        const bool ok = make_new_positions<TPW, PT>(sd, x64, P, M, slot, g);
+        const bool ok = make_new_positions<TPW, PT, GEOM>(sd, x64, P, M, slot, g);
         // a trial position beyond the container's wall: infinite energy, not evaluated
-        const bool wall = ok && !container_ok<TPW, PT>(sd, x64, P, M, slot, g, sizeof(PT) == 8, seed, t);
+        bool wall = false;
+        if constexpr (GEOM) wall = ok && sd.has_sphere && !container_ok<TPW, PT>(sd, x64, P, M, slot, g, sizeof(PT) == 8, seed, t);
         const bool eval = ok && !wall;
         DF dE32{0.0f, 0.0f};
         double dE64 = 0.0;
@@ -147,12 +174,12 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
             if (eval) {
                 part = sd.box_L > 0.0 ? pair_delta32<TPW, 3, true>(sd, M, P.chain, slot, g)
                                       : pair_delta32<TPW, 3, false>(sd, M, P.chain, slot, g);
-                part = df_add(part, DF{local_delta<TPW, PT>(sd, P, M, slot, g), 0.0f});
+                part = df_add(part, DF{local_delta<TPW, PT, GEOM>(sd, P, M, slot, g), 0.0f});
             }
             dE32 = group_sum_df<TPW>(part, g);
         } else {
             double part = 0.0;
-            if (eval) part = local_delta<TPW, PT>(sd, P, M, slot, g) + pair_delta<TPW, PT, 4>(sd, M, P.chain, slot, g);
+            if (eval) part = local_delta<TPW, PT, GEOM>(sd, P, M, slot, g) + pair_delta<TPW, PT, 4>(sd, M, P.chain, slot, g);
             dE64 = g.sum(part);
         }
         const bool finite = eval && (sizeof(PT) == 4 ? (isfinite(dE32.hi) && isfinite(dE32.lo)) : isfinite(dE64));
@@ -195,7 +222,7 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
             if constexpr (sizeof(PT) == 4) {
                 accept_move32<TPW>(sd, P, t, M, slot, g, queued);
                 if (++queued == qcap) {
-                    flush_queue<TPW>(sd, x64, seed, slot, g, queued);
+                    flush_queue<TPW, GEOM>(sd, x64, seed, slot, g, queued);
                     queued = 0;
                 }
             } else {
@@ -206,26 +233,13 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         ++t;
         if (period && (t % period) == 0) {   // FP64 full energy kills the drift of the running sum
             if constexpr (sizeof(PT) == 4) {
-                flush_queue<TPW>(sd, x64, seed, slot, g, queued);
+                flush_queue<TPW, GEOM>(sd, x64, seed, slot, g, queued);
                 queued = 0;
             }
-            const double Ef = full_energy64<TPW>(sd, x64, g);
-            if (g.lane == 0) {
-                ls->drift_max = fmax(ls->drift_max, fabs(E - Ef));
-                ls->recomputes++;
-            }
-            const int bf = bin_of(sd, Ef);
-            if (bf >= 0) {
-                E = Ef;
-                bin = bf;
-                lnw_here = __ldg(lnW + bin);
-                erel = (float)(E - sd.e_min);
-            }
-            g.sync();
-            build_working<TPW, PT>(sd, x64, slot, g);
+            recompute_energy<TPW, PT>(sd, x64, lnW, slot, g, ls, E, bin, lnw_here, erel);
         }
     }
-    if constexpr (sizeof(PT) == 4) flush_queue<TPW>(sd, x64, seed, slot, g, queued);
+    if constexpr (sizeof(PT) == 4) flush_queue<TPW, GEOM>(sd, x64, seed, slot, g, queued);
     if (g.lane == 0) {
         a.E[gw] = E;
         a.bin[gw] = bin;
@@ -241,7 +255,7 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
 
 constexpr int kMaxTileThreads = 512;
 
-template <int TPW, typename PT>
+template <int TPW, typename PT, bool GEOM>
 __global__ void __launch_bounds__(kMaxTileThreads)
 sweep_batched_kernel(const SweepArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -276,7 +290,7 @@ sweep_batched_kernel(const SweepArgs a) {
             const int mine = jk_block(w_local, W, a.n_jk);
             unsigned long long* hg =
                 (a.hist_sum && mine != blk) ? a.hist_sum + a.hs_off[s_id] + (int64_t)mine * sd.n_bins : nullptr;
-            run_walker<TPW, PT>(sd, a, s_id, w_local, slot, hist, hg, g);
+            run_walker<TPW, PT, GEOM>(sd, a, s_id, w_local, slot, hist, hg, g);
         }
         __syncthreads();
         if (a.hist_sum) {
@@ -525,15 +539,21 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
 // ---------------------------------------------------------------------------
 typedef void (*batched_fn)(const SweepArgs);
 
-batched_fn pick_batched(int tpw, bool fp32) {
+template <bool G>
+batched_fn pick_batched_g(int tpw, bool fp32) {
     switch (tpw) {
-        case 4: return fp32 ? sweep_batched_kernel<4, float> : sweep_batched_kernel<4, double>;
-        case 8: return fp32 ? sweep_batched_kernel<8, float> : sweep_batched_kernel<8, double>;
-        case 16: return fp32 ? sweep_batched_kernel<16, float> : sweep_batched_kernel<16, double>;
-        case 32: return fp32 ? sweep_batched_kernel<32, float> : sweep_batched_kernel<32, double>;
+        case 4: return fp32 ? sweep_batched_kernel<4, float, G> : sweep_batched_kernel<4, double, G>;
+        case 8: return fp32 ? sweep_batched_kernel<8, float, G> : sweep_batched_kernel<8, double, G>;
+        case 16: return fp32 ? sweep_batched_kernel<16, float, G> : sweep_batched_kernel<16, double, G>;
+        case 32: return fp32 ? sweep_batched_kernel<32, float, G> : sweep_batched_kernel<32, double, G>;
         default: return nullptr;
     }
 }
+
+batched_fn pick_batched(int tpw, bool fp32, bool geom) {
+    return geom ? pick_batched_g<true>(tpw, fp32) : pick_batched_g<false>(tpw, fp32);
+}
+
 
 size_t batched_smem(const phast_ctx* c, bool fp32, int wpc, SlotLayout* L) {
     *L = fp32 ? slot_layout<float>(c->max_N, c->max_nc, c->max_chain)
@@ -606,6 +626,15 @@ void layout_tiles(const phast_ctx* c, int wpc, int grid, SweepArgs* a) {
     a->n_tiles = start;
 }
 
+// Whether any system type of the context needs the paper's own geometry.
+bool uses_geometry(const phast_ctx* c) {
+    for (int s = 0; s < c->n_sys; ++s) {
+        const SysDesc& d = c->desc[s];
+        if (d.has_sphere || d.k_fene != 0.0 || d.p[PHAST_BOND] > 0.0 || d.p[PHAST_CAP] > 0.0) return true;
+    }
+    return false;
+}
+
 struct BatchedLaunch {
     batched_fn fn;
     int grid, threads;
@@ -620,7 +649,7 @@ int prepare_batched(phast_ctx* c, const SweepArgs& a0, int tpw, int wpc, bool fp
     SlotLayout SL;
     L->smem = batched_smem(c, fp32, wpc, &SL);
     L->a.L = SL;
-    L->fn = pick_batched(tpw, fp32);
+    L->fn = pick_batched(tpw, fp32, uses_geometry(c));
     if (!L->fn) return phast_set_error(PHAST_EINVAL, "threads per walker %d not in {4, 8, 16, 32}", tpw);
     L->threads = tpw * wpc;
     if (L->threads < 32 || L->threads > kMaxTileThreads || L->threads % 32)
