@@ -94,6 +94,8 @@ def lib():
         L.orc_propose.argtypes = [P(_Model), P(_Muca), C.c_uint64, C.c_uint64, P(Move), P(C.c_double)]
         L.orc_apply_move.argtypes = [P(_Model), P(Move), P(C.c_double), P(C.c_double)]
         L.orc_apply_move.restype = C.c_int
+        L.orc_move_jacobian.argtypes = [P(_Model), P(C.c_double), P(Move)]
+        L.orc_move_jacobian.restype = C.c_double
         L.orc_delta_energy.argtypes = [P(_Model), P(C.c_double), P(Move), P(C.c_double)]
         L.orc_delta_energy.restype = C.c_double
         L.orc_delta_scale.argtypes = [P(_Model), P(C.c_double), P(Move)]
@@ -259,6 +261,13 @@ def apply_move(model: Model, mv: Move, xyz):
     m = model.c_struct()
     n = lib().orc_apply_move(C.byref(m), C.byref(mv), _ptr(x, C.c_double), _ptr(out, C.c_double))
     return n, out.reshape(-1, 3)
+
+
+def move_jacobian(model: Model, xyz, mv: Move) -> float:
+    """Hastings factor of the move from xyz (1 except for bond-length moves)."""
+    x = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1)
+    m = model.c_struct()
+    return lib().orc_move_jacobian(C.byref(m), _ptr(x, C.c_double), C.byref(mv))
 
 
 def delta_energy(model: Model, xyz, mv: Move):

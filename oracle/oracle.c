@@ -194,6 +194,24 @@ void orc_propose(const orc_model* m, const orc_muca* mu, uint64_t seed, uint64_t
     }
 }
 
+/* Hastings factor of a move: 1, except for a bond-length move, whose map
+ * b -> b (r + delta) / r of the stretched bond vector (length r, every other
+ * bond vector of the moved side unchanged) has Jacobian determinant
+ * ((r + delta) / r)^2 in Cartesian coordinates.  Reading: the density of
+ * states of Eq. 4 counts configuration-space volume in the bead coordinates,
+ * in which pivot, crankshaft, rigid and cap moves are symmetric proposals;
+ * a uniform dilation step delta is not, so the acceptance carries this
+ * factor (Metropolis-Hastings).  r is computed as in orc_apply_move. */
+double orc_move_jacobian(const orc_model* m, const double* xyz, const orc_move* mv) {
+    if (mv->type != ORC_BOND) return 1.0;
+    int o = orc_chain_offset(m, mv->chain), l = mv->index;
+    double b[3];
+    for (int d = 0; d < 3; ++d) b[d] = xyz[3 * (o + l + 1) + d] - xyz[3 * (o + l) + d];
+    double r = sqrt((b[0] * b[0] + b[1] * b[1]) + b[2] * b[2]);
+    double q = (r + mv->angle) / r;
+    return q * q;
+}
+
 /* Centroid of monomers o..o+n-1 (the rotation centre of a rigid rotation).
  * Reading: the paper names the centre of mass but not the floating-point order
  * of its sum; it is fixed here so that every implementation reproduces the
@@ -241,6 +259,7 @@ int orc_apply_move(const orc_model* m, const orc_move* mv, const double* xyz, do
         for (int d = 0; d < 3; ++d) b[d] = xyz[3 * (o + l + 1) + d] - xyz[3 * (o + l) + d];
         double len = sqrt((b[0] * b[0] + b[1] * b[1]) + b[2] * b[2]);
         if (!(len > 1e-12)) return 0;
+        if (!(len + mv->angle > 0.0)) return 0;   /* the bond would pass through zero length */
         int head = (l + 1) < (n - 1 - l);
         double delta = head ? -mv->angle : mv->angle;
         for (int d = 0; d < 3; ++d) { u[d] = b[d] / len; step[d] = delta * u[d]; }
@@ -547,7 +566,7 @@ int32_t orc_bin(const orc_muca* mu, double E) {
 
 /* ------------------------------------------------------------------------- */
 /* The multicanonical Metropolis sweep of one walker (Sec. 2.2 and Sec. 3.2,   */
-/* MONTE_CARLO.f): accept with min(1, W(E')/W(E)), W = exp(lnW[bin]) piecewise  */
+/* MONTE_CARLO.f): accept with min(1, J W(E')/W(E)), W = exp(lnW[bin]) piecewise*/
 /* constant per bin (Eq. 8 tabulated), and count the current bin into the      */
 /* histogram after every attempt, accepted or not.  Readings: one sweep is      */
 /* N_tot attempts; a proposal out of the bin range or with non-finite dE is     */
@@ -575,8 +594,10 @@ int orc_sweep_walker(const orc_model* m, const orc_muca* mu, const double* lnW,
         int32_t b_new = orc_bin(mu, E_new);
         int own = 0;
         if (b_new >= 0) {
+            /* min(1, J W(E') / W(E)); J = 1 except for bond-length moves */
             double dlnW = lnW[b_new] - lnW[*bin];
-            own = (dlnW >= 0.0) || (u_acc < exp(dlnW));
+            double J = orc_move_jacobian(m, xyz, &mv);
+            own = (dlnW >= 0.0 && J >= 1.0) || (u_acc < J * exp(dlnW));
         }
         int acc = own;
         if (force && force[it] >= 0) {

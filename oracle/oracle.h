@@ -90,6 +90,9 @@ void orc_propose(const orc_model* m, const orc_muca* mu, uint64_t seed, uint64_t
  * move applied.  Returns the number of moved monomers, 0 if degenerate. */
 int orc_apply_move(const orc_model* m, const orc_move* mv, const double* xyz, double* xyz_new);
 
+/* Hastings factor J of the move from xyz (1 except for bond-length moves). */
+double orc_move_jacobian(const orc_model* m, const double* xyz, const orc_move* mv);
+
 /* Energy change of the move by its affected terms only. */
 double orc_delta_energy(const orc_model* m, const double* xyz, const orc_move* mv, double* xyz_new);
 

@@ -7,8 +7,13 @@ spherical-cap moves (the paper's own geometry, Sec. 2.1 Eq. 2 and Sec. 3.2).
 * Bond-length moves change exactly one bond, by delta, along its direction, on
   the shorter side, and -delta undoes them; caps keep the bond to their centre.
 * E_after - E_before = dE for every move type; long runs stay inside the wall.
-* A trimer with bond-length moves only under flat weights samples its two bond
-  stretches uniformly, so its energy histogram is an exact area integral.
+* Bond-length moves carry the Hastings factor ((r + delta) / r)^2 of their
+  radial map, so that they sample the Cartesian measure of the bead
+  coordinates: a collinear trimer with bond-length moves only, under flat
+  weights, samples each bond length r with density proportional to r^2 on the
+  FENE range (capped by the last bin), which makes its energy histogram and its
+  stretch distribution exact integrals (a plain Metropolis rule would sample r
+  uniformly and fail both).
 """
 import dataclasses
 
@@ -91,7 +96,14 @@ def test_bond_length_moves(orc):
         assert set(moved) <= set(want)
         _, z = orc.apply_move(m, orc.make_move(orc.BOND, c, l, angle=-d), y)
         assert np.allclose(z, x, rtol=0, atol=1e-13)
+        J = orc.move_jacobian(m, x, orc.make_move(orc.BOND, c, l, angle=d))
+        assert J == pytest.approx(((b0[k] + d) / b0[k]) ** 2, rel=1e-14)
         x = y
+    # a step that takes the bond through zero length is no move
+    n, _ = orc.apply_move(m, orc.make_move(orc.BOND, 0, 3, angle=-1.5), x)
+    assert n == 0
+    for t in (orc.PIVOT, orc.TRANS, orc.ROT, orc.CRANK, orc.CAP):
+        assert orc.move_jacobian(m, x, orc.make_move(t, 0, 3, angle=0.3)) == 1.0
 
 
 def test_spherical_cap_moves(orc):
@@ -148,30 +160,57 @@ def test_runs_stay_inside_and_in_range(orc):
     assert np.sum(np.isinf(rec["dE"])) > 0                       # the wall / bond range rejected some
 
 
-def _uniform_stretch_histogram(e_min, w, K, kR2=1.8):
-    """P(E in bin) for E = E_F(x1) + E_F(x2), x uniform on (-1, 1)^2, E_F(x) = -kR2 ln(1 - x^2),
-    restricted to E < e_min + K w, as an integral over x1 of the x2-interval lengths."""
-    def g(e):   # |x| with E_F(x) = e
-        e = np.maximum(e, 0.0)
-        return np.sqrt(1.0 - np.exp(-e / kR2))
+R_F, KR2 = 0.3, 1.8      # the trimer's FENE range and -k R^2 (k = -20)
+
+
+def _g(e):
+    """|x| at which E_F(x) = -KR2 ln(1 - x^2) equals e (0 below 0)."""
+    return np.sqrt(1.0 - np.exp(-np.maximum(e, 0.0) / KR2))
+
+
+def _G(e):
+    """Integral of the Cartesian weight (1 + R x)^2 over {x : E_F(x) < e}."""
+    g = _g(e)
+    return 2.0 * g + (2.0 / 3.0) * R_F * R_F * g ** 3
+
+
+def _stretch_energy_histogram(e_min, w, K):
+    """P(E in bin) for E = E_F(x1) + E_F(x2), x = (r - 1) / R with density
+    (1 + R x1)^2 (1 + R x2)^2 on (-1, 1)^2, restricted to E < e_min + K w."""
     x1, wq = np.polynomial.legendre.leggauss(4000)
-    E1 = -kR2 * np.log(1.0 - x1 * x1)
+    E1 = -KR2 * np.log(1.0 - x1 * x1)
     edges = e_min + w * np.arange(K + 1)
-    G = 2.0 * g(edges[None, :] - E1[:, None])          # length of {x2 : E_F(x2) < edge - E1}
-    area = np.sum(wq[:, None] * np.diff(G, axis=1), axis=0)
-    return area / area.sum()
+    G = _G(edges[None, :] - E1[:, None])
+    mass = np.sum((wq * (1.0 + R_F * x1) ** 2)[:, None] * np.diff(G, axis=1), axis=0)
+    return mass / mass.sum()
 
 
-def test_bond_moves_sample_stretches_uniformly(orc):
-    s = dataclasses.replace(_fene_trimer(), k_tors=0.0, e_min=0.0, bin_width=0.05, n_bins=80,
-                            p=(0.0, 0.0, 0.0, 0.0, 1.0, 0.0), amax=(0.5, 0.5, 0.3, 0.5, 0.06, 0.5))
+def _stretch_marginal(edges, e_max):
+    """P(x1 in each interval of edges): density (1 + R x1)^2 G(e_max - E_F(x1))."""
+    out = []
+    for a, b in zip(edges[:-1], edges[1:]):
+        x, wq = np.polynomial.legendre.leggauss(200)
+        x = 0.5 * (b - a) * x + 0.5 * (a + b)
+        E1 = -KR2 * np.log(1.0 - x * x)
+        out.append(0.5 * (b - a) * np.sum(wq * (1.0 + R_F * x) ** 2 * _G(e_max - E1)))
+    out = np.array(out)
+    return out / out.sum()
+
+
+def _bond_only_trimer():
+    return dataclasses.replace(_fene_trimer(), k_tors=0.0, e_min=0.0, bin_width=0.05, n_bins=80,
+                               p=(0.0, 0.0, 0.0, 0.0, 1.0, 0.0), amax=(0.5, 0.5, 0.3, 0.5, 0.06, 0.5))
+
+
+def test_bond_moves_sample_the_cartesian_measure(orc):
+    s = _bond_only_trimer()
     m, mu = oracle_model(orc, s), oracle_muca(orc, s)
     H = np.zeros(s.n_bins, np.uint64)
     for seed in range(8):
         wk = orc.new_walker(m, mu, _line(1.0, 1.0), seed)
         orc.sweep_walker(m, mu, np.zeros(s.n_bins), wk, 2000)             # equilibrate
         H, _, _ = orc.sweep_walker(m, mu, np.zeros(s.n_bins), wk, 200000, hist=H)
-    p = _uniform_stretch_histogram(s.e_min, s.bin_width, s.n_bins)
+    p = _stretch_energy_histogram(s.e_min, s.bin_width, s.n_bins)
     n = H.sum()
     exp_ = n * p
     keep = exp_ > 50
@@ -180,3 +219,27 @@ def test_bond_moves_sample_stretches_uniformly(orc):
     z = (H[keep] - exp_[keep]) / np.sqrt(exp_[keep])
     assert np.max(np.abs(z)) < 25.0, np.max(np.abs(z))
     assert np.sum(np.abs(H[keep] / exp_[keep] - 1.0) > 0.1) == 0
+
+
+def test_bond_moves_stretch_distribution(orc):
+    # the energy sees only x^2; the stretch itself shows the odd part of the
+    # r^2 weight: <x> is about 0.06 here, 0 for a uniform density
+    s = _bond_only_trimer()
+    m, mu = oracle_model(orc, s), oracle_muca(orc, s)
+    xs = []
+    for seed in range(4):
+        wk = orc.new_walker(m, mu, _line(1.0, 1.0), 100 + seed)
+        orc.sweep_walker(m, mu, np.zeros(s.n_bins), wk, 2000)
+        for _ in range(3000):
+            orc.sweep_walker(m, mu, np.zeros(s.n_bins), wk, 60)
+            r = np.linalg.norm(np.diff(wk.xyz, axis=0), axis=1)
+            xs.extend((r - 1.0) / R_F)
+    xs = np.array(xs)
+    edges = np.linspace(-1.0, 1.0, 11)
+    p = _stretch_marginal(edges, s.e_min + s.bin_width * s.n_bins)
+    h = np.histogram(xs, edges)[0] / xs.size
+    keep = p > 0.01
+    assert np.max(np.abs(h[keep] / p[keep] - 1.0)) < 0.08, (h, p)
+    x_mean = np.sum(p * 0.5 * (edges[1:] + edges[:-1]))
+    assert x_mean > 0.04
+    assert abs(xs.mean() - x_mean) < 0.02, (xs.mean(), x_mean)
