@@ -270,7 +270,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved_tf / peak_tf, "traffic": traffic_per_launch(args.walkers),
                 "peak_basis": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz (max SM clock)",
-                "kernel": "sweep_batched_kernel<32,float>",
+                "kernel": "sweep_batched_kernel<32,float,0> (no FENE, sphere, bond or cap moves)",
                 "frac_at_median_clock": (achieved_tf / (n_sm * 256 * clocks["sm_mhz"] * 1e6 / 1e12))
                 if clocks.get("sm_mhz") else None}
 

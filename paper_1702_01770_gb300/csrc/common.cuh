@@ -350,12 +350,18 @@ __device__ __forceinline__ double3 ld3(const double* p) { return make_double3(p[
 
 // Exact step of a bond-length move on bond l of the chain at o (n monomers):
 // the shorter side slides by +delta u (tail) or -delta u (head), u the unit
-// bond vector (x_{l+1} - x_l) / |x_{l+1} - x_l|; false for coincident monomers.
-__device__ __forceinline__ bool bond_step(const double* x64, int o, int n, int l, double delta, double3* step) {
+// bond vector (x_{l+1} - x_l) / |x_{l+1} - x_l|; false for coincident monomers
+// or a step through zero length.  *jac: the move's Hastings factor
+// ((r + delta) / r)^2, the Jacobian determinant of the radial map of the bond
+// vector (bead coordinates are the sampled measure).
+__device__ __forceinline__ bool bond_step(const double* x64, int o, int n, int l, double delta, double3* step,
+                                          double* jac) {
     const double3 a = ld3(x64 + 3 * (o + l)), b = ld3(x64 + 3 * (o + l + 1));
     const double bx = xsub(b.x, a.x), by = xsub(b.y, a.y), bz = xsub(b.z, a.z);
     const double len = xsqrt(xadd(xadd(xmul(bx, bx), xmul(by, by)), xmul(bz, bz)));
-    if (!(len > 1e-12)) return false;
+    if (!(len > 1e-12) || !(xadd(len, delta) > 0.0)) return false;
+    const double q = xdiv(xadd(len, delta), len);
+    *jac = xmul(q, q);
     const double dl = (l + 1 < n - 1 - l) ? -delta : delta;
     *step = make_double3(xmul(dl, xdiv(bx, len)), xmul(dl, xdiv(by, len)), xmul(dl, xdiv(bz, len)));
     return true;

@@ -390,8 +390,9 @@ __device__ __forceinline__ uint64_t move_pair_evals(const SysDesc& d, int type, 
 
 // Lane 0 builds the move's exact centre and rotation (FP64, bit-reproducible)
 // into the slot's geo scratch: geo[0..8] R, geo[9..11] centre, geo[12] 1 (0 for
-// a degenerate crankshaft axis).  axis64 is the exact axis of a pivot or
-// rotation.
+// a degenerate crankshaft axis or bond step); for a bond-length move geo[13..15]
+// the step and geo[16] its Hastings factor.  axis64 is the exact axis of a
+// pivot or rotation.
 template <int TPW, typename PT>
 __device__ bool prepare_exact(const SysDesc& d, const double* x64, const Proposal& P, double3 axis64, Slot<PT>& s,
                               const Group<TPW>& g) {
@@ -400,10 +401,12 @@ __device__ bool prepare_exact(const SysDesc& d, const double* x64, const Proposa
     if (P.type == PHAST_ROT) rot_center = centroid_tree<TPW>(x64, o, n, g);
     if (P.type == PHAST_BOND && g.lane == 0) {   // the slide of the moved side
         double3 step = make_double3(0.0, 0.0, 0.0);
-        s.geo[12] = bond_step(x64, o, n, P.index, P.angle, &step) ? 1.0 : 0.0;
+        double jac = 1.0;
+        s.geo[12] = bond_step(x64, o, n, P.index, P.angle, &step, &jac) ? 1.0 : 0.0;
         s.geo[13] = step.x;
         s.geo[14] = step.y;
         s.geo[15] = step.z;
+        s.geo[16] = jac;
     } else if (P.type != PHAST_TRANS && g.lane == 0) {
         double3 axis = axis64, center;
         double ok = 1.0;
@@ -470,14 +473,17 @@ __device__ __forceinline__ void sincos32(float a, float* s, float* c) {
 // FP64 mode: the exact FP64 positions (also kept in new64).  FP32 mode: the
 // FP32 relative coordinates moved by an FP32 rotation or translation built
 // from FP32 data only; the exact FP64 move is made only when it is accepted
-// (commit_move).  Returns false for a degenerate crankshaft axis.
+// (commit_move).  Returns false for a degenerate crankshaft axis or bond step.
+// *jac (bond-length moves, when given): the Hastings factor ((r + delta) / r)^2,
+// exact in FP64 mode, from the FP32 bond length in FP32 mode.
 template <int TPW, typename PT, bool GEOM = true>
 __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Proposal& P, const MoveSet& M,
-                                   Slot<PT>& s, const Group<TPW>& g) {
+                                   Slot<PT>& s, const Group<TPW>& g, double* jac = nullptr) {
     const int m = M.hi - M.lo + 1;
     const int c = P.chain, o = d.chain_off[c], n = d.chain_off[c + 1] - o;
     if constexpr (sizeof(PT) == 8) {
         if (!prepare_exact<TPW, PT>(d, x64, P, P.axis, s, g)) return false;
+        if (GEOM && jac && P.type == PHAST_BOND) *jac = s.geo[16];
         for (int q = g.lane; q < m; q += TPW) {
             const int j = M.lo + q;
             const double3 y = exact_position(P, s.geo, ld3(x64 + 3 * j));
@@ -501,7 +507,11 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
                 const P4<PT> a = s.r[o + P.index], b = s.r[o + P.index + 1];
                 const float bx = b.x - a.x, by = b.y - a.y, bz = b.z - a.z;
                 const float len = sqrtf(bx * bx + by * by + bz * bz);
-                if (!(len > 1e-12f)) return false;
+                if (!(len > 1e-12f) || !(len + P.angle32 > 0.0f)) return false;
+                if (jac) {
+                    const float q = (len + P.angle32) / len;
+                    *jac = (double)(q * q);
+                }
                 const float dl = (P.index + 1 < n - 1 - P.index) ? -P.angle32 : P.angle32;
                 dx = dl * (bx / len);
                 dy = dl * (by / len);
@@ -1094,6 +1104,13 @@ __device__ __forceinline__ bool accept_below(double dl, const Proposal& P) {
         if (u24 - 6e-8f > e * (1.0f + rel)) return false;
     }
     return u52(P.uz, P.uw) < exp(dl);
+}
+
+// Acceptance of a bond-length move: min(1, J W(E')/W(E)) with its Hastings
+// factor J; one FP64 test (bond moves are a small share of the moves).
+__device__ __forceinline__ bool accept_stretch(double dl, double J, const Proposal& P) {
+    if (dl >= 0.0 && J >= 1.0) return true;
+    return u52(P.uz, P.uw) < J * exp(dl);
 }
 
 // Full FP64 energy (Eq. 2 per chain + inter-chain term of Eq. 3) of the

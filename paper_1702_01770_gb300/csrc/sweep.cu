@@ -162,7 +162,8 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         const Proposal P = propose_group<TPW, PT, GEOM>(sd, seed, t, blk, g);
         if constexpr (!GEOM) __builtin_assume(P.type >= 0 && P.type < PHAST_BOND);   // no bond or cap moves
         const MoveSet M = move_set(sd, P.type, P.chain, P.index);
-        const bool ok = make_new_positions<TPW, PT, GEOM>(sd, x64, P, M, slot, g);
+        double jac = 1.0;   // Hastings factor (bond-length moves)
+        const bool ok = make_new_positions<TPW, PT, GEOM>(sd, x64, P, M, slot, g, &jac);
         // a trial position beyond the container's wall: infinite energy, not evaluated
         bool wall = false;
         if constexpr (GEOM) wall = ok && sd.has_sphere && !container_ok<TPW, PT>(sd, x64, P, M, slot, g, sizeof(PT) == 8, seed, t);
@@ -190,7 +191,8 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         bool acc = false;
         if (b_new >= 0) {
             const double dl = lnw_new - lnw_here;
-            acc = (dl >= 0.0) || accept_below<PT>(dl, P);
+            if (GEOM && P.type == PHAST_BOND) acc = accept_stretch(dl, jac, P);
+            else acc = (dl >= 0.0) || accept_below<PT>(dl, P);
         }
         if (acc) {
             E = E + (sizeof(PT) == 4 ? (double)dE32.hi + (double)dE32.lo : dE64);
@@ -372,6 +374,7 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
     const uint64_t period = (uint64_t)sd.recompute_every * (uint64_t)sd.N;
 
     for (int64_t it = 0; it < n_moves; ++it) {
+        double jac = 1.0;   // Hastings factor of a bond-length move (thread 0)
         if (threadIdx.x == 0) {   // proposal, serial Marsaglia, centre and rotation
             Proposal P;
             propose_select(sd, stream_block(seed, t, 0), stream_block(seed, t, 1), stream_block(seed, t, 2), &P);
@@ -389,7 +392,7 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
             } else if (P.type == PHAST_CAP) {
                 center = ld3(x64 + 3 * (o + (P.index > 0 ? P.index - 1 : 1)));
             } else if (P.type == PHAST_BOND) {
-                ok = bond_step(x64, o, n, P.index, P.angle, &step) ? 1 : 0;
+                ok = bond_step(x64, o, n, P.index, P.angle, &step, &jac) ? 1 : 0;
             } else if (P.type == PHAST_ROT) {
                 center = centroid_serial(x64, o, n);
             } else if (P.type == PHAST_CRANK) {
@@ -488,7 +491,7 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
             int acc = 0;
             if (b_new >= 0) {
                 const double dl = lnW[b_new] - lnW[bin];
-                acc = (dl >= 0.0) || (u52(P.uz, P.uw) < exp(dl));
+                acc = P.type == PHAST_BOND ? accept_stretch(dl, jac, P) : (dl >= 0.0) || (u52(P.uz, P.uw) < exp(dl));
             }
             s_acc = acc;
             if (acc) { E = E_new; bin = b_new; }

@@ -155,3 +155,27 @@ def test_gradient_with_bonds(phast, orc, precision):
         assert abs(E[b] - Eo) <= (1e-11 if precision == 64 else 1e-4) * max(1.0, abs(Eo))
         assert np.max(np.abs(gx[b] - go)) <= tol * gmax
         assert np.all(np.abs(gf[b] - po) <= tol * np.maximum(1.0, np.abs(po)))
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_bond_moves_sample_the_cartesian_measure(phast, precision):
+    # bond-length moves alone on a collinear trimer under flat weights: every
+    # walker's final state is one sample of two independent bond lengths with
+    # density proportional to r^2 on the FENE range (capped by the last bin)
+    import dataclasses
+
+    from test_oracle_geometry import R_F, _bond_only_trimer, _line, _stretch_marginal
+    s = dataclasses.replace(_bond_only_trimer(), walkers=8192, xyz0=_line(1.0, 1.0))
+    ctx = phast.Context(s, pair_precision=precision)
+    ctx.sweep(1500, torch.zeros(s.n_bins, dtype=torch.float64, device="cuda"))
+    xyz = ctx.get_state("cpu")["xyz"].numpy().reshape(s.walkers, 3, 3)
+    torch.cuda.synchronize()
+    ctx.close()
+    x = ((np.linalg.norm(np.diff(xyz, axis=1), axis=2) - 1.0) / R_F).ravel()
+    edges = np.linspace(-1.0, 1.0, 11)
+    p = _stretch_marginal(edges, s.e_min + s.bin_width * s.n_bins)
+    h = np.histogram(x, edges)[0] / x.size
+    keep = p > 0.02
+    assert np.max(np.abs(h[keep] / p[keep] - 1.0)) < 0.15, (h, p)
+    x_mean = np.sum(p * 0.5 * (edges[1:] + edges[:-1]))
+    assert abs(x.mean() - x_mean) < 0.02, (x.mean(), x_mean)     # 0 without the Hastings factor
