@@ -30,6 +30,8 @@ METRIC = "MUCA walker-moves/s and pair-evals/s (% FP32 peak), batched vs plain a
 WORKLOAD = "8x55-mer aggregation: 8 chains x 55 monomers, periodic L=40, 16384 walkers, 8000 bins of 0.1 on [-400,400)"
 N_JK = 16
 N_T = 64
+GEOM_WALKERS = 16384
+GEOM_SWEEPS = 100
 FLOPS_OPEN, FLOPS_PBC = 14, 23          # algorithmic flops of one pair evaluation (open / minimum image)
 LAUNCHES_PER_STEP = 5                   # sweep, 3 analysis kernels, Berg update
 
@@ -47,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
+    ap.add_argument("--no-geom", action="store_true")
     return ap.parse_args()
 
 
@@ -115,7 +118,8 @@ def oracle_walker_moves_per_s(s, seconds: float, threads: int):
 
     import oracle
     m = oracle.Model(s.chain_len, s.seq, box_L=s.box_L, k_bend=s.k_bend, k_tors=s.k_tors,
-                     k_lj_intra=s.k_lj_intra, k_lj_inter=s.k_lj_inter, C=s.C)
+                     k_lj_intra=s.k_lj_intra, k_lj_inter=s.k_lj_inter, C=s.C, sphere_R=s.sphere_R,
+                     k_fene=s.k_fene, fene_r0=s.fene_r0, fene_R=s.fene_R, C_F=s.C_F)
     mu = oracle.Muca(s.e_min, s.bin_width, s.n_bins, p=s.p, amax=s.amax, recompute_every=s.recompute_every)
     lnW = np.zeros(s.n_bins)
     N = s.n_total
@@ -336,6 +340,54 @@ def run_ours(args):
                                   "pair_terms_per_s": gx0.shape[0] * pairs / (gms / 1e3),
                                   "outputs": "E, dE/dx, dE/d(C_AA, C_BB, C_AB, kappa, kappa_C)", "dtype": "f32"}
         del gxyz
+
+    # free energy and Maxwell construction of the last step's S(E), with the
+    # leave-one-block-out replicates of its 16 jackknife blocks
+    if rank == 0:
+        for _ in range(2):
+            phast.phast_maxwell(lnW, hs.view(N_JK, K), s.e_min, s.bin_width, N, fd_half_width=5)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        a.record()
+        for _ in range(reps):
+            phast.phast_maxwell(lnW, hs.view(N_JK, K), s.e_min, s.bin_width, N, fd_half_width=5)
+        b.record()
+        torch.cuda.synchronize()
+        out["maxwell"] = {"ms_per_call": a.elapsed_time(b) / reps, "bins": K, "replicates": 1 + N_JK,
+                          "outputs": "f(E) per monomer; beta_c, eps_1, eps_2, latent heat, barrier, with errors"}
+
+    # the paper's own geometry: steric sphere, FENE bonds, bond-length and cap moves
+    # (the batched kernel's build with them), two Fibonacci 13-mers, FP32 pair terms
+    if not args.no_geom and rank == 0:
+        gsys = inputs.fene_sphere(walkers=GEOM_WALKERS)
+        gctx = phast.Context(gsys, pair_precision=32)
+        glnW = torch.zeros(gsys.n_bins, dtype=torch.float64, device=dev)
+        gctx.sweep(20, glnW)
+        torch.cuda.synchronize()
+        g0 = gctx.stats()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        gctx.sweep(GEOM_SWEEPS, glnW)
+        b.record()
+        torch.cuda.synchronize()
+        g1 = gctx.stats()
+        gms = a.elapsed_time(b)
+        gmoves = int(g1["attempts"].sum() - g0["attempts"].sum())
+        assert gmoves == GEOM_WALKERS * gsys.n_total * GEOM_SWEEPS
+        out["geometry"] = {
+            "workload": "2 Fibonacci 13-mers in a steric sphere R = 8, FENE bonds (k_F = -20, R_F = 0.3), "
+                        f"all six move types, {GEOM_WALKERS} walkers, flat weights, {GEOM_SWEEPS} sweeps",
+            "kernel": "sweep_batched_kernel<32,float,1>", "walker_moves_per_s": gmoves / (gms / 1e3),
+            "pair_evals_per_s": float((g1["pair_evals"].sum() - g0["pair_evals"].sum()) / (gms / 1e3)),
+            "accept_rate": float((g1["accepts"].sum() - g0["accepts"].sum()) / gmoves), "dtype": "f32",
+            "l2": "walker state %.0f MB, L2-resident" % (GEOM_WALKERS * gsys.n_total * 24 / 1e6)}
+        if not args.no_cpu_baseline:
+            v, pev, n, dt = oracle_walker_moves_per_s(inputs.fene_sphere(walkers=1), 4.0, os.cpu_count() or 1)
+            out["geometry"]["cpu_baseline"] = {"value": v, "unit": "walker-moves/s", "cores": os.cpu_count() or 1,
+                                               "kind": "oracle", "sample": f"{n} walkers x 1 sweep, FP64 oracle, "
+                                                                           f"{dt:.1f} s", "pair_evals_per_s": pev}
+        gctx.close()
 
     # end to end through the C ABI with host buffers: state in from pinned host memory, results out
     if not args.no_e2e:

@@ -247,7 +247,7 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         a.bin[gw] = bin;
         a.t[gw] = t;
         phast_walker_stats* st = a.stats + gw;
-        for (int i = 0; i < 4; ++i) { st->attempts[i] += ls->attempts[i]; st->accepts[i] += ls->accepts[i]; }
+        for (int i = 0; i < PHAST_N_MOVES; ++i) { st->attempts[i] += ls->attempts[i]; st->accepts[i] += ls->accepts[i]; }
         st->pair_evals += ls->pair_evals;
         st->pair_evals_inter += ls->pair_evals_inter;
         st->recomputes += ls->recomputes;
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
         a.bin[gw] = bin;
         a.t[gw] = t;
         phast_walker_stats* st = a.stats + gw;
-        for (int i = 0; i < 4; ++i) { st->attempts[i] += ls->attempts[i]; st->accepts[i] += ls->accepts[i]; }
+        for (int i = 0; i < PHAST_N_MOVES; ++i) { st->attempts[i] += ls->attempts[i]; st->accepts[i] += ls->accepts[i]; }
         st->pair_evals += ls->pair_evals;
         st->pair_evals_inter += ls->pair_evals_inter;
         st->recomputes += ls->recomputes;

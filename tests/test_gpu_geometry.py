@@ -179,3 +179,32 @@ def test_bond_moves_sample_the_cartesian_measure(phast, precision):
     assert np.max(np.abs(h[keep] / p[keep] - 1.0)) < 0.15, (h, p)
     x_mean = np.sum(p * 0.5 * (edges[1:] + edges[:-1]))
     assert abs(x.mean() - x_mean) < 0.02, (x.mean(), x_mean)     # 0 without the Hastings factor
+
+
+@pytest.mark.parametrize("form", ["plain", "batched"])
+def test_fp64_sweeps_follow_the_oracle_unforced(phast, orc, form):
+    # no imposed decisions: the GPU and the oracle walk the same chains move for
+    # move, so histograms, coordinates and per-type acceptance counts agree
+    from test_gpu_sweep import oracle_walkers
+    s = inputs.fene_sphere(8)
+    ctx = phast.Context(s, pair_precision=64)
+    k = np.arange(s.n_bins)
+    lnW = -0.02 * k + 0.6 * np.sin(k / 23.0)
+    n_sweeps = 500
+    hw = ctx.hist_walker_zeros()
+    ctx.sweep(n_sweeps, torch.from_numpy(lnW).cuda(), form=phast.FORM_PLAIN if form == "plain" else phast.FORM_BATCHED,
+              hist_walker=hw)
+    st = ctx.get_state("cpu")
+    torch.cuda.synchronize()
+    hw = hw.cpu().numpy().reshape(s.walkers, s.n_bins)
+    res = oracle_walkers(orc, s, lnW, n_sweeps * s.n_total)
+    xyz = st["xyz"].numpy().reshape(s.walkers, s.n_total, 3)
+    stt = ctx.stats()
+    for w, (wk, h, stats, _) in enumerate(res):
+        assert np.array_equal(hw[w].astype(np.uint64), h), f"walker {w}: histogram differs"
+        assert np.array_equal(xyz[w], wk.xyz), f"walker {w}: coordinates differ"
+        assert abs(float(st["E"][w]) - wk.E) < 1e-9 and int(st["bin"][w]) == wk.bin
+        assert np.array_equal(stt["attempts"][w], np.array(stats[:orc.N_MOVES]).astype(np.uint64))
+        assert np.array_equal(stt["accepts"][w], np.array(stats[orc.N_MOVES:2 * orc.N_MOVES]).astype(np.uint64))
+        assert stats[orc.N_MOVES + orc.BOND] > 0 and stats[orc.N_MOVES + orc.CAP] > 0
+    ctx.close()
