@@ -172,10 +172,14 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
+SWEEP_SOURCES = ("common.cuh", "group.cuh", "sweep.cu")   # what the sweep kernel is compiled from
+
+
 def csrc_digest() -> str:
+    """Digest of the sweep kernel's sources: a committed traffic figure counts only while it matches."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1702_01770_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
+    for fn in SWEEP_SOURCES:
         h.update(fn.encode())
         h.update(open(os.path.join(d, fn), "rb").read())
     return h.hexdigest()[:16]

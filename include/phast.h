@@ -321,7 +321,8 @@ int phast_micro_analysis(int32_t K, double e_min, double bin_width, const double
  * equal-area line on beta(E) is the common tangent of S(E): an edge of the
  * upper concave hull of (E_k, S_k) spanning bins below it.  Among those with
  * latent heat (E_b - E_a)/N >= tol_L across which beta_k = (S_{k+h} -
- * S_{k-h})/(2 h w) rises by >= tol_beta, the widest gives beta_c (its slope),
+ * S_{k-h})/(2 h w) rises by >= tol_beta, the widest (the first of equal
+ * width) gives beta_c (its slope),
  * eps_1 = E_a/N, eps_2 = E_b/N, the latent heat, and the barrier
  * max (hull - S) / (beta_c N) of f between the coexisting states.  beta_c > 0
  * fixes beta_c instead (no construction); 0 asks for it.
@@ -332,8 +333,8 @@ int phast_micro_analysis(int32_t K, double e_min, double bin_width, const double
  *       eps_2, latent, barrier, found (1/0)};
  *  err: dev [6] or NULL: jackknife errors of row 0 over the R rows (NaN unless
  *       every row found a transition); err[5] = the number of rows that did.
- * K <= PHAST_MAX_BINS (up to 192 KB of shared memory per CTA).  PHAST_EINVAL
- * for bad arguments. */
+ * K <= PHAST_MAX_BINS (13 bytes of shared memory per bin and CTA, 208 KB at
+ * the limit).  PHAST_EINVAL for bad arguments. */
 int phast_maxwell(int32_t K, double e_min, double bin_width, const double* lnW, const uint64_t* hist,
                   int32_t n_blocks, int32_t fd_half_width, int32_t n_monomers, double beta_c,
                   double tol_beta, double tol_L, double* f_out, double* rep, double* err, void* stream);

@@ -187,20 +187,44 @@ finish_kernel(int K, const double* __restrict__ T, int n_T, int R, int n_jk, Wor
 // tangent of S(E), an edge of the upper concave hull of (E_k, S_k) over the
 // visited bins that spans bins below it.  Among those whose latent heat is at
 // least tol_L and across which beta_k = (S_{k+h} - S_{k-h}) / (2 h w) rises by
-// at least tol_beta, the widest is taken.  One CTA per replicate: S in shared
-// memory, the hull and the selection on one thread (O(K)), f on all threads.
+// at least tol_beta, the widest is taken (the first of equal width).
+//
+// One CTA per replicate, S in shared memory.  The hull is Andrew's monotone
+// chain on one thread with the same FP64 orientation test throughout, so the
+// hull vertices are those of the sequential definition even for nearly
+// collinear bins; the test of three consecutive bins (k-2, k-1, k), the one
+// the chain meets wherever S is concave, is evaluated beforehand by all
+// threads, which leaves the serial loop almost free of FP64 instructions.
+// The edges, the rise of beta along them, the barrier and f run on all threads.
 // ---------------------------------------------------------------------------
+
+// E_k = e_min + (k + 1/2) w, each operation rounded separately.
+__device__ __forceinline__ double bin_centre(double e_min, double w, int k) {
+    return __dadd_rn(e_min, __dmul_rn(__dadd_rn((double)k, 0.5), w));
+}
+
+// Monotone-chain test: drop j (i < j < k) when it lies on or below the chord
+// from i to k.
+__device__ __forceinline__ bool chain_drops(const double* S, double e_min, double w, int i, int j, int k) {
+    const double ei = bin_centre(e_min, w, i), ej = bin_centre(e_min, w, j), ek = bin_centre(e_min, w, k);
+    return __dmul_rn(__dsub_rn(S[j], S[i]), __dsub_rn(ek, ei)) <= __dmul_rn(__dsub_rn(S[k], S[i]), __dsub_rn(ej, ei));
+}
+
+constexpr size_t kMaxwellSmemPerBin = sizeof(double) + sizeof(int) + 1;   // S, hull, precomputed test
+
 __global__ void __launch_bounds__(kThreads)
 maxwell_kernel(int K, double e_min, double w, const double* __restrict__ lnW,
                const unsigned long long* __restrict__ hist, int n_blocks, int h, int n_monomers, double beta_c_in,
                double tol_beta, double tol_L, double* __restrict__ f_out, double* __restrict__ rep) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* S = reinterpret_cast<double*>(smem_raw);                 // [K]
-    int* hull = reinterpret_cast<int*>(smem_raw + sizeof(double) * (size_t)K);   // [K]
+    double* S = reinterpret_cast<double*>(smem_raw);                                       // [K]
+    int* hull = reinterpret_cast<int*>(smem_raw + sizeof(double) * (size_t)K);             // [K]
+    uint8_t* pre = smem_raw + (sizeof(double) + sizeof(int)) * (size_t)K;                  // [K]
     __shared__ double red[32];
-    __shared__ double s_beta_c;
+    __shared__ int s_nh, s_best_q;
     const int r = blockIdx.x;
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    const double N = (double)n_monomers;
     double mx = -INFINITY;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         const double H = rep_hist(hist, n_blocks, K, r, k);
@@ -214,71 +238,108 @@ maxwell_kernel(int K, double e_min, double w, const double* __restrict__ lnW,
     for (int k = threadIdx.x; k < K; k += blockDim.x)
         if (!isnan(S[k])) S[k] -= mx;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const double N = (double)n_monomers;
-        auto Ek = [&](int k) { return e_min + ((double)k + 0.5) * w; };
-        double out[6] = {nan, nan, nan, nan, nan, 0.0};
+    // the chain test of (k-2, k-1, k): 1 drop, 0 keep, 2 not all three visited
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        uint8_t v = 2;
+        if (k >= 2 && isfinite(S[k]) && isfinite(S[k - 1]) && isfinite(S[k - 2]))
+            v = chain_drops(S, e_min, w, k - 2, k - 1, k) ? 1 : 0;
+        pre[k] = v;
+    }
+    if (threadIdx.x == 0) s_best_q = INT_MAX;
+    __syncthreads();
+    if (threadIdx.x == 0) {   // upper hull, left to right over the visited bins
         int nh = 0;
-        for (int k = 0; k < K; ++k) {   // monotone chain, upper hull
+        for (int k = 0; k < K; ++k) {
             if (!isfinite(S[k])) continue;
             while (nh >= 2) {
                 const int i = hull[nh - 2], j = hull[nh - 1];
-                if ((S[j] - S[i]) * (Ek(k) - Ek(i)) <= (S[k] - S[i]) * (Ek(j) - Ek(i))) --nh;
-                else break;
+                const bool drop = (i == k - 2 && j == k - 1) ? pre[k] == 1 : chain_drops(S, e_min, w, i, j, k);
+                if (!drop) break;
+                --nh;
             }
             hull[nh++] = k;
         }
-        int best_a = -1, best_b = -1;
-        double best_L = -1.0;
-        if (beta_c_in <= 0.0) {
-            for (int q = 0; q + 1 < nh; ++q) {
-                const int a = hull[q], b = hull[q + 1];
-                bool inside = false;
-                for (int k = a + 1; k < b; ++k) inside |= (bool)isfinite(S[k]);
-                if (!inside) continue;
-                const double L = (Ek(b) - Ek(a)) / N;
-                double rise = 0.0, bmin = INFINITY;
-                for (int k = a; k <= b; ++k) {
-                    if (k - h < 0 || k + h >= K || !isfinite(S[k - h]) || !isfinite(S[k + h])) continue;
-                    const double bk = (S[k + h] - S[k - h]) / (2.0 * h * w);
-                    if (bk - bmin > rise) rise = bk - bmin;
-                    if (bk < bmin) bmin = bk;
+        s_nh = nh;
+    }
+    __syncthreads();
+    const int nh = s_nh;
+    // qualifying edges, one warp per edge: latent heat, interior bins, the rise
+    // max_j (beta_j - min_{k<j} beta_k) over the edge's bins with a defined beta
+    double my_L = -1.0;
+    int my_q = INT_MAX;
+    if (beta_c_in <= 0.0) {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+        const double den = 2.0 * h * w;
+        for (int q = warp; q + 1 < nh; q += n_warps) {
+            const int a = hull[q], b = hull[q + 1];
+            if (b - a < 2) continue;
+            bool in = false;
+            for (int k = a + 1 + lane; k < b; k += 32) in |= (bool)isfinite(S[k]);
+            if (!__any_sync(0xffffffffu, in)) continue;
+            const double L = __ddiv_rn(__dsub_rn(bin_centre(e_min, w, b), bin_centre(e_min, w, a)), N);
+            double rise = 0.0, run_min = INFINITY;
+            for (int base = a; base <= b; base += 32) {
+                const int k = base + lane;
+                const bool ok = k <= b && k - h >= 0 && k + h < K && isfinite(S[k - h]) && isfinite(S[k + h]);
+                const double bk = ok ? (S[k + h] - S[k - h]) / den : INFINITY;
+                double incl = bk;   // inclusive prefix minimum over the lanes
+                for (int o = 1; o < 32; o <<= 1) {
+                    const double v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl = fmin(incl, v);
                 }
-                if (L >= tol_L && rise >= tol_beta && L > best_L) {
-                    best_L = L;
-                    best_a = a;
-                    best_b = b;
-                }
+                double excl = __shfl_up_sync(0xffffffffu, incl, 1);
+                excl = lane == 0 ? run_min : fmin(run_min, excl);
+                if (ok && bk - excl > rise) rise = bk - excl;
+                run_min = fmin(run_min, __shfl_sync(0xffffffffu, incl, 31));
+            }
+            for (int o = 16; o > 0; o >>= 1) rise = fmax(rise, __shfl_xor_sync(0xffffffffu, rise, o));
+            if (L >= tol_L && rise >= tol_beta && L > my_L) {   // q rises along this warp's edges
+                my_L = L;
+                my_q = q;
             }
         }
-        double bc = beta_c_in;
+    }
+    const double best_L = block_max(my_L, red);
+    if (best_L >= 0.0 && my_L == best_L) atomicMin(&s_best_q, my_q);
+    __syncthreads();
+    const int best_q = s_best_q;
+    double bc = beta_c_in;
+    int best_a = -1, best_b = -1;
+    if (best_q != INT_MAX) {
+        best_a = hull[best_q];
+        best_b = hull[best_q + 1];
+        bc = __ddiv_rn(__dsub_rn(S[best_b], S[best_a]),
+                       __dsub_rn(bin_centre(e_min, w, best_b), bin_centre(e_min, w, best_a)));
+    }
+    double gap = 0.0;   // the barrier: the largest drop of S below the common tangent
+    if (best_a >= 0) {
+        const double ea = bin_centre(e_min, w, best_a);
+        for (int k = best_a + 1 + threadIdx.x; k < best_b; k += blockDim.x) {
+            if (!isfinite(S[k])) continue;
+            const double line = __dadd_rn(S[best_a], __dmul_rn(bc, __dsub_rn(bin_centre(e_min, w, k), ea)));
+            if (line - S[k] > gap) gap = line - S[k];
+        }
+    }
+    gap = block_max(gap, red);
+    if (threadIdx.x == 0) {
+        double out[6] = {nan, nan, nan, nan, nan, 0.0};
         if (best_a >= 0) {
-            const double ea = Ek(best_a), eb = Ek(best_b);
-            bc = (S[best_b] - S[best_a]) / (eb - ea);
-            double gap = 0.0;
-            for (int k = best_a + 1; k < best_b; ++k) {
-                if (!isfinite(S[k])) continue;
-                const double line = S[best_a] + bc * (Ek(k) - ea);
-                if (line - S[k] > gap) gap = line - S[k];
-            }
+            const double ea = bin_centre(e_min, w, best_a), eb = bin_centre(e_min, w, best_b);
             out[0] = bc;
             out[1] = ea / N;
             out[2] = eb / N;
             out[3] = (eb - ea) / N;
-            out[4] = gap / (bc * N);
+            out[4] = gap / __dmul_rn(bc, N);
             out[5] = 1.0;
         } else if (beta_c_in > 0.0) {
             out[0] = beta_c_in;
         }
         for (int q = 0; q < 6; ++q) rep[(size_t)r * 6 + q] = out[q];
-        s_beta_c = bc;
     }
-    __syncthreads();
     if (r == 0 && f_out) {
-        const double bc = s_beta_c;
         for (int k = threadIdx.x; k < K; k += blockDim.x) {
-            const double ek = e_min + ((double)k + 0.5) * w;
-            f_out[k] = (isfinite(S[k]) && bc > 0.0) ? (ek - S[k] / bc) / (double)n_monomers : nan;
+            const double ek = bin_centre(e_min, w, k);
+            f_out[k] = (isfinite(S[k]) && bc > 0.0) ? (ek - S[k] / bc) / N : nan;
         }
     }
 }
@@ -408,10 +469,10 @@ extern "C" int phast_maxwell(int32_t K, double e_min, double bin_width, const do
     if (!(beta_c >= 0.0) || !(tol_beta >= 0.0) || !(tol_L >= 0.0))
         return phast_set_error(PHAST_EINVAL, "phast_maxwell: beta_c, tol_beta, tol_L must be >= 0");
     const int R = (hist && n_blocks >= 2) ? n_blocks : 0;
-    const size_t sm = (sizeof(double) + sizeof(int)) * (size_t)K;
+    const size_t sm = kMaxwellSmemPerBin * (size_t)K;
     cudaStream_t st = (cudaStream_t)stream;
     PHAST_CUDA_TRY(cudaFuncSetAttribute(maxwell_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)((sizeof(double) + sizeof(int)) * PHAST_MAX_BINS)));
+                                        (int)(kMaxwellSmemPerBin * PHAST_MAX_BINS)));
     maxwell_kernel<<<1 + R, kThreads, sm, st>>>(K, e_min, bin_width, lnW, reinterpret_cast<const unsigned long long*>(hist),
                                                 hist ? n_blocks : 0, fd_half_width, n_monomers, beta_c, tol_beta,
                                                 tol_L, f_out, rep);

@@ -84,3 +84,28 @@ def test_given_beta_and_plain_weights(phast, orc):
     _check_row(rep[0].cpu().numpy(), ro)
     assert np.allclose(f.cpu().numpy(), fo, rtol=1e-12, atol=1e-12)
     assert rep.shape == (1, 6) and float(err[5]) == 0.0
+
+
+def test_full_size_noisy_against_oracle(phast, orc):
+    # the benchmark's binning (8000 bins of 0.1 on [-400, 400), 440 monomers, 16
+    # blocks): an S-bend with Poisson noise and unvisited holes, so the hull has
+    # many short edges, gaps in the chain and one long edge scanned in chunks
+    K, e_min, w, N, B = 8000, -400.0, 0.1, 440, 16
+    E = e_min + (np.arange(K) + 0.5) * w
+    S = np.maximum(-(E + 150.0) ** 2 / 4000.0, 3.0 - (E - 120.0) ** 2 / 4000.0)
+    rng = np.random.default_rng(9)
+    lnW = -S
+    H = rng.poisson(40, size=(B, K)).astype(np.int64)
+    H[:, :300] = 0
+    H[:, 5000:5013] = 0
+    H[:, 7900:] = 0
+    f, rep, err = phast.phast_maxwell(torch.from_numpy(lnW).cuda(), torch.from_numpy(H).cuda(), e_min, w, N,
+                                      fd_half_width=5, tol_beta=0.001, tol_L=0.05)
+    rep = rep.cpu().numpy()
+    for r in range(B + 1):
+        Hr = H.sum(0) if r == 0 else H.sum(0) - H[r - 1]
+        fo, ro = orc.maxwell(_S_from(lnW, Hr), e_min, w, N, fd_half_width=5, tol_beta=0.001, tol_L=0.05)
+        _check_row(rep[r], ro)
+        if r == 0:
+            assert ro["found"] == 1.0
+            assert np.allclose(f.cpu().numpy(), fo, rtol=1e-12, atol=1e-12, equal_nan=True)
