@@ -69,7 +69,7 @@ delta_kernel(const SysDesc d, int B, const double* __restrict__ xyz, const phast
     const MoveSet M = move_set(d, P.type, P.chain, P.index);
     double dE = __longlong_as_double(0x7ff8000000000000ll);   // NaN for a degenerate or invalid move
     const bool ok = valid && make_new_positions<32, PT>(d, x64, P, M, s, g);
-    const bool wall = ok && !container_ok<32, PT>(d, x64, P, M, s, g, true, 0ull, 0ull);
+    const bool wall = ok && !container_ok<32, PT>(d, const_cast<double*>(x64), P, M, s, g, true, 0ull, 0ull, nullptr);
     if (wall) dE = INFINITY;   // beyond the container's wall
     if (ok && !wall) {
         double part = (double)local_delta<32, PT>(d, P, M, s, g);

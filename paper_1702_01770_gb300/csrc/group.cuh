@@ -580,11 +580,18 @@ __device__ bool make_new_positions(const SysDesc& d, const double* x64, const Pr
 // to the wall.  The same value on every lane of the group.
 // exact: P carries the exact FP64 move (else it is regenerated from the
 // walker's stream, key seed and move index t, as the replay does).
+// queued (FP32 sweep): accepted moves not yet replayed on x64; they are
+// replayed first, so that the exact test sees the current coordinates.
 // Kept out of line: the check runs only with a container, and its code stays
 // out of the instruction stream of the moves that need none.
+template <int TPW, bool GEOM = true>
+__device__ __noinline__ void flush_queue(const SysDesc& d, double* x64, uint64_t seed, Slot<float>& s, const Group<TPW>& g,
+                                         int count);
+
 template <int TPW, typename PT>
-__device__ __noinline__ bool container_ok(const SysDesc& d, const double* x64, const Proposal& P, const MoveSet& M,
-                                          Slot<PT>& s, const Group<TPW>& g, bool exact, uint64_t seed, uint64_t t) {
+__device__ __noinline__ bool container_ok(const SysDesc& d, double* x64, const Proposal& P, const MoveSet& M,
+                                          Slot<PT>& s, const Group<TPW>& g, bool exact, uint64_t seed, uint64_t t,
+                                          int* queued) {
     if (!d.has_sphere) return true;
     const int m = M.hi - M.lo + 1;
     const unsigned gm = TPW == 32 ? 0xffffffffu : ((1u << TPW) - 1u);
@@ -606,6 +613,10 @@ __device__ __noinline__ bool container_ok(const SysDesc& d, const double* x64, c
             unsure |= fabsf(r2 - R2) <= band;
         }
         if ((__ballot_sync(g.mask, unsure) >> g.base) & gm) {   // near the wall: the exact positions decide
+            if (queued && *queued > 0) {
+                flush_queue<TPW, true>(d, x64, seed, s, g, *queued);
+                *queued = 0;
+            }
             Proposal E = P;
             if (!exact) {
                 propose_select(d, stream_block(seed, t, 0u), stream_block(seed, t, 1u), stream_block(seed, t, 2u), &E);
@@ -671,7 +682,7 @@ __device__ void accept_move32(const SysDesc& d, const Proposal& P, uint64_t t, c
 // once, one move per lane; centres are read from the coordinates as each move
 // is made.  Then the working copy of the chains they moved is refreshed from
 // the exact coordinates.
-template <int TPW, bool GEOM = true>
+template <int TPW, bool GEOM>
 __device__ __noinline__ void flush_queue(const SysDesc& d, double* x64, uint64_t seed, Slot<float>& s, const Group<TPW>& g,
                             int count) {
     if (count == 0) return;

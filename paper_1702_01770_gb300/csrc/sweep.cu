@@ -166,7 +166,9 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         const bool ok = make_new_positions<TPW, PT, GEOM>(sd, x64, P, M, slot, g, &jac);
         // a trial position beyond the container's wall: infinite energy, not evaluated
         bool wall = false;
-        if constexpr (GEOM) wall = ok && sd.has_sphere && !container_ok<TPW, PT>(sd, x64, P, M, slot, g, sizeof(PT) == 8, seed, t);
+        if constexpr (GEOM)
+            wall = ok && sd.has_sphere &&
+                   !container_ok<TPW, PT>(sd, x64, P, M, slot, g, sizeof(PT) == 8, seed, t, sizeof(PT) == 4 ? &queued : nullptr);
         const bool eval = ok && !wall;
         DF dE32{0.0f, 0.0f};
         double dE64 = 0.0;

@@ -208,3 +208,58 @@ def test_fp64_sweeps_follow_the_oracle_unforced(phast, orc, form):
         assert np.array_equal(stt["accepts"][w], np.array(stats[orc.N_MOVES:2 * orc.N_MOVES]).astype(np.uint64))
         assert stats[orc.N_MOVES + orc.BOND] > 0 and stats[orc.N_MOVES + orc.CAP] > 0
     ctx.close()
+
+
+def _tight_sphere(walkers):
+    """One Fibonacci 13-mer with FENE bonds pressed into a sphere of radius 2.6:
+    its monomers meet the wall all the time."""
+    import dataclasses
+    rng = np.random.Generator(np.random.Philox(11))
+    while True:
+        x = inputs.random_saw(13, 1.0, rng)
+        x = x - x.mean(axis=0)
+        if np.max(np.linalg.norm(x, axis=1)) <= 2.0:
+            break
+    return dataclasses.replace(inputs.fene_sphere(walkers), name="tight_sphere", chain_len=np.array([13], np.int32),
+                               seq=inputs.fibonacci_sequence(13), sphere_R=2.6, xyz0=x)
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_tight_sphere_stays_inside(phast, orc, precision):
+    # near the wall the FP32 sweep decides with the exact positions, which must
+    # include the accepted moves still waiting for their exact replay
+    s = _tight_sphere(4096)
+    ctx = phast.Context(s, pair_precision=precision)
+    n_tr, n_sweeps = 6, 300
+    k = np.arange(s.n_bins)
+    lnW = -0.02 * k
+    trace = ctx.trace_buffer(n_sweeps, n_tr)
+    ctx.sweep(n_sweeps, torch.from_numpy(lnW).cuda(), trace=trace, trace_walkers=n_tr)
+    st = ctx.get_state("cpu")
+    torch.cuda.synchronize()
+    xyz = st["xyz"].numpy().reshape(s.walkers, s.n_total, 3)
+    r2 = (xyz[..., 0] * xyz[..., 0] + xyz[..., 1] * xyz[..., 1]) + xyz[..., 2] * xyz[..., 2]
+    assert np.all(r2 <= s.sphere_R ** 2), int(np.sum(np.any(r2 > s.sphere_R ** 2, axis=1)))
+    assert np.mean(np.max(r2, axis=1) > (0.95 * s.sphere_R) ** 2) > 0.3     # the chains do press on the wall
+    m, mu = oracle_model(orc, s), oracle_muca(orc, s)
+    E = st["E"].numpy()
+    for w in range(0, s.walkers, 97):
+        assert abs(orc.energy(m, xyz[w]) - E[w]) <= 1e-3 * max(1.0, abs(E[w])), w
+    # the traced walkers' wall rejections agree with the oracle's replay
+    tr = trace.cpu().numpy().view(phast.TRACE_DTYPE).reshape(n_tr, -1)
+    seeds = s.seeds()
+    for w in range(n_tr):
+        wk = orc.new_walker(m, mu, s.xyz0, int(seeds[w]))
+        f = tr[w]["accepted"].astype(np.int8)
+        _, stats, rec = orc.sweep_walker(m, mu, lnW, wk, n_sweeps * s.n_total, force=f, record=True)
+        inf_o, inf_g = np.isinf(rec["dE"]), np.isinf(tr[w]["dE"])
+        one = inf_o != inf_g
+        if precision == 64:
+            assert not np.any(one), w
+        else:   # an FP32 bond at the edge of its range: infinite on one side only, rejected by both
+            E_prev = np.concatenate([[orc.energy(m, s.xyz0)], rec["E_after"][:-1]])
+            fin = np.where(inf_o, tr[w]["dE"], rec["dE"])
+            assert np.all(E_prev[one] + fin[one] >= s.e_min + s.bin_width * s.n_bins), w
+            assert not np.any(tr[w]["accepted"][one]), w
+        assert np.array_equal(xyz[w], wk.xyz), w
+    ctx.close()
