@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-grad", action="store_true")
     ap.add_argument("--no-geom", action="store_true")
+    ap.add_argument("--geom-only", action="store_true")
+    ap.add_argument("--geom-tile", type=int, nargs=2, default=None, metavar=("TPW", "WPC"))
     return ap.parse_args()
 
 
@@ -197,6 +199,49 @@ def traffic_per_launch(walkers: int):
     return j["dram_bytes_per_walker"] * walkers
 
 
+def measure_geometry(args, dev):
+    """The paper's own geometry: steric sphere, FENE bonds, bond-length and cap moves
+    (the batched kernel's build with them), two Fibonacci 13-mers, FP32 pair terms."""
+    import torch
+
+    from paper_1702_01770_gb300 import inputs, phast
+    gsys = inputs.fene_sphere(walkers=GEOM_WALKERS)
+    gctx = phast.Context(gsys, pair_precision=32)
+    glnW = torch.zeros(gsys.n_bins, dtype=torch.float64, device=dev)
+    if args.geom_tile:
+        gctx.set_tile(*args.geom_tile)
+    else:
+        gctx.autotune(glnW, sweeps=2)   # small chains: the best tile depends on the workload
+    gtile = gctx.get_tile()
+    gctx.sweep(20, glnW)
+    torch.cuda.synchronize()
+    g0 = gctx.stats()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    gctx.sweep(GEOM_SWEEPS, glnW)
+    b.record()
+    torch.cuda.synchronize()
+    g1 = gctx.stats()
+    gms = a.elapsed_time(b)
+    gmoves = int(g1["attempts"].sum() - g0["attempts"].sum())
+    assert gmoves == GEOM_WALKERS * gsys.n_total * GEOM_SWEEPS
+    res = {
+        "workload": "2 Fibonacci 13-mers in a steric sphere R = 8, FENE bonds (k_F = -20, R_F = 0.3), "
+                    f"all six move types, {GEOM_WALKERS} walkers, flat weights, {GEOM_SWEEPS} sweeps",
+        "kernel": f"sweep_batched_kernel<{gtile[0]},float,1>", "tile": list(gtile),
+        "walker_moves_per_s": gmoves / (gms / 1e3),
+        "pair_evals_per_s": float((g1["pair_evals"].sum() - g0["pair_evals"].sum()) / (gms / 1e3)),
+        "accept_rate": float((g1["accepts"].sum() - g0["accepts"].sum()) / gmoves), "dtype": "f32",
+        "l2": "walker state %.0f MB, L2-resident" % (GEOM_WALKERS * gsys.n_total * 24 / 1e6)}
+    if not args.no_cpu_baseline:
+        v, pev, n, dt = oracle_walker_moves_per_s(inputs.fene_sphere(walkers=1), 4.0, os.cpu_count() or 1)
+        res["cpu_baseline"] = {"value": v, "unit": "walker-moves/s", "cores": os.cpu_count() or 1,
+                               "kind": "oracle", "sample": f"{n} walkers x 1 sweep, FP64 oracle, "
+                                                           f"{dt:.1f} s", "pair_evals_per_s": pev}
+    gctx.close()
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -208,6 +253,10 @@ def run_ours(args):
         torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.geom_only:   # the geometry measurement alone (a profiling aid)
+        if rank == 0:
+            print(json.dumps({"geometry": measure_geometry(args, dev)}), flush=True)
+        return
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -361,37 +410,8 @@ def run_ours(args):
         out["maxwell"] = {"ms_per_call": a.elapsed_time(b) / reps, "bins": K, "replicates": 1 + N_JK,
                           "outputs": "f(E) per monomer; beta_c, eps_1, eps_2, latent heat, barrier, with errors"}
 
-    # the paper's own geometry: steric sphere, FENE bonds, bond-length and cap moves
-    # (the batched kernel's build with them), two Fibonacci 13-mers, FP32 pair terms
     if not args.no_geom and rank == 0:
-        gsys = inputs.fene_sphere(walkers=GEOM_WALKERS)
-        gctx = phast.Context(gsys, pair_precision=32)
-        glnW = torch.zeros(gsys.n_bins, dtype=torch.float64, device=dev)
-        gctx.sweep(20, glnW)
-        torch.cuda.synchronize()
-        g0 = gctx.stats()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        gctx.sweep(GEOM_SWEEPS, glnW)
-        b.record()
-        torch.cuda.synchronize()
-        g1 = gctx.stats()
-        gms = a.elapsed_time(b)
-        gmoves = int(g1["attempts"].sum() - g0["attempts"].sum())
-        assert gmoves == GEOM_WALKERS * gsys.n_total * GEOM_SWEEPS
-        out["geometry"] = {
-            "workload": "2 Fibonacci 13-mers in a steric sphere R = 8, FENE bonds (k_F = -20, R_F = 0.3), "
-                        f"all six move types, {GEOM_WALKERS} walkers, flat weights, {GEOM_SWEEPS} sweeps",
-            "kernel": "sweep_batched_kernel<32,float,1>", "walker_moves_per_s": gmoves / (gms / 1e3),
-            "pair_evals_per_s": float((g1["pair_evals"].sum() - g0["pair_evals"].sum()) / (gms / 1e3)),
-            "accept_rate": float((g1["accepts"].sum() - g0["accepts"].sum()) / gmoves), "dtype": "f32",
-            "l2": "walker state %.0f MB, L2-resident" % (GEOM_WALKERS * gsys.n_total * 24 / 1e6)}
-        if not args.no_cpu_baseline:
-            v, pev, n, dt = oracle_walker_moves_per_s(inputs.fene_sphere(walkers=1), 4.0, os.cpu_count() or 1)
-            out["geometry"]["cpu_baseline"] = {"value": v, "unit": "walker-moves/s", "cores": os.cpu_count() or 1,
-                                               "kind": "oracle", "sample": f"{n} walkers x 1 sweep, FP64 oracle, "
-                                                                           f"{dt:.1f} s", "pair_evals_per_s": pev}
-        gctx.close()
+        out["geometry"] = measure_geometry(args, dev)
 
     # end to end through the C ABI with host buffers: state in from pinned host memory, results out
     if not args.no_e2e:
