@@ -211,7 +211,7 @@ def measure_geometry(args, dev):
     if args.geom_tile:
         gctx.set_tile(*args.geom_tile)
     else:
-        gctx.autotune(glnW, sweeps=2)   # small chains: the best tile depends on the workload
+        gctx.autotune(glnW, sweeps=10)   # small chains: the best tile depends on the workload
     gtile = gctx.get_tile()
     gctx.sweep(20, glnW)
     torch.cuda.synchronize()
@@ -327,7 +327,7 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                 "frac": achieved_tf / peak_tf, "traffic": traffic_per_launch(args.walkers),
                 "peak_basis": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz (max SM clock)",
-                "kernel": "sweep_batched_kernel<32,float,0> (no FENE, sphere, bond or cap moves)",
+                "kernel": "sweep_batched_kernel<32,float,0,1> (no FENE, sphere, bond or cap moves)",
                 "frac_at_median_clock": (achieved_tf / (n_sm * 256 * clocks["sm_mhz"] * 1e6 / 1e12))
                 if clocks.get("sm_mhz") else None}
 

@@ -1005,6 +1005,11 @@ __device__ DF pair_delta32(const SysDesc& d, const MoveSet& M, int mchain, const
     const int full = U / (TPW * R) * (TPW * R);       // partners in chunks of R per lane
     const int full1 = U / TPW * TPW;                    // then one per lane
     DF sum{0.0f, 0.0f};
+    if constexpr (TPW < 32) {   // small systems: one partner per lane, the shortest code
+        for (int t = g.lane; t < U; t += TPW)
+            sum = df_add(sum, DF{pair_chunk32<1, PBC>(d, M, mchain, m, t, TPW, s.r, s.D, mv), 0.0f});
+        return sum;
+    }
     int t0 = g.lane;
     for (; t0 < full; t0 += TPW * R) sum = df_add(sum, DF{pair_chunk32<R, PBC>(d, M, mchain, m, t0, TPW, s.r, s.D, mv), 0.0f});
     for (; t0 < full1; t0 += TPW) sum = df_add(sum, DF{pair_chunk32<1, PBC>(d, M, mchain, m, t0, TPW, s.r, s.D, mv), 0.0f});
