@@ -109,7 +109,8 @@ typedef struct {
  * `angle` around unit `axis`; translation by `disp`; rotation of the chain
  * about its centroid; crankshaft of monomer `index` about its neighbours' axis
  * (axis ignored); bond-length change of bond `index` (monomers index and
- * index+1) by `angle` (the shorter side slides along the bond); spherical cap:
+ * index+1) by `angle` (the shorter side slides along the bond; a change that
+ * takes the bond through zero length is no move, dE NaN); spherical cap:
  * monomer `index` alone rotated by `angle` around `axis` through its bonded
  * neighbour index-1 (monomer 1 for index 0). */
 typedef struct {
@@ -199,9 +200,11 @@ enum { PHAST_FORM_BATCHED = 0, PHAST_FORM_PLAIN = 1 };
 
 /* n_sweeps sweeps (a sweep = N_s move attempts) of every walker with the
  * tabulated log-weights lnW (dev, concatenated per type [n_bins_s]): propose
- * (Philox stream), dE from the changed terms, accept with min(1, W(E')/W(E)),
- * count the current bin after every attempt.  Proposals out of range or with
- * non-finite dE are rejected.  Every recompute_every sweeps (by each walker's
+ * (Philox stream), dE from the changed terms, accept with min(1, W(E')/W(E))
+ * (times ((r + delta) / r)^2 for a bond-length move, the Jacobian of its
+ * radial map), count the current bin after every attempt.  Proposals out of
+ * range, beyond the sphere or with non-finite dE are rejected.  Every
+ * recompute_every sweeps (by each walker's
  * own move index) the running energy is replaced by an FP64 full energy.
  *  form: PHAST_FORM_BATCHED (shared-memory tiles, FP32 or FP64 pairs per
  *        mp.pair_precision) or PHAST_FORM_PLAIN (one walker per CTA, all FP64,
