@@ -62,7 +62,8 @@ def check_fp32_trace_dE(orc, s, lnW, seed, dE_gpu, rec, force, label=""):
     m, mu = oracle_model(orc, s), oracle_muca(orc, s)
     ok = np.isfinite(rec["dE"])
     assert np.array_equal(ok, np.isfinite(dE_gpu)), label
-    err = np.where(ok, np.abs(dE_gpu - rec["dE"]), 0.0)
+    err = np.zeros(ok.shape)
+    err[ok] = np.abs(dE_gpu[ok] - rec["dE"][ok])
     base = 1e-4 * np.maximum(1.0, np.abs(np.where(ok, rec["dE"], 0.0)))
     worst = 0.0
     for k in np.nonzero(err > base)[0]:

@@ -263,3 +263,29 @@ def test_tight_sphere_stays_inside(phast, orc, precision):
             assert not np.any(tr[w]["accepted"][one]), w
         assert np.array_equal(xyz[w], wk.xyz), w
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_bond_move_edge_cases(phast, orc, precision):
+    # a bond shrunk through zero length is no move (NaN, coordinates unchanged);
+    # a stretch beyond the FENE range and a step into the wall are infinite
+    s = inputs.fene_sphere(1)
+    x = _states(orc, s, 1, 5)[0]
+    m = oracle_model(orc, s)
+    r3 = float(np.linalg.norm(x[4] - x[3]))
+    mvs = [orc.make_move(orc.BOND, 0, 3, angle=-(r3 + 0.5)),     # through zero length
+           orc.make_move(orc.BOND, 0, 3, angle=0.35),            # |r - r0| beyond R = 0.3
+           orc.make_move(orc.BOND, 1, 6, angle=0.02),            # an ordinary stretch
+           orc.make_move(orc.TRANS, 0, 0, disp=(30.0, 0.0, 0.0))]  # into the wall
+    arr = np.zeros(len(mvs), phast.MOVE_DTYPE)
+    for i, mv in enumerate(mvs):
+        arr[i] = (mv.type, mv.chain, mv.index, 0, tuple(mv.axis), mv.angle, tuple(mv.disp))
+    xs = torch.from_numpy(np.broadcast_to(x, (len(mvs),) + x.shape).copy()).cuda()
+    dE, xn = phast.phast_delta_energy(s, xs, arr, precision, want_xyz=True)
+    dE, xn = dE.cpu().numpy(), xn.cpu().numpy()
+    ref = [orc.delta_energy(m, x, mv) for mv in mvs]
+    assert np.isnan(ref[0][0]) and np.isnan(dE[0]) and np.array_equal(xn[0], x)
+    assert ref[1][0] == np.inf and dE[1] == np.inf
+    assert np.isfinite(dE[2]) and np.array_equal(xn[2], ref[2][1])
+    assert abs(dE[2] - ref[2][0]) <= (1e-9 if precision == 64 else 1e-4) * max(1.0, abs(ref[2][0]))
+    assert ref[3][0] == np.inf and dE[3] == np.inf

@@ -24,9 +24,13 @@ def _hs_offsets(ctx, n_jk):
     return out
 
 
+@pytest.mark.parametrize("workload", ["four types", "sphere"])
 @pytest.mark.parametrize("precision", [32, 64])
-def test_graph_iterations_equal_eager_calls(phast, precision):
-    systems = inputs.config2(walkers_each=8)      # four uneven system types in one launch
+def test_graph_iterations_equal_eager_calls(phast, precision, workload):
+    if workload == "four types":
+        systems = inputs.config2(walkers_each=8)  # four uneven system types in one launch
+    else:
+        systems = [inputs.fene_sphere(24)]        # FENE bonds, the sphere, all six move types
     n_jk, S, iters = 2, 15, 3
     a = phast.Context(systems, pair_precision=precision)
     b = phast.Context(systems, pair_precision=precision)
