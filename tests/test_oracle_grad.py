@@ -1,6 +1,8 @@
 """Pins of the oracle's energy derivatives and reweighted sensitivities.
 
 * A straight AAB trimer's gradient and dE/dC_AB in closed form (exact binary values).
+* The FENE bond term's gradient through the finite differences of a stretched
+  two-13-mer conformation in the sphere (bond terms about 8 of its 11 units).
 * dE/dx against central finite differences of the (separately pinned) energy, at
   h = 1e-3 and, tighter, at h = 1e-5, on conformations of several workloads.
 * dE/dp is exact: the energy is linear in every parameter.
@@ -26,7 +28,18 @@ def _cases():
     x2 = random_conformations(s2, 1, 6)[0]
     s8 = inputs.config2(1)[3]          # eight 9-mers, periodic L = 30
     x8 = random_conformations(s8, 1, 7, d_min=0.85)[0]
-    return [("fib55", s3, x3[0]), ("fib13", s13, x13), ("2x34", s2, x2), ("8x9", s8, x8)]
+    sf = inputs.fene_sphere(1)         # FENE bonds stretched up to 0.8 R, inside the sphere
+    return [("fib55", s3, x3[0]), ("fib13", s13, x13), ("2x34", s2, x2), ("8x9", s8, x8),
+            ("fene", sf, _fene_state(sf))]
+
+
+def _fene_state(s):
+    import oracle as orc
+    from helpers import oracle_muca
+    m, mu = oracle_model(orc, s), oracle_muca(orc, s)
+    wk = orc.new_walker(m, mu, s.xyz0, 3)
+    orc.sweep_walker(m, mu, -0.05 * np.arange(s.n_bins), wk, 26 * 50)
+    return wk.xyz.copy()
 
 
 CASES = _cases()
