@@ -94,10 +94,29 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
-// Block b of move t of the walker keyed by `seed`.
+// The same rounds kept out of line and not unrolled: one short copy of the
+// code.  Small systems, whose per-move path does not stay in the instruction
+// cache, run faster with it; the one-warp-per-walker build keeps the unrolled
+// rounds inline.
+static __device__ __noinline__ uint4 philox4x32_10_outline(uint4 c, uint2 k) {
+#pragma unroll 1
+    for (int r = 0; r < 10; ++r) {
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Block b of move t of the walker keyed by `seed` (OUTLINE: the out-of-line rounds).
+template <bool OUTLINE = false>
 __device__ __forceinline__ uint4 stream_block(uint64_t seed, uint64_t t, uint32_t b) {
-    return philox4x32_10(make_uint4((uint32_t)t, (uint32_t)(t >> 32), b, PHAST_STREAM_TAG),
-                         make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+    const uint4 c = make_uint4((uint32_t)t, (uint32_t)(t >> 32), b, PHAST_STREAM_TAG);
+    const uint2 k = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    if constexpr (OUTLINE) return philox4x32_10_outline(c, k);
+    else return philox4x32_10(c, k);
 }
 
 // Uniform in (0,1) from 52 bits, exact: ((a>>6) 2^26 + (b>>6) + 1/2) 2^-52.

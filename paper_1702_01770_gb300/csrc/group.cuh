@@ -279,7 +279,7 @@ __device__ Proposal propose_group(const SysDesc& d, uint64_t seed, uint64_t t, u
         while (bits == 0 && (round + 1) * TPW <= 2 + PHAST_MARSAGLIA_TRIES) {
             ++round;
             const uint32_t blkid = (uint32_t)(round * TPW + g.lane);
-            mine = stream_block(seed, t, blkid);
+            mine = stream_block<(TPW < 32 || GEOM)>(seed, t, blkid);
             ok = blkid <= 2 + PHAST_MARSAGLIA_TRIES && disc_test(mine, &v1f, &v2f, &sf);
             bits = (__ballot_sync(g.mask, ok) >> g.base) & gm;
         }
@@ -335,10 +335,11 @@ __device__ double3 centroid_tree(const double* x64, int o, int n, const Group<TP
 }
 
 // Exact FP64 axis of a pivot or rotation: the winning Marsaglia attempt replayed.
+template <bool OUTLINE = false>
 __device__ __forceinline__ double3 exact_axis(uint64_t seed, uint64_t t, int attempt) {
     if (attempt < 0) return make_double3(0.0, 0.0, 1.0);
     double v1, v2, s;
-    marsaglia_in_disc(stream_block(seed, t, 3u + (uint32_t)attempt), &v1, &v2, &s);
+    marsaglia_in_disc(stream_block<OUTLINE>(seed, t, 3u + (uint32_t)attempt), &v1, &v2, &s);
     return marsaglia_axis(v1, v2, s);
 }
 
@@ -692,10 +693,12 @@ __device__ __noinline__ void flush_queue(const SysDesc& d, double* x64, uint64_t
     if (g.lane < count) {   // the exact proposal of queued move `lane`, regenerated from its stream blocks
         const QEntry e = s.queue[g.lane];
         Proposal Q;
-        propose_select(d, stream_block(seed, e.t, 0u), stream_block(seed, e.t, 1u), stream_block(seed, e.t, 2u), &Q);
+        constexpr bool OUT = TPW < 32 || GEOM;
+        propose_select(d, stream_block<OUT>(seed, e.t, 0u), stream_block<OUT>(seed, e.t, 1u),
+                       stream_block<OUT>(seed, e.t, 2u), &Q);
         if constexpr (!GEOM) __builtin_assume(Q.type >= 0 && Q.type < PHAST_BOND);
         if (Q.type == PHAST_PIVOT || Q.type == PHAST_ROT || Q.type == PHAST_CAP) {
-            const double3 ax = exact_axis(seed, e.t, e.attempt);
+            const double3 ax = exact_axis<OUT>(seed, e.t, e.attempt);
             double sn, cs;
             taylor_sincos(Q.angle, &sn, &cs);
             Rl = rodrigues(ax.x, ax.y, ax.z, sn, cs);

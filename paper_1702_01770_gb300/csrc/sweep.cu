@@ -157,7 +157,8 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
     // from the same broadcast values; lane 0 alone writes histograms and counters.
     double lnw_here = __ldg(lnW + bin);
     float erel = (float)(E - sd.e_min);                     // FP32 image of E - e_min (FP32 mode)
-    uint4 blk = stream_block(seed, t, (uint32_t)g.lane);    // this lane's block of the current move
+    constexpr bool OUT = TPW < 32 || GEOM;                  // the Philox rounds out of line
+    uint4 blk = stream_block<OUT>(seed, t, (uint32_t)g.lane);   // this lane's block of the current move
     for (int64_t it = 0; it < n_moves; ++it) {
         const Proposal P = propose_group<TPW, PT, GEOM>(sd, seed, t, blk, g);
         if constexpr (!GEOM) __builtin_assume(P.type >= 0 && P.type < PHAST_BOND);   // no bond or cap moves
@@ -189,7 +190,7 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         int b_new = -1;
         if (finite) b_new = sizeof(PT) == 4 ? bin_after(sd, E, erel, dE32) : bin_of(sd, E + dE64);
         const double lnw_new = __ldg(lnW + (b_new >= 0 ? b_new : bin));
-        blk = stream_block(seed, t + 1, (uint32_t)g.lane);   // next move's block, while the load is in flight
+        blk = stream_block<OUT>(seed, t + 1, (uint32_t)g.lane);   // next move's block, while the load is in flight
         bool acc = false;
         if (b_new >= 0) {
             const double dl = lnw_new - lnw_here;
