@@ -115,6 +115,9 @@ def lib():
                                          P(C.c_double), P(C.c_double), P(C.c_double),
                                          P(C.c_double), P(C.c_double), P(C.c_double),
                                          P(C.c_double)]
+        L.orc_micro_binned.argtypes = ([C.c_int32, C.c_double, C.c_double, P(C.c_double), P(C.c_double),
+                                        C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P(C.c_double)]
+                                       + [P(C.c_double)] * 12)
         _lib = L
     return _lib
 
@@ -348,6 +351,28 @@ def berg_update(H, lnW, g_acc, bin_width: float = 1.0):
     lib().orc_berg_update(C.c_int32(H.size), C.c_double(bin_width), _ptr(H, C.c_double),
                           _ptr(lnW, C.c_double), _ptr(g_acc, C.c_double), _ptr(flat, C.c_double))
     return lnW, g_acc, flat
+
+
+def micro_binned(lnW, e_min: float, bin_width: float, H=None, block: int = 1, fd_half_width: int = 1,
+                 n_monomers: int = 1, T=()):
+    """Binning over iterations: lnW [n_it, K] and H [n_it, K] (or None) one row per
+    iteration; returns the values and their *_err, as micro_analysis's keys."""
+    lnW = np.ascontiguousarray(lnW, dtype=np.float64)
+    n_it, K = lnW.shape
+    Hh = None if H is None else np.ascontiguousarray(H, dtype=np.float64)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    nT = max(T.size, 1)
+    out = {k: np.zeros(n) for k, n in (("S", K), ("beta", K), ("CV", K), ("E_T", nT), ("cV_T", nT), ("peak", 2))}
+    err = {k + "_err": np.zeros(v.size) for k, v in out.items()}
+    lib().orc_micro_binned(C.c_int32(K), C.c_double(e_min), C.c_double(bin_width), _ptr(lnW, C.c_double),
+                           _ptr(Hh, C.c_double) if Hh is not None else None, C.c_int32(n_it), C.c_int32(block),
+                           C.c_int32(fd_half_width), C.c_int32(n_monomers), C.c_int32(T.size), _ptr(T, C.c_double),
+                           *[_ptr(out[k], C.c_double) for k in ("S", "beta", "CV", "E_T", "cV_T", "peak")],
+                           *[_ptr(err[k + "_err"], C.c_double) for k in ("S", "beta", "CV", "E_T", "cV_T", "peak")])
+    res = {**out, **err}
+    for k in ("E_T", "cV_T", "E_T_err", "cV_T_err"):
+        res[k] = res[k][: T.size]
+    return res
 
 
 def micro_analysis(lnW, e_min: float, bin_width: float, H=None, fd_half_width: int = 1,

@@ -777,6 +777,69 @@ void orc_micro_analysis(int32_t K, double e_min, double bin_width, const double*
 }
 
 /* ------------------------------------------------------------------------- */
+/* Error bars by binning over iterations (Sec. 4.1, ANALYST: data blocks of     */
+/* dN iterations of the range [N_S, N_E], the binning method).  Iteration i     */
+/* (row i of lnW and, if given, of H) is analysed alone as orc_micro_analysis   */
+/* does; each observable is averaged over n_b = n_it / block consecutive        */
+/* blocks of `block` iterations (a remainder at the end is left out).  The      */
+/* value is the mean of the block means B_b, the error                          */
+/* sqrt(sum_b (B_b - mean)^2 / (n_b (n_b - 1))), NaN for n_b < 2.  A bin left   */
+/* unvisited by any iteration of the range stays NaN.                           */
+/* ------------------------------------------------------------------------- */
+static void orc_binning(const double* v, size_t stride, int n_it, int block, double* val, double* err) {
+    int n_b = n_it / block;
+    double* bm = (double*)malloc(sizeof(double) * (size_t)(n_b > 0 ? n_b : 1));
+    double mean = 0.0;
+    for (int b = 0; b < n_b; ++b) {
+        double s = 0.0;
+        for (int i = b * block; i < (b + 1) * block; ++i) s = s + v[(size_t)i * stride];
+        bm[b] = s / (double)block;
+        mean = mean + bm[b];
+    }
+    mean = mean / (double)n_b;
+    *val = mean;
+    if (n_b < 2) {
+        *err = NAN;
+    } else {
+        double q = 0.0;
+        for (int b = 0; b < n_b; ++b) q = q + (bm[b] - mean) * (bm[b] - mean);
+        *err = sqrt(q / ((double)n_b * (double)(n_b - 1)));
+    }
+    free(bm);
+}
+
+void orc_micro_binned(int32_t K, double e_min, double bin_width, const double* lnW, const double* H,
+                      int32_t n_it, int32_t block, int32_t h, int32_t n_monomers, int32_t n_T, const double* T,
+                      double* S, double* beta, double* CV, double* E_T, double* cV_T, double* peak,
+                      double* S_err, double* beta_err, double* CV_err, double* E_T_err, double* cV_T_err,
+                      double* peak_err) {
+    size_t nk = (size_t)n_it * (size_t)K, nt = (size_t)n_it * (size_t)(n_T > 0 ? n_T : 1);
+    double* s = (double*)malloc(sizeof(double) * nk);
+    double* b = (double*)malloc(sizeof(double) * nk);
+    double* c = (double*)malloc(sizeof(double) * nk);
+    double* et = (double*)malloc(sizeof(double) * nt);
+    double* cv = (double*)malloc(sizeof(double) * nt);
+    double* pk = (double*)malloc(sizeof(double) * 2 * (size_t)n_it);
+    for (int i = 0; i < n_it; ++i) {
+        size_t o = (size_t)i * (size_t)K, ot = (size_t)i * (size_t)(n_T > 0 ? n_T : 1);
+        pk[2 * i] = pk[2 * i + 1] = NAN;
+        orc_micro_analysis(K, e_min, bin_width, lnW + o, H ? H + o : NULL, h, n_monomers, n_T, T,
+                           s + o, b + o, c + o, et + ot, cv + ot, pk + 2 * i);
+    }
+    for (int k = 0; k < K; ++k) {
+        orc_binning(s + k, (size_t)K, n_it, block, &S[k], &S_err[k]);
+        orc_binning(b + k, (size_t)K, n_it, block, &beta[k], &beta_err[k]);
+        orc_binning(c + k, (size_t)K, n_it, block, &CV[k], &CV_err[k]);
+    }
+    for (int i = 0; i < n_T; ++i) {
+        orc_binning(et + i, (size_t)n_T, n_it, block, &E_T[i], &E_T_err[i]);
+        orc_binning(cv + i, (size_t)n_T, n_it, block, &cV_T[i], &cV_T_err[i]);
+    }
+    for (int q = 0; q < 2; ++q) orc_binning(pk + q, 2, n_it, block, &peak[q], &peak_err[q]);
+    free(s); free(b); free(c); free(et); free(cv); free(pk);
+}
+
+/* ------------------------------------------------------------------------- */
 /* Derivatives of the energy of Eq. 2/3 (with the torsion term), for the      */
 /* force-field sensitivities: every term differentiated by hand, in the same  */
 /* loops as orc_energy.  Parameters p = (C_AA, C_BB, C_AB, kappa, kappa_C):   */

@@ -135,6 +135,16 @@ void orc_micro_analysis(int32_t K, double e_min, double bin_width, const double*
                         double* S, double* beta, double* CV,
                         double* E_T, double* cV_T, double* peak);
 
+/* Binning over iterations (Sec. 4.1): rows i < n_it of lnW and H (nullable)
+ * analysed one by one, each observable averaged over n_it / block blocks of
+ * `block` consecutive iterations; values = mean of the block means, errors =
+ * their standard error (NaN with fewer than 2 blocks). */
+void orc_micro_binned(int32_t K, double e_min, double bin_width, const double* lnW, const double* H,
+                      int32_t n_it, int32_t block, int32_t h, int32_t n_monomers, int32_t n_T, const double* T,
+                      double* S, double* beta, double* CV, double* E_T, double* cV_T, double* peak,
+                      double* S_err, double* beta_err, double* CV_err, double* E_T_err, double* cV_T_err,
+                      double* peak_err);
+
 /* Energy (returned) and its derivatives: gx [N*3] (nullable) with respect to
  * the coordinates, gp [5] (nullable) with respect to (C_AA, C_BB, C_AB, kappa,
  * kappa_C), each term of Eq. 2/3 and the torsion term differentiated by hand. */
