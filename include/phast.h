@@ -321,6 +321,27 @@ int phast_micro_analysis(int32_t K, double e_min, double bin_width, const double
                          const phast_micro_out* out, void* workspace, size_t workspace_bytes,
                          void* stream);
 
+/* Error bars by binning over iterations (Sec. 4.1: data blocks of dN
+ * iterations of a range [N_S, N_E], the binning method), the alternative to
+ * the jackknife over walker blocks.  lnW: dev [n_it][K], the weight tables of
+ * the iterations of the range (row i = iteration N_S + i); hist: dev uint64
+ * [n_it][K], each iteration's histogram summed over walkers, or NULL (S =
+ * -lnW).  Each iteration is analysed alone as phast_micro_analysis does (one
+ * replicate, its own weights and histogram); every observable is then averaged
+ * over n_b = n_it / block consecutive blocks of `block` iterations (a
+ * remainder at the end is left out).  out's values are the means of the block
+ * means, its *_err fields (when not NULL) their standard error
+ * sqrt(sum_b (B_b - mean)^2 / (n_b (n_b - 1))), NaN for n_b < 2; a bin that
+ * any iteration of the used range leaves unvisited is NaN.  workspace: dev,
+ * phast_micro_binned_workspace_size() bytes.  PHAST_EINVAL for bad arguments
+ * (including n_it < block). */
+size_t phast_micro_binned_workspace_size(int32_t K, int32_t n_T, int32_t n_it);
+int phast_micro_analysis_binned(int32_t K, double e_min, double bin_width, const double* lnW,
+                                const uint64_t* hist, int32_t n_it, int32_t block, int32_t fd_half_width,
+                                int32_t n_monomers, int32_t n_T, const double* T,
+                                const phast_micro_out* out, void* workspace, size_t workspace_bytes,
+                                void* stream);
+
 /* Free energy (Eq. 7) and the Maxwell construction on the caloric curve
  * (Sec. 3.3, ANALYST with Tol_Beta and Tol_L).  S_k from lnW and hist as in
  * phast_micro_analysis (shifted to max S = 0, unvisited bins skipped).  The

@@ -1,9 +1,11 @@
 // analysis.cu -- microcanonical analysis (Eq. 4-6; ANALYST of Sec. 3.3) with
-// canonical reweighting and jackknife errors over histogram blocks.
-// Replicate 0 uses every block; replicate r >= 1 leaves block r-1 out.
+// canonical reweighting, and error bars either by a jackknife over histogram
+// blocks (replicate 0 uses every block; replicate r >= 1 leaves block r-1 out)
+// or by binning over iterations (replicate i is iteration i, with its own
+// weights and histogram; Sec. 4.1).
 //   kernel 1 (one CTA per replicate): S_k, beta_k, C_V,k;
 //   kernel 2 (one CTA per replicate and temperature): <E>_T and c_V(T);
-//   kernel 3 (one CTA): c_V peak per replicate, values and jackknife errors.
+//   kernel 3 (one CTA): c_V peak per replicate, values and errors.
 #include "common.cuh"
 
 namespace {
@@ -55,18 +57,21 @@ __device__ __forceinline__ double rep_hist(const unsigned long long* hist, int n
     return (double)s;
 }
 
+// iters: replicate r is iteration r (weights row r, histogram row r); else the
+// jackknife replicates of the histogram blocks with one weight table.
 __global__ void __launch_bounds__(kThreads)
 entropy_kernel(int K, double w, const double* __restrict__ lnW, const unsigned long long* __restrict__ hist,
-               int n_blocks, int h, Work wk) {
+               int n_blocks, int h, Work wk, int iters) {
     __shared__ double red[32];
     const int r = blockIdx.x;
     double* S = wk.S + (size_t)r * K;
     double* beta = wk.beta + (size_t)r * K;
     double* CV = wk.CV + (size_t)r * K;
     const double nan = __longlong_as_double(0x7ff8000000000000ll);
+    if (iters) lnW += (size_t)r * K;
     double mx = -INFINITY;
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        double H = rep_hist(hist, n_blocks, K, r, k);
+        double H = iters ? (hist ? (double)hist[(size_t)r * K + k] : -1.0) : rep_hist(hist, n_blocks, K, r, k);
         double s = nan;
         if (H < 0.0) s = -lnW[k];
         else if (H > 0.0) s = -lnW[k] + log(H);
@@ -144,8 +149,37 @@ __device__ __forceinline__ void jackknife(const double* v, size_t stride, int n,
     err[idx] = sqrt((double)(n - 1) / n * s);
 }
 
+// Binning over rows 0 .. n_b * block - 1 of v (stride apart), n_b = R / block:
+// the mean of the block means and their standard error (NaN for n_b < 2), with
+// the oracle's order of summation.
+__device__ __forceinline__ void binning(const double* v, size_t stride, int R, int block, double* val, double* err,
+                                        size_t idx) {
+    const int n_b = R / block;
+    double mean = 0.0;
+    for (int b = 0; b < n_b; ++b) {
+        double s = 0.0;
+        for (int i = b * block; i < (b + 1) * block; ++i) s = s + v[(size_t)i * stride];
+        mean = mean + s / (double)block;
+    }
+    mean = mean / (double)n_b;
+    if (val) val[idx] = mean;
+    if (!err) return;
+    if (n_b < 2) { err[idx] = __longlong_as_double(0x7ff8000000000000ll); return; }
+    double q = 0.0;
+    for (int b = 0; b < n_b; ++b) {
+        double s = 0.0;
+        for (int i = b * block; i < (b + 1) * block; ++i) s = s + v[(size_t)i * stride];
+        const double d = s / (double)block - mean;
+        q = q + d * d;
+    }
+    err[idx] = sqrt(q / ((double)n_b * (double)(n_b - 1)));
+}
+
+// block > 0: binning over iterations in blocks of `block`; else the jackknife
+// over the n_jk leave-one-block-out replicates.
 __global__ void __launch_bounds__(kThreads)
-finish_kernel(int K, const double* __restrict__ T, int n_T, int R, int n_jk, Work wk, phast_micro_out o) {
+finish_kernel(int K, const double* __restrict__ T, int n_T, int R, int n_jk, Work wk, phast_micro_out o,
+              int block) {
     // c_V peak of each replicate: grid maximum, refined by a parabola through it and its neighbours
     for (int r = threadIdx.x; r < R; r += blockDim.x) {
         const double* c = wk.cVT + (size_t)r * n_T;
@@ -169,6 +203,19 @@ finish_kernel(int K, const double* __restrict__ T, int n_T, int R, int n_jk, Wor
         }
     }
     __syncthreads();
+    if (block > 0) {
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            binning(wk.S + k, (size_t)K, R, block, o.S, o.S_err, k);
+            binning(wk.beta + k, (size_t)K, R, block, o.beta, o.beta_err, k);
+            binning(wk.CV + k, (size_t)K, R, block, o.CV, o.CV_err, k);
+        }
+        for (int i = threadIdx.x; i < n_T; i += blockDim.x) {
+            binning(wk.ET + i, (size_t)n_T, R, block, o.E_T, o.E_T_err, i);
+            binning(wk.cVT + i, (size_t)n_T, R, block, o.cV_T, o.cV_T_err, i);
+        }
+        if (threadIdx.x < 2) binning(wk.peak + threadIdx.x, 2, R, block, o.peak, o.peak_err, threadIdx.x);
+        return;
+    }
     for (int k = threadIdx.x; k < K; k += blockDim.x) {
         jackknife(wk.S + k, (size_t)K, n_jk, o.S, o.S_err, k);
         jackknife(wk.beta + k, (size_t)K, n_jk, o.beta, o.beta_err, k);
@@ -395,13 +442,49 @@ extern "C" int phast_micro_analysis(int32_t K, double e_min, double bin_width, c
     Work wk = carve((double*)workspace, K, n_T, R);
     const int njk = n_blocks >= 2 ? n_blocks : 0;
     entropy_kernel<<<R, kThreads, 0, st>>>(K, bin_width, lnW, reinterpret_cast<const unsigned long long*>(hist),
-                                           n_blocks, h, wk);
+                                           n_blocks, h, wk, 0);
     PHAST_CUDA_TRY(cudaGetLastError());
     if (n_T > 0) {
         canonical_kernel<<<dim3(n_T, R), 256, 0, st>>>(K, e_min, bin_width, T, n_T, n_monomers, wk);
         PHAST_CUDA_TRY(cudaGetLastError());
     }
-    finish_kernel<<<1, kThreads, 0, st>>>(K, T, n_T, R, njk, wk, *out);
+    finish_kernel<<<1, kThreads, 0, st>>>(K, T, n_T, R, njk, wk, *out, 0);
+    PHAST_CUDA_TRY(cudaGetLastError());
+    return PHAST_OK;
+}
+
+extern "C" size_t phast_micro_binned_workspace_size(int32_t K, int32_t n_T, int32_t n_it) {
+    if (K < 1 || n_T < 0 || n_it < 1) return 0;
+    return sizeof(double) * work_doubles(K, n_T, n_it);
+}
+
+extern "C" int phast_micro_analysis_binned(int32_t K, double e_min, double bin_width, const double* lnW,
+                                           const uint64_t* hist, int32_t n_it, int32_t block, int32_t h,
+                                           int32_t n_monomers, int32_t n_T, const double* T,
+                                           const phast_micro_out* out, void* workspace, size_t workspace_bytes,
+                                           void* stream) {
+    const char* f = "phast_micro_analysis_binned";
+    if (K < 1 || K > PHAST_MAX_BINS) return phast_set_error(PHAST_EINVAL, "%s: K %d outside [1, %d]", f, K, PHAST_MAX_BINS);
+    if (!(bin_width > 0.0) || !isfinite(e_min)) return phast_set_error(PHAST_EINVAL, "%s: bad bins", f);
+    if (h < 1 || 2 * h >= K) return phast_set_error(PHAST_EINVAL, "%s: fd_half_width %d outside [1, K/2)", f, h);
+    if (n_monomers < 1) return phast_set_error(PHAST_EINVAL, "%s: n_monomers < 1", f);
+    if (n_T < 0 || (n_T > 0 && !T)) return phast_set_error(PHAST_EINVAL, "%s: bad temperature grid", f);
+    if (!lnW || !out) return phast_set_error(PHAST_EINVAL, "%s: NULL argument", f);
+    if (n_it < 1 || block < 1 || n_it / block < 1)
+        return phast_set_error(PHAST_EINVAL, "%s: %d iterations do not fill one block of %d", f, n_it, block);
+    const size_t need = sizeof(double) * work_doubles(K, n_T, n_it);
+    if (!workspace || workspace_bytes < need)
+        return phast_set_error(PHAST_EINVAL, "%s: workspace of %zu bytes < %zu", f, workspace_bytes, need);
+    cudaStream_t st = (cudaStream_t)stream;
+    Work wk = carve((double*)workspace, K, n_T, n_it);
+    entropy_kernel<<<n_it, kThreads, 0, st>>>(K, bin_width, lnW, reinterpret_cast<const unsigned long long*>(hist),
+                                              0, h, wk, 1);
+    PHAST_CUDA_TRY(cudaGetLastError());
+    if (n_T > 0) {
+        canonical_kernel<<<dim3(n_T, n_it), 256, 0, st>>>(K, e_min, bin_width, T, n_T, n_monomers, wk);
+        PHAST_CUDA_TRY(cudaGetLastError());
+    }
+    finish_kernel<<<1, kThreads, 0, st>>>(K, T, n_T, n_it, 0, wk, *out, block);
     PHAST_CUDA_TRY(cudaGetLastError());
     return PHAST_OK;
 }

@@ -29,7 +29,8 @@ SYMBOLS = ["phast_energy", "phast_delta_energy", "phast_ctx_create", "phast_ctx_
            "phast_micro_analysis", "phast_micro_analysis_noalloc", "phast_ctx_checkpoint", "phast_ctx_restore", "phast_last_error",
            "phast_version", "phast_ctx_capture_iteration", "phast_graph_launch",
            "phast_graph_destroy", "phast_energy_grad",
-           "phast_reweight_sensitivity", "phast_maxwell"]
+           "phast_reweight_sensitivity", "phast_maxwell", "phast_micro_binned_workspace_size",
+           "phast_micro_analysis_binned"]
 
 
 class PhastError(RuntimeError):
@@ -95,6 +96,10 @@ def lib():
         L.phast_weight_update.argtypes = [i32, dbl, vp, i32, vp, vp, vp, vp, vp]
         L.phast_micro_workspace_size.argtypes = [i32, i32, i32]
         L.phast_micro_workspace_size.restype = C.c_size_t
+        L.phast_micro_binned_workspace_size.argtypes = [i32, i32, i32]
+        L.phast_micro_binned_workspace_size.restype = C.c_size_t
+        L.phast_micro_analysis_binned.argtypes = [i32, dbl, dbl, vp, vp, i32, i32, i32, i32, i32, vp, P(_MicroOut),
+                                                  vp, C.c_size_t, vp]
         L.phast_micro_analysis.argtypes = [i32, dbl, dbl, vp, vp, i32, i32, i32, i32, vp, P(_MicroOut), vp,
                                            C.c_size_t, vp]
         L.phast_micro_analysis_noalloc.argtypes = [i32, dbl, dbl, vp, vp, i32, i32, i32, i32, vp, P(_MicroOut),
@@ -510,6 +515,34 @@ def phast_micro_analysis(lnW: torch.Tensor, e_min: float, bin_width: float, hist
     _check(lib().phast_micro_analysis(K, float(e_min), float(bin_width), _ptr(lnW), _ptr(hist), n_blocks,
                                       fd_half_width, n_monomers, n_T, _ptr(T), C.byref(o), _ptr(workspace),
                                       workspace.numel(), _stream(stream)))
+    return r
+
+
+def phast_micro_analysis_binned(lnW: torch.Tensor, e_min: float, bin_width: float, hist: torch.Tensor | None = None,
+                                block: int = 1, fd_half_width: int = 1, n_monomers: int = 1,
+                                T: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                                stream=None) -> MicroResult:
+    """Binning over iterations: lnW [n_it, K] and hist int64 [n_it, K] (or None), one
+    row per iteration; values and errors over n_it // block blocks of iterations."""
+    dev = lnW.device
+    lnW = lnW.contiguous()
+    n_it, K = lnW.shape
+    if T is None:
+        T = torch.empty(0, dtype=torch.float64, device=dev)
+    n_T = T.numel()
+    f = lambda n: torch.full((n,), float("nan"), dtype=torch.float64, device=dev)
+    r = MicroResult(f(K), f(K), f(K), f(n_T), f(n_T), f(2))
+    r.S_err, r.beta_err, r.CV_err, r.E_T_err, r.cV_T_err, r.peak_err = f(K), f(K), f(K), f(n_T), f(n_T), f(2)
+    o = _MicroOut()
+    for name in _MicroOut._fields_:
+        v = getattr(r, name[0])
+        setattr(o, name[0], None if v is None else v.data_ptr())
+    need = lib().phast_micro_binned_workspace_size(K, n_T, n_it)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(max(need, 1), dtype=torch.uint8, device=dev)
+    _check(lib().phast_micro_analysis_binned(K, float(e_min), float(bin_width), _ptr(lnW), _ptr(hist),
+                                             n_it, int(block), fd_half_width, n_monomers, n_T, _ptr(T), C.byref(o),
+                                             _ptr(workspace), workspace.numel(), _stream(stream)))
     return r
 
 

@@ -146,3 +146,35 @@ def test_full_muca_on_trimer_recovers_exact_entropy(phast, orc):
     d -= np.average(d, weights=1 / e ** 2)
     assert np.all(np.abs(d) < 5 * e), np.max(np.abs(d) / e)
     ctx.close()
+
+
+@pytest.mark.parametrize("with_hist", [True, False])
+def test_binning_over_iterations_matches_oracle(phast, orc, with_hist):
+    # twelve iterations of weights and histograms, blocks of three (Sec. 4.1)
+    rng = np.random.default_rng(12)
+    n_it, K, e_min, w, h, N, block = 12, 1500, -60.0, 0.1, 4, 30, 3
+    Ek = e_min + (np.arange(K) + 0.5) * w
+    base = -(-((Ek + 20) / 25.0) ** 2 + 0.4 * np.tanh((Ek + 30) / 4.0)) * 15
+    lnW = np.stack([base + 0.05 * np.cumsum(rng.standard_normal(K)) / np.sqrt(K) for _ in range(n_it)])
+    H = rng.poisson(200, size=(n_it, K)).astype(np.int64) if with_hist else None
+    if with_hist:
+        H[:, :40] = 0
+        H[5, 700] = 0                                 # one iteration leaves a bin unvisited
+    T = np.linspace(0.3, 3.0, 48)
+    r = phast.phast_micro_analysis_binned(torch.from_numpy(lnW).cuda(), e_min, w,
+                                          hist=None if H is None else torch.from_numpy(H).cuda(), block=block,
+                                          fd_half_width=h, n_monomers=N, T=torch.from_numpy(T).cuda())
+    torch.cuda.synchronize()
+    o = orc.micro_binned(lnW, e_min, w, H, block=block, fd_half_width=h, n_monomers=N, T=T)
+    for k, tol in (("S", 1e-12), ("beta", 1e-9), ("CV", 1e-7), ("E_T", 1e-10), ("cV_T", 1e-9), ("peak", 1e-9)):
+        _close(getattr(r, k).cpu(), o[k], tol)
+        _close(getattr(r, k + "_err").cpu(), o[k + "_err"], 1e-6)
+    if with_hist:
+        assert np.isnan(r.S[700].item()) and np.isnan(r.S_err[700].item())
+    assert np.all(np.isfinite(r.S_err.cpu().numpy()[100:600]))
+
+
+def test_binning_needs_a_full_block(phast):
+    lnW = torch.zeros(2, 100, dtype=torch.float64, device="cuda")
+    with pytest.raises(phast.PhastError, match="block"):
+        phast.phast_micro_analysis_binned(lnW, 0.0, 0.1, block=3, fd_half_width=2)
