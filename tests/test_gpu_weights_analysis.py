@@ -178,3 +178,41 @@ def test_binning_needs_a_full_block(phast):
     lnW = torch.zeros(2, 100, dtype=torch.float64, device="cuda")
     with pytest.raises(phast.PhastError, match="block"):
         phast.phast_micro_analysis_binned(lnW, 0.0, 0.1, block=3, fd_half_width=2)
+
+
+def test_entropy_is_invariant_to_the_walker_count(phast):
+    """The analogue of the paper's data collapse over processor counts (Fig. 4):
+    the Fibonacci 13-mer with 256 walkers x 200 sweeps and with 1024 walkers x 50
+    sweeps per iteration (the same statistics), six Berg iterations each; the
+    final S(E) of the two runs agree within five combined jackknife errors on
+    the well-visited bins, up to the free additive constant."""
+    from paper_1702_01770_gb300 import inputs
+
+    def run(walkers, sweeps, seed_base):
+        s = inputs.config0(walkers)
+        s.seed_base = seed_base
+        ctx = phast.Context(s, pair_precision=32)
+        K = s.n_bins
+        lnW = torch.zeros(K, dtype=torch.float64, device="cuda")
+        g = torch.zeros(K - 1, dtype=torch.float64, device="cuda")
+        for it in range(7):
+            hs = ctx.hist_sum_zeros(16)
+            ctx.sweep(sweeps, lnW, n_jk=16, hist_sum=hs)
+            if it < 6:
+                phast.phast_weight_update(hs, lnW, g, s.bin_width)
+        r = phast.phast_micro_analysis(lnW, s.e_min, s.bin_width, hist=hs.view(16, K), fd_half_width=2)
+        H = hs.view(16, K).sum(0).cpu().numpy()
+        torch.cuda.synchronize()
+        out = r.S.cpu().numpy(), r.S_err.cpu().numpy(), H
+        ctx.close()
+        return out
+
+    Sa, ea, Ha = run(256, 200, 0)
+    Sb, eb, Hb = run(1024, 50, 5000)
+    sel = (Ha > 300) & (Hb > 300) & np.isfinite(Sa) & np.isfinite(Sb)
+    assert sel.sum() > 50, (int(sel.sum()), int(Ha.max()), int(Hb.max()), int((Ha > 0).sum()))
+    e = np.sqrt(ea[sel] ** 2 + eb[sel] ** 2)
+    e = np.maximum(e, np.median(e))             # the normalising bin shows no error of its own
+    d = Sa[sel] - Sb[sel]
+    d -= np.average(d, weights=1 / e ** 2)
+    assert np.all(np.abs(d) < 5 * e), np.max(np.abs(d) / e)
