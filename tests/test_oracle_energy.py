@@ -59,7 +59,7 @@ def test_right_angle_trimer(orc, seq):
     assert t[0] == pytest.approx(0.25, abs=1e-15) and t[1] == 0.0 and t[3] == 0.0
 
 
-def test_survey_trimer_values(orc):
+def test_trimer_decimal_values(orc):
     # the same closed forms, as decimal numbers
     for seq, straight, right in [("AAA", -0.0615234375, -0.1875), ("BBB", -0.0302734375, 0.0625),
                                  ("AAB", 0.0322265625, 0.5625)]:
