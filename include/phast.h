@@ -346,8 +346,9 @@ int phast_micro_analysis_binned(int32_t K, double e_min, double bin_width, const
  * (Sec. 3.3, ANALYST with Tol_Beta and Tol_L).  S_k from lnW and hist as in
  * phast_micro_analysis (shifted to max S = 0, unvisited bins skipped).  The
  * equal-area line on beta(E) is the common tangent of S(E): an edge of the
- * upper concave hull of (E_k, S_k) spanning bins below it.  Among those with
- * latent heat (E_b - E_a)/N >= tol_L across which beta_k = (S_{k+h} -
+ * upper concave hull of (E_k, S_k) spanning bins below it.  Among those with a
+ * positive slope (beta_c > 0) and a latent heat (E_b - E_a)/N >= tol_L, across
+ * which beta_k = (S_{k+h} -
  * S_{k-h})/(2 h w) rises by >= tol_beta, the widest (the first of equal
  * width) gives beta_c (its slope),
  * eps_1 = E_a/N, eps_2 = E_b/N, the latent heat, and the barrier

@@ -1027,8 +1027,9 @@ void orc_reweight_sensitivity(int64_t n, const double* E, const double* D, const
 /* (Sec. 3.3, ANALYST: Tol_Beta, Tol_L).  Reading: the equal-area line on     */
 /* beta(E) is the common tangent of S(E), i.e. an edge of the upper concave   */
 /* hull of the points (E_k, S_k) over visited bins that spans bins lying      */
-/* below it (a convex intruder).  Among intruders whose latent heat           */
-/* (E_b - E_a)/N is at least tol_L and across which beta_k = (S_{k+h} -       */
+/* below it (a convex intruder).  Among intruders with a positive slope      */
+/* (beta_c = 1/T_c > 0: a transition at a positive temperature), a latent    */
+/* heat (E_b - E_a)/N of at least tol_L, and across which beta_k = (S_{k+h} - */
 /* S_{k-h})/(2 h w) rises by at least tol_beta (the S-bend), the one with the */
 /* largest latent heat is taken: beta_c its slope, eps_1 = E_a/N,             */
 /* eps_2 = E_b/N, and the barrier of f = (E - S/beta_c)/N between the two     */
@@ -1065,6 +1066,8 @@ void orc_maxwell(int32_t K, double e_min, double bin_width, const double* S, int
             for (int k = a + 1; k < b; ++k) if (isfinite(S[k])) inside = 1;
             if (!inside) continue;
             double ea = e_min + ((double)a + 0.5) * bin_width, eb = e_min + ((double)b + 0.5) * bin_width;
+            /* the common tangent's slope is beta_c = 1/T_c: a transition needs beta_c > 0 */
+            if (!((S[b] - S[a]) / (eb - ea) > 0.0)) continue;
             double L = (eb - ea) / N;
             /* largest rise of beta across [a, b]: max over k <= j of beta_j - beta_k */
             double rise = 0.0, bmin = INFINITY;

@@ -232,9 +232,10 @@ finish_kernel(int K, const double* __restrict__ T, int n_T, int R, int n_jk, Wor
 // Free energy (Eq. 7) and the Maxwell construction on the caloric curve
 // (ANALYST's Tol_Beta / Tol_L): the equal-area line on beta(E) is the common
 // tangent of S(E), an edge of the upper concave hull of (E_k, S_k) over the
-// visited bins that spans bins below it.  Among those whose latent heat is at
-// least tol_L and across which beta_k = (S_{k+h} - S_{k-h}) / (2 h w) rises by
-// at least tol_beta, the widest is taken (the first of equal width).
+// visited bins that spans bins below it.  Among those with a positive slope
+// (beta_c = 1/T_c > 0), a latent heat of at least tol_L, and across which
+// beta_k = (S_{k+h} - S_{k-h}) / (2 h w) rises by at least tol_beta, the widest
+// is taken (the first of equal width).
 //
 // One CTA per replicate, S in shared memory.  The hull is Andrew's monotone
 // chain on one thread with the same FP64 orientation test throughout, so the
@@ -323,7 +324,9 @@ maxwell_kernel(int K, double e_min, double w, const double* __restrict__ lnW,
             bool in = false;
             for (int k = a + 1 + lane; k < b; k += 32) in |= (bool)isfinite(S[k]);
             if (!__any_sync(0xffffffffu, in)) continue;
-            const double L = __ddiv_rn(__dsub_rn(bin_centre(e_min, w, b), bin_centre(e_min, w, a)), N);
+            const double eab = __dsub_rn(bin_centre(e_min, w, b), bin_centre(e_min, w, a));
+            if (!(__ddiv_rn(__dsub_rn(S[b], S[a]), eab) > 0.0)) continue;   // beta_c = 1/T_c > 0
+            const double L = __ddiv_rn(eab, N);
             double rise = 0.0, run_min = INFINITY;
             for (int base = a; base <= b; base += 32) {
                 const int k = base + lane;

@@ -109,3 +109,14 @@ def test_full_size_noisy_against_oracle(phast, orc):
         if r == 0:
             assert ro["found"] == 1.0
             assert np.allclose(f.cpu().numpy(), fo, rtol=1e-12, atol=1e-12, equal_nan=True)
+
+
+def test_negative_temperature_bend_is_no_transition(phast, orc):
+    K, e_min, w, N = 100, -0.05, 0.1, 10
+    E = e_min + (np.arange(K) + 0.5) * w
+    S = np.maximum(-(E - 2.0) ** 2 / 4.0, 1.0 - (E - 6.0) ** 2 / 4.0)[::-1].copy()   # falling common tangent
+    lnW = -S
+    f, rep, err = phast.phast_maxwell(torch.from_numpy(lnW).cuda(), None, e_min, w, N)
+    fo, ro = orc.maxwell(S - S.max(), e_min, w, N)
+    _check_row(rep[0].cpu().numpy(), ro)
+    assert ro["found"] == 0.0 and np.all(np.isnan(f.cpu().numpy()))

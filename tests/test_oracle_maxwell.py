@@ -77,3 +77,15 @@ def test_largest_intruder_wins_and_holes_are_skipped(orc):
     _, rh = orc.maxwell(holes, E_MIN, W, N)
     assert rh["latent"] == pytest.approx(0.4, rel=1e-12)
     assert rh["beta_c"] == pytest.approx(r["beta_c"], rel=1e-12)
+
+
+def test_negative_temperature_bend_is_no_transition(orc):
+    # the mirror image of the two parabolas (E -> const - E): its common tangent
+    # falls (beta_c < 0, a negative temperature) and is not a transition; the
+    # unmirrored entropy on the same bins gives the closed-form beta_c > 0
+    E = _E()
+    S = _two_parabolas()
+    f, r = orc.maxwell(S[::-1].copy(), E_MIN, W, N)
+    assert r["found"] == 0.0 and np.isnan(r["beta_c"]) and np.all(np.isnan(f))
+    _, r = orc.maxwell(S, E_MIN, W, N)
+    assert r["found"] == 1.0 and r["beta_c"] > 0.0
