@@ -47,8 +47,9 @@ enum {
     PHAST_ERANGE = -2,     /* a walker energy outside its bin range */
     PHAST_ENOMEM = -3,     /* device or host allocation failed */
     PHAST_ECUDA = -4,      /* a CUDA runtime call failed */
-    PHAST_ETIMEOUT = -5,   /* a bounded device wait ran out */
-    PHAST_EDEVICE = -6,    /* a kernel reported an error word */
+    PHAST_ETIMEOUT = -5,   /* reserved: a bounded device wait ran out (no kernel of this build waits) */
+    PHAST_EDEVICE = -6,    /* reserved: a kernel reported an error word (none of this build does:
+                              bad inputs are refused on the host, bad moves rejected in the sweep) */
     PHAST_ENONFINITE = -7  /* non-finite coordinates or energy */
 };
 
