@@ -34,6 +34,7 @@ GEOM_WALKERS = 16384
 GEOM_SWEEPS = 100
 FLOPS_OPEN, FLOPS_PBC = 14, 23          # algorithmic flops of one pair evaluation (open / minimum image)
 LAUNCHES_PER_STEP = 5                   # sweep, 3 analysis kernels, Berg update
+MOVE_NAMES = ("pivot", "translation", "rotation", "crankshaft", "bond", "cap")
 
 
 def parse():
@@ -346,6 +347,9 @@ def run_ours(args):
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clocks,
         "drift_max": float(st1["drift_max"].max()),
+        "accept_rate": {name: (float(a) / float(n) if n else None) for name, a, n in
+                        zip(MOVE_NAMES, st1["accepts"].sum(0) - st0["accepts"].sum(0),
+                            st1["attempts"].sum(0) - st0["attempts"].sum(0))},
         "flatness_cvar": float(flat[2].item()),
     }
 
