@@ -115,6 +115,7 @@ def lib():
                                          P(C.c_double), P(C.c_double), P(C.c_double),
                                          P(C.c_double), P(C.c_double), P(C.c_double),
                                          P(C.c_double)]
+        L.orc_jackknife.argtypes = [C.c_int32, C.c_int32, P(C.c_double), P(C.c_double)]
         L.orc_micro_binned.argtypes = ([C.c_int32, C.c_double, C.c_double, P(C.c_double), P(C.c_double),
                                         C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P(C.c_double)]
                                        + [P(C.c_double)] * 12)
@@ -351,6 +352,20 @@ def berg_update(H, lnW, g_acc, bin_width: float = 1.0):
     lib().orc_berg_update(C.c_int32(H.size), C.c_double(bin_width), _ptr(H, C.c_double),
                           _ptr(lnW, C.c_double), _ptr(g_acc, C.c_double), _ptr(flat, C.c_double))
     return lnW, g_acc, flat
+
+
+def jackknife(replicates):
+    """Jackknife errors (Sec. 4.1, error bars from data blocks) from leave-one-block-out
+    replicates [n, ...]: sqrt((n-1)/n sum_b (v_b - mean)^2) elementwise, NaN for n < 2."""
+    v = np.ascontiguousarray(replicates, dtype=np.float64)
+    n = v.shape[0]
+    rest = v.shape[1:]
+    m = int(np.prod(rest)) if rest else 1
+    flat = v.reshape(n, m) if n else np.zeros((0, m))
+    flat = np.ascontiguousarray(flat)
+    err = np.zeros(m)
+    lib().orc_jackknife(C.c_int32(n), C.c_int32(m), _ptr(flat, C.c_double) if n else None, _ptr(err, C.c_double))
+    return err.reshape(rest) if rest else float(err[0])
 
 
 def micro_binned(lnW, e_min: float, bin_width: float, H=None, block: int = 1, fd_half_width: int = 1,

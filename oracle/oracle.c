@@ -777,6 +777,32 @@ void orc_micro_analysis(int32_t K, double e_min, double bin_width, const double*
 }
 
 /* ------------------------------------------------------------------------- */
+/* Jackknife error over data blocks (Sec. 4.1: error bars from blocks of the    */
+/* data; here the blocks are groups of walkers).  The caller computes each      */
+/* estimate once more with block b left out (replicate v_b, b < n); the error   */
+/* of the estimate is sqrt((n - 1)/n * sum_b (v_b - vbar)^2), vbar the mean of  */
+/* the replicates.  rep is [n][m] (m observables per replicate), err [m].  NaN  */
+/* for n < 2; a NaN replicate makes that observable's error NaN.                */
+/* ------------------------------------------------------------------------- */
+void orc_jackknife(int32_t n, int32_t m, const double* rep, double* err) {
+    for (int q = 0; q < m; ++q) {
+        if (n < 2) {
+            err[q] = NAN;
+            continue;
+        }
+        double mean = 0.0;
+        for (int b = 0; b < n; ++b) mean = mean + rep[(size_t)b * (size_t)m + (size_t)q];
+        mean = mean / (double)n;
+        double ss = 0.0;
+        for (int b = 0; b < n; ++b) {
+            const double d = rep[(size_t)b * (size_t)m + (size_t)q] - mean;
+            ss = ss + d * d;
+        }
+        err[q] = sqrt((double)(n - 1) / (double)n * ss);
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* Error bars by binning over iterations (Sec. 4.1, ANALYST: data blocks of     */
 /* dN iterations of the range [N_S, N_E], the binning method).  Iteration i     */
 /* (row i of lnW and, if given, of H) is analysed alone as orc_micro_analysis   */

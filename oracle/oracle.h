@@ -135,6 +135,11 @@ void orc_micro_analysis(int32_t K, double e_min, double bin_width, const double*
                         double* S, double* beta, double* CV,
                         double* E_T, double* cV_T, double* peak);
 
+/* Jackknife error (Sec. 4.1, error bars from data blocks) of an estimate from
+ * its n leave-one-block-out replicates: rep [n][m], err [m] =
+ * sqrt((n-1)/n sum_b (rep[b] - mean)^2) per column; NaN for n < 2. */
+void orc_jackknife(int32_t n, int32_t m, const double* rep, double* err);
+
 /* Binning over iterations (Sec. 4.1): rows i < n_it of lnW and H (nullable)
  * analysed one by one, each observable averaged over n_it / block blocks of
  * `block` consecutive iterations; values = mean of the block means, errors =

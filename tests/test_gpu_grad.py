@@ -173,7 +173,7 @@ def test_trimer_sensitivities_by_quadrature_nodes(phast):
     assert np.allclose(g["dcV_T"].cpu().numpy(), truth[:, 3], rtol=1e-4, atol=1e-8)
 
 
-def test_muca_run_trimer_sensitivities(phast):
+def test_muca_run_trimer_sensitivities(phast, orc):
     """A multicanonical run of the AAB trimer on flat weights (its walkers then
     sample cos theta uniformly): reweighted d<E>_T/dC_AB and dc_V/dC_AB from the
     run's snapshots match the exact values within five jackknife errors."""
@@ -204,7 +204,7 @@ def test_muca_run_trimer_sensitivities(phast):
                                        zeros[:, keep].reshape(-1), 3, T)
         reps.append(torch.stack([r["dE_T"], r["dcV_T"]]).cpu().numpy())
     reps = np.array(reps)
-    err = np.sqrt((blocks - 1) / blocks * np.sum((reps - reps.mean(axis=0)) ** 2, axis=0))
+    err = orc.jackknife(reps)
     truth = _trimer_truth(T.cpu().numpy(), e_max=s.e_min + s.n_bins * s.bin_width)   # the sampled range
     est = np.stack([full["dE_T"].cpu().numpy(), full["dcV_T"].cpu().numpy()])
     ref = np.stack([truth[:, 2], truth[:, 3]])

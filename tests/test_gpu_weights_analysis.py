@@ -57,10 +57,6 @@ def _orc_replicates(orc, lnW, H, e_min, w, h, N, T):
     return full, reps
 
 
-def _jk(vals):
-    v = np.array(vals)
-    n = v.shape[0]
-    return np.sqrt((n - 1) / n * ((v - v.mean(0)) ** 2).sum(0))
 
 
 def _close(a, b, rtol):
@@ -89,11 +85,11 @@ def test_micro_analysis_matches_oracle(phast, orc, n_blocks):
     _close(r.cV_T.cpu(), full["cV_T"], 1e-9)
     _close(r.peak.cpu(), full["peak"], 1e-9)
     if n_blocks >= 2:
-        _close(r.S_err.cpu(), _jk([x["S"] for x in reps]), 1e-8)
-        _close(r.beta_err.cpu(), _jk([x["beta"] for x in reps]), 1e-6)
-        _close(r.E_T_err.cpu(), _jk([x["E_T"] for x in reps]), 1e-7)
-        _close(r.cV_T_err.cpu(), _jk([x["cV_T"] for x in reps]), 1e-6)
-        _close(r.peak_err.cpu(), _jk([x["peak"] for x in reps]), 1e-6)
+        _close(r.S_err.cpu(), orc.jackknife([x["S"] for x in reps]), 1e-8)
+        _close(r.beta_err.cpu(), orc.jackknife([x["beta"] for x in reps]), 1e-6)
+        _close(r.E_T_err.cpu(), orc.jackknife([x["E_T"] for x in reps]), 1e-7)
+        _close(r.cV_T_err.cpu(), orc.jackknife([x["cV_T"] for x in reps]), 1e-6)
+        _close(r.peak_err.cpu(), orc.jackknife([x["peak"] for x in reps]), 1e-6)
     else:
         assert r.S_err is None
 
