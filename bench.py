@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--no-geom", action="store_true")
     ap.add_argument("--geom-only", action="store_true")
     ap.add_argument("--geom-tile", type=int, nargs=2, default=None, metavar=("TPW", "WPC"))
+    ap.add_argument("--dry-run-cpu", action="store_true",
+                    help="rank plumbing only, on CPU over gloo: walker keys, one histogram exchange per step, "
+                         "max-over-ranks time (no GPU, no sweep)")
     return ap.parse_args()
 
 
@@ -458,10 +461,64 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def relaunch(args) -> int:
+    """`--gpus N` (N > 1) outside torchrun: start N ranks on this node, one per GPU."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", f"--master-port={port}", os.path.abspath(__file__), *sys.argv[1:]]
+    return subprocess.call(cmd)
+
+
+def run_dry(args):
+    """The multi-rank plumbing of the GPU arm on CPU (gloo): each rank's walker keys,
+    one histogram all-reduce per step, the max-over-ranks time; rank 0 prints one line."""
+    import torch
+
+    from paper_1702_01770_gb300 import inputs, parallel
+    rank, world, _ = parallel.world()
+    if world > 1:
+        torch.distributed.init_process_group("gloo")
+    s = inputs.config4(walkers=args.walkers)
+    s.seed_base = parallel.walker_seed_base(rank, args.walkers)
+    keys = s.seeds()
+    K = s.n_bins
+    hs = torch.zeros(N_JK * K, dtype=torch.int64)
+    exchanges = 0
+    t0 = time.perf_counter()
+    for i in range(args.warmup + args.steps):
+        hs.zero_()
+        hs[(rank * 7 + i) % K] = rank + 1          # a rank-specific count, summed by the exchange
+        parallel.combine_histograms(hs)
+        exchanges += 1
+        assert int(hs.sum()) == world * (world + 1) // 2
+    local_ms = (time.perf_counter() - t0) * 1e3
+    ms = parallel.max_over_ranks(local_ms, torch.device("cpu"))
+    mine = torch.tensor([float(keys[0]), float(keys[-1]), local_ms], dtype=torch.float64)
+    rows = [torch.zeros_like(mine) for _ in range(world)]
+    if world > 1:
+        torch.distributed.all_gather(rows, mine)
+    else:
+        rows = [mine]
+    if rank == 0:
+        print(json.dumps({"dry_run": True, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                          "exchanges_per_step": exchanges / (args.warmup + args.steps), "max_ms": ms,
+                          "rank_ms": [float(r[2]) for r in rows],
+                          "key_ranges": [[int(r[0]), int(r[1])] for r in rows], "scaling": "weak"}), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(relaunch(args))
     if args.impl == "reference":
         run_reference(args)
+    elif args.dry_run_cpu:
+        run_dry(args)
     else:
         run_ours(args)
 

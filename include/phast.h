@@ -129,6 +129,9 @@ typedef struct {
     uint64_t pair_evals_inter;  /* the part of pair_evals between different chains */
     uint64_t recomputes;
     double drift_max;      /* largest |E_running - E_full| seen at a recompute */
+    uint64_t recompute_kept;    /* recomputes whose FP64 energy fell outside the bins: the running
+                                   energy and its bin were kept (the drift was not removed) */
+    uint64_t pad;
 } phast_walker_stats;
 
 /* One traced move (16 bytes). */
@@ -214,12 +217,27 @@ enum { PHAST_FORM_BATCHED = 0, PHAST_FORM_PLAIN = 1 };
  *        the walkers of jackknife block b of type s, block b holding walkers
  *        [b W_s / n_jk, (b+1) W_s / n_jk) (integer division).
  *  hist_walker: dev uint32 [sum_s W_s * n_bins_s] or NULL; += per-walker counts.
+ *        A call adds n_sweeps * N_s counts per walker, so a call with
+ *        n_sweeps * max_s N_s >= 2^32 is refused (PHAST_EINVAL); keeping the
+ *        counts accumulated over calls below 2^32 is the caller's part.
+ *  The batched form counts the walkers of a tile in a 32-bit shared-memory
+ *  histogram; a bin that reaches the context's flush count (2^31 unless
+ *  phast_ctx_set_hist_flush says otherwise) moves that count into hist_sum at
+ *  once, so no count wraps however long the call.
  *  trace: dev [trace_walkers][n_sweeps * N] or NULL; per-move record of the
  *        first trace_walkers walkers of type 0 (walker-major).
  * Histograms are added to, never cleared. */
 int phast_muca_sweep(phast_ctx* ctx, int64_t n_sweeps, const double* lnW, int32_t form,
                      int32_t n_jk, uint64_t* hist_sum, uint32_t* hist_walker,
                      phast_trace* trace, int32_t trace_walkers, void* stream);
+
+/* The count at which a tile's 32-bit shared-memory histogram bin is moved
+ * into the 64-bit hist_sum during a batched sweep: a power of two, at most
+ * 2^31 (the default; 0 restores it); PHAST_EINVAL otherwise.  Whenever an
+ * increment takes a bin to a multiple of it, that many counts move.  The
+ * results do not depend on it: a small value only exercises the flush (a
+ * testing hook). */
+int phast_ctx_set_hist_flush(phast_ctx* ctx, uint32_t count);
 
 /* ---- Berg's weight recursion (Sec. 2.2) ------------------------------- */
 
@@ -381,9 +399,12 @@ int phast_maxwell(int32_t K, double e_min, double bin_width, const double* lnW, 
  *    n_blocks when n_blocks >= 2 (else 0); a larger request fails with
  *    PHAST_EINVAL and a message naming the sizes (use phast_micro_analysis).
  *    K = 8000 bins with 64 temperatures and 16 blocks fits.
- *  - The first call on a device looks up the array's device address (with that
- *    device current) and caches it; make that first call before any stream
- *    capture.
+ *  - The array has its own device address in each CUDA context.  The first
+ *    call in a context (the device's primary context, or any context the
+ *    caller has made current) looks that address up and caches it under the
+ *    context's unique ID, so a context created later -- after cudaDeviceReset,
+ *    say -- gets a fresh lookup.  Make the first call in each context before
+ *    any stream capture.
  *  - Every call shares the one array and every element it reads is written
  *    earlier in the same call, so nothing needs clearing; calls that overlap on
  *    the GPU (other streams, other host threads) race on it.

@@ -500,13 +500,50 @@ extern "C" int phast_micro_analysis_binned(int32_t K, double e_min, double bin_w
 // the workspace lives in a file-scope device array that the library reserves
 // when its module is loaded on a device (and keeps until the process exits).
 // ---------------------------------------------------------------------------
+#include <cuda.h>   // CUcontext and CUresult types only; the driver calls are resolved at run time
 #include <mutex>
 
 static __device__ __align__(256) double g_micro_scratch[PHAST_MICRO_NOALLOC_DOUBLES];
 
 namespace {
+// The array's name is a host-side stand-in: its device address has to be looked
+// up, and it differs between CUDA contexts (a module is loaded once per
+// context).  The address is cached per context, keyed by the driver's unique
+// context ID, so a context created later (after cudaDeviceReset, or a
+// non-primary context a host program makes current) gets its own lookup.
+typedef CUresult (*ctx_get_current_fn)(CUcontext*);
+typedef CUresult (*ctx_get_id_fn)(CUcontext, unsigned long long*);
+struct ScratchEntry {
+    unsigned long long ctx_id;
+    double* addr;
+};
+constexpr int kScratchCache = 64;
 std::mutex g_scratch_mu;
-double* g_scratch_addr[256];   // device address of g_micro_scratch, per device ordinal
+ScratchEntry g_scratch_cache[kScratchCache];
+int g_scratch_used = 0, g_scratch_next = 0;
+ctx_get_current_fn g_ctx_get_current = nullptr;
+ctx_get_id_fn g_ctx_get_id = nullptr;
+
+// ID of the calling thread's current context; 0 when there is none yet.
+int current_ctx_id(unsigned long long* id) {
+    *id = 0;
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return phast_set_error(PHAST_ECUDA, "phast_micro_analysis_noalloc: driver context queries unavailable");
+        g_ctx_get_current = (ctx_get_current_fn)f1;
+        g_ctx_get_id = (ctx_get_id_fn)f2;
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS)
+        return phast_set_error(PHAST_ECUDA, "phast_micro_analysis_noalloc: cuCtxGetCurrent failed");
+    if (ctx && g_ctx_get_id(ctx, id) != CUDA_SUCCESS)
+        return phast_set_error(PHAST_ECUDA, "phast_micro_analysis_noalloc: cuCtxGetId failed");
+    return PHAST_OK;
+}
 }  // namespace
 
 extern "C" int phast_micro_analysis_noalloc(int32_t K, double e_min, double bin_width, const double* lnW,
@@ -522,22 +559,29 @@ extern "C" int phast_micro_analysis_noalloc(int32_t K, double e_min, double bin_
                                "phast_micro_analysis_noalloc: K=%d, n_T=%d, %d blocks need %zu doubles of scratch, "
                                "more than the %d of the static workspace (use phast_micro_analysis)",
                                K, n_T, n_blocks, need, PHAST_MICRO_NOALLOC_DOUBLES);
-    int dev = 0;
-    PHAST_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 256) return phast_set_error(PHAST_EINVAL, "phast_micro_analysis_noalloc: device %d", dev);
     double* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_scratch_mu);
-        if (!g_scratch_addr[dev]) {
-            // the array's name is a host-side stand-in; its device address is looked up once per device
+        unsigned long long id = 0;
+        int rc = current_ctx_id(&id);
+        if (rc != PHAST_OK) return rc;
+        for (int i = 0; i < g_scratch_used && id; ++i)
+            if (g_scratch_cache[i].ctx_id == id) scratch = g_scratch_cache[i].addr;
+        if (!scratch) {
+            // first call in this context: look the address up (this also makes the
+            // runtime's context current when none was)
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_micro_scratch);
             if (e != cudaSuccess)
                 return phast_set_error(PHAST_ECUDA, "phast_micro_analysis_noalloc: cudaGetSymbolAddress: %s",
                                        cudaGetErrorString(e));
-            g_scratch_addr[dev] = (double*)p;
+            scratch = (double*)p;
+            if (!id && (rc = current_ctx_id(&id)) != PHAST_OK) return rc;
+            if (id) {
+                const int slot = g_scratch_used < kScratchCache ? g_scratch_used++ : (g_scratch_next++ % kScratchCache);
+                g_scratch_cache[slot] = ScratchEntry{id, scratch};
+            }
         }
-        scratch = g_scratch_addr[dev];
     }
     return phast_micro_analysis(K, e_min, bin_width, lnW, hist, n_blocks, h, n_monomers, n_T, T, out, scratch,
                                 sizeof(double) * (size_t)PHAST_MICRO_NOALLOC_DOUBLES, stream);

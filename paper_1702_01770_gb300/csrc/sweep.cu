@@ -38,6 +38,7 @@ struct phast_ctx {
     int32_t* tile_counter;
     double* plain_scratch;   // [W][max_chain][3] new positions of the plain form
     int tpw, wpc;
+    uint32_t hist_flush;     // count at which a shared histogram bin moves into hist_sum
     int order[PHAST_MAX_SYSTEMS];   // tile order: most expensive system types first
 };
 
@@ -70,6 +71,7 @@ struct SweepArgs {
     int scratch_stride;                   // doubles per walker in scratch
     SlotLayout L;
     int hist_bins;                        // shared histogram capacity (max n_bins)
+    uint32_t hist_flush;                  // a shared bin reaching this count moves it into hist_sum
 };
 
 __device__ __forceinline__ void copy_desc(SysDesc* dst, const SysDesc* src) {
@@ -124,6 +126,8 @@ __device__ __forceinline__ void recompute_energy(const SysDesc& sd, const double
         bin = bf;
         lnw_here = __ldg(lnW + bin);
         erel = (float)(E - sd.e_min);
+    } else if (g.lane == 0) {
+        ls->recompute_kept++;
     }
     g.sync();
     build_working<TPW, PT>(sd, x64, slot, g);
@@ -133,9 +137,12 @@ __device__ __forceinline__ void recompute_energy(const SysDesc& sd, const double
 // keeps the per-move loop short in the instruction cache.
 template <int TPW, typename PT, bool GEOM>
 __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int w_local, Slot<PT>& slot,
-                           uint32_t* hist, unsigned long long* hist_g, const Group<TPW>& g) {
-    // hist: the tile's shared histogram; hist_g (non-null): this walker's jackknife
-    // block differs from the tile's, so its visits go straight to the global sums
+                           uint32_t* hist, unsigned long long* hist_tile, unsigned long long* hist_g,
+                           const Group<TPW>& g) {
+    // hist: the tile's shared histogram, whose bins move into hist_tile (the global
+    // sums of the tile's jackknife block, or null) on reaching a.hist_flush; hist_g
+    // (non-null): this walker's jackknife block differs from the tile's, so its
+    // visits go straight to the global sums
     const int gw = sd.walker_off + w_local;
     double* x64 = a.xyz + sd.xyz_off + (int64_t)w_local * sd.N * 3;
     const double* lnW = a.lnW + sd.lnw_off;
@@ -204,8 +211,16 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
             erel = (float)(E - sd.e_min);
         }
         if (g.lane == 0) {   // histogram and bookkeeping on one lane
-            if (hist_g) atomicAdd(hist_g + bin, 1ull);
-            else atomicAdd(hist + bin, 1u);
+            if (hist_g) {
+                atomicAdd(hist_g + bin, 1ull);
+            } else if (((atomicAdd(hist + bin, 1u) + 1u) & (a.hist_flush - 1u)) == 0u && hist_tile) {
+                // this increment took the bin to a multiple of the flush count (a power
+                // of two): move that many into the 64-bit sums.  Each multiple is crossed
+                // by one increment, so the bin stays below the flush count plus the
+                // walkers of the tile.
+                atomicSub(hist + bin, a.hist_flush);
+                atomicAdd(hist_tile + bin, (unsigned long long)a.hist_flush);
+            }
             if (hw) atomicAdd(hw + bin, 1u);
             ls->attempts[P.type]++;
             ls->accepts[P.type] += acc;
@@ -254,11 +269,13 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         st->pair_evals += ls->pair_evals;
         st->pair_evals_inter += ls->pair_evals_inter;
         st->recomputes += ls->recomputes;
+        st->recompute_kept += ls->recompute_kept;
         st->drift_max = fmax(st->drift_max, ls->drift_max);
     }
 }
 
 constexpr int kMaxTileThreads = 512;
+constexpr uint32_t kHistFlushDefault = 1u << 31;   // shared histogram bins stay below 2^31 + wpc
 
 // MINB: CTAs of kMaxTileThreads per SM the registers must allow.  Small systems
 // run a build held to 64 registers (MINB = 2): their moves are short and
@@ -294,17 +311,17 @@ sweep_batched_kernel(const SweepArgs a) {
         const int w_local = w_a + slot_id;
         const int blk = jk_block(w_a, W, a.n_jk);
         __syncthreads();
+        unsigned long long* hs_tile = a.hist_sum ? a.hist_sum + a.hs_off[s_id] + (int64_t)blk * sd.n_bins : nullptr;
         if (w_local < w_b) {
             const int mine = jk_block(w_local, W, a.n_jk);
             unsigned long long* hg =
                 (a.hist_sum && mine != blk) ? a.hist_sum + a.hs_off[s_id] + (int64_t)mine * sd.n_bins : nullptr;
-            run_walker<TPW, PT, GEOM>(sd, a, s_id, w_local, slot, hist, hg, g);
+            run_walker<TPW, PT, GEOM>(sd, a, s_id, w_local, slot, hist, hs_tile, hg, g);
         }
         __syncthreads();
-        if (a.hist_sum) {
-            unsigned long long* hs = a.hist_sum + a.hs_off[s_id] + (int64_t)blk * sd.n_bins;
+        if (hs_tile) {
             for (int k = threadIdx.x; k < sd.n_bins; k += blockDim.x)
-                if (hist[k]) atomicAdd(hs + k, (unsigned long long)hist[k]);
+                if (hist[k]) atomicAdd(hs_tile + k, (unsigned long long)hist[k]);
         }
         __syncthreads();
     }
@@ -526,6 +543,7 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
                 ls->drift_max = fmax(ls->drift_max, fabs(E - Ef));
                 const int bf = bin_of(sd, Ef);
                 if (bf >= 0) { E = Ef; bin = bf; }
+                else ls->recompute_kept++;
                 ls->recomputes++;
             }
         }
@@ -539,6 +557,7 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
         st->pair_evals += ls->pair_evals;
         st->pair_evals_inter += ls->pair_evals_inter;
         st->recomputes += ls->recomputes;
+        st->recompute_kept += ls->recompute_kept;
         st->drift_max = fmax(st->drift_max, ls->drift_max);
     }
 }
@@ -614,6 +633,7 @@ int fill_args(const phast_ctx* c, int64_t n_sweeps, const double* lnW, int n_jk,
     a->scratch = c->plain_scratch;
     a->scratch_stride = 3 * c->max_chain;
     a->hist_bins = c->max_bins;
+    a->hist_flush = c->hist_flush;
     return PHAST_OK;
 }
 
@@ -833,6 +853,7 @@ extern "C" int phast_ctx_create(phast_ctx** out, int32_t n_systems, const phast_
             return phast_set_error(PHAST_ERANGE, "phast_ctx_create: walker %d starts at E = %.17g outside its bins", w, Es[w]);
         }
     default_tile(c, &c->tpw, &c->wpc);
+    c->hist_flush = kHistFlushDefault;
     *out = c;
     return PHAST_OK;
 }
@@ -906,6 +927,14 @@ extern "C" int phast_ctx_set_tile(phast_ctx* c, int32_t tpw, int32_t wpc) {
     return PHAST_OK;
 }
 
+extern "C" int phast_ctx_set_hist_flush(phast_ctx* c, uint32_t count) {
+    if (!c) return phast_set_error(PHAST_EINVAL, "phast_ctx_set_hist_flush: NULL context");
+    if (count > kHistFlushDefault || (count & (count - 1u)))
+        return phast_set_error(PHAST_EINVAL, "phast_ctx_set_hist_flush: %u is not a power of two <= 2^31", count);
+    c->hist_flush = count ? count : kHistFlushDefault;
+    return PHAST_OK;
+}
+
 extern "C" int phast_ctx_get_tile(const phast_ctx* c, int32_t* tpw, int32_t* wpc) {
     if (!c || !tpw || !wpc) return phast_set_error(PHAST_EINVAL, "phast_ctx_get_tile: NULL argument");
     *tpw = c->tpw;
@@ -928,6 +957,10 @@ extern "C" int phast_muca_sweep(phast_ctx* c, int64_t n_sweeps, const double* ln
             return phast_set_error(PHAST_EINVAL, "phast_muca_sweep: n_jk %d > walkers of system %d", n_jk, s);
     if (trace && (trace_walkers < 0 || trace_walkers > c->desc[0].n_walkers))
         return phast_set_error(PHAST_EINVAL, "phast_muca_sweep: trace_walkers outside [0, walkers of system 0]");
+    if (hist_walker && (uint64_t)n_sweeps * (uint64_t)c->max_N >= (1ull << 32))
+        return phast_set_error(PHAST_EINVAL,
+                               "phast_muca_sweep: %lld sweeps x %d moves add >= 2^32 counts to a walker's uint32 "
+                               "histogram (hist_walker); split the call", (long long)n_sweeps, c->max_N);
     if (n_sweeps == 0) return PHAST_OK;
     cudaStream_t st = (cudaStream_t)stream;
     SweepArgs a;

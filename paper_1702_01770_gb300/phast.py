@@ -30,7 +30,7 @@ SYMBOLS = ["phast_energy", "phast_delta_energy", "phast_ctx_create", "phast_ctx_
            "phast_version", "phast_ctx_capture_iteration", "phast_graph_launch",
            "phast_graph_destroy", "phast_energy_grad",
            "phast_reweight_sensitivity", "phast_maxwell", "phast_micro_binned_workspace_size",
-           "phast_micro_analysis_binned"]
+           "phast_micro_analysis_binned", "phast_ctx_set_hist_flush"]
 
 
 class PhastError(RuntimeError):
@@ -67,7 +67,8 @@ class _MicroOut(C.Structure):
 MOVE_DTYPE = np.dtype([("type", "<i4"), ("chain", "<i4"), ("index", "<i4"), ("pad", "<i4"),
                        ("axis", "<f8", 3), ("angle", "<f8"), ("disp", "<f8", 3)])
 STATS_DTYPE = np.dtype([("attempts", "<u8", N_MOVES), ("accepts", "<u8", N_MOVES), ("pair_evals", "<u8"),
-                        ("pair_evals_inter", "<u8"), ("recomputes", "<u8"), ("drift_max", "<f8")])
+                        ("pair_evals_inter", "<u8"), ("recomputes", "<u8"), ("drift_max", "<f8"),
+                        ("recompute_kept", "<u8"), ("pad", "<u8")])
 TRACE_DTYPE = np.dtype([("dE", "<f8"), ("bin_after", "<i4"), ("accepted", "<i4")])
 
 _lib = None
@@ -91,6 +92,7 @@ def lib():
         L.phast_ctx_set_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.phast_ctx_set_tile.argtypes = [vp, i32, i32]
         L.phast_ctx_get_tile.argtypes = [vp, P(i32), P(i32)]
+        L.phast_ctx_set_hist_flush.argtypes = [vp, C.c_uint32]
         L.phast_ctx_autotune.argtypes = [vp, vp, i32, vp]
         L.phast_muca_sweep.argtypes = [vp, i64, vp, i32, i32, vp, vp, vp, i32, vp]
         L.phast_weight_update.argtypes = [i32, dbl, vp, i32, vp, vp, vp, vp, vp]
@@ -365,6 +367,10 @@ class Context:
         _check(lib().phast_ctx_get_tile(self.h, C.byref(a), C.byref(b)))
         return a.value, b.value
 
+    def set_hist_flush(self, count: int = 0):
+        """Count at which a tile's shared histogram bin moves into hist_sum (0: default 2^31)."""
+        _check(lib().phast_ctx_set_hist_flush(self.h, int(count)))
+
     def autotune(self, lnW: torch.Tensor, sweeps: int = 1, stream=None):
         _check(lib().phast_ctx_autotune(self.h, _ptr(lnW), sweeps, _stream(stream)))
         return self.get_tile()
@@ -500,21 +506,37 @@ def phast_micro_analysis(lnW: torch.Tensor, e_min: float, bin_width: float, hist
     r = MicroResult(f(K), f(K), f(K), f(n_T), f(n_T), f(2))
     if errs:
         r.S_err, r.beta_err, r.CV_err, r.E_T_err, r.cV_T_err, r.peak_err = f(K), f(K), f(K), f(n_T), f(n_T), f(2)
-    o = _MicroOut()
-    for name in _MicroOut._fields_:
-        v = getattr(r, name[0])
-        setattr(o, name[0], None if v is None else v.data_ptr())
     if noalloc:
-        _check(lib().phast_micro_analysis_noalloc(K, float(e_min), float(bin_width), _ptr(lnW), _ptr(hist), n_blocks,
-                                                  fd_half_width, n_monomers, n_T, _ptr(T), C.byref(o),
-                                                  _stream(stream)))
-        return r
+        return fill_micro_analysis_noalloc(r, lnW, e_min, bin_width, hist, fd_half_width, n_monomers, T, stream)
+    o = _micro_out(r)
     need = lib().phast_micro_workspace_size(K, n_T, n_blocks)
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty(need, dtype=torch.uint8, device=dev)
     _check(lib().phast_micro_analysis(K, float(e_min), float(bin_width), _ptr(lnW), _ptr(hist), n_blocks,
                                       fd_half_width, n_monomers, n_T, _ptr(T), C.byref(o), _ptr(workspace),
                                       workspace.numel(), _stream(stream)))
+    return r
+
+
+def _micro_out(r: MicroResult) -> _MicroOut:
+    o = _MicroOut()
+    for name in _MicroOut._fields_:
+        v = getattr(r, name[0])
+        setattr(o, name[0], None if v is None else v.data_ptr())
+    return o
+
+
+def fill_micro_analysis_noalloc(r: MicroResult, lnW: torch.Tensor, e_min: float, bin_width: float,
+                                hist: torch.Tensor | None = None, fd_half_width: int = 1, n_monomers: int = 1,
+                                T: torch.Tensor | None = None, stream=None) -> MicroResult:
+    """phast_micro_analysis_noalloc into the caller's result tensors r (no device allocation
+    on this path; T may be None only when r's E_T and cV_T are empty)."""
+    K = lnW.numel()
+    n_blocks = 0 if hist is None else hist.numel() // K
+    n_T = 0 if T is None else T.numel()
+    _check(lib().phast_micro_analysis_noalloc(K, float(e_min), float(bin_width), _ptr(lnW), _ptr(hist), n_blocks,
+                                              fd_half_width, n_monomers, n_T, _ptr(T), C.byref(_micro_out(r)),
+                                              _stream(stream)))
     return r
 
 

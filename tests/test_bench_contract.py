@@ -25,3 +25,20 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_gpus_flag_starts_one_rank_per_gpu_dry_run():
+    """`--gpus 2` outside torchrun relaunches itself as two ranks; the CPU dry run
+    checks the plumbing: disjoint walker keys, one histogram exchange per step, the
+    slowest rank's time, and one line from rank 0 with n_gpus = 2."""
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--dry-run-cpu", "--steps", "3",
+                        "--warmup", "1", "--walkers", "64"], capture_output=True, text=True, timeout=300, cwd=ROOT,
+                       env=env)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1, r.stdout
+    d = json.loads(lines[0])
+    assert d["dry_run"] is True and d["n_gpus"] == 2 and d["exchanges_per_step"] == 1.0
+    assert d["key_ranges"] == [[0, 63], [64, 127]]
+    assert d["max_ms"] == max(d["rank_ms"]) and len(d["rank_ms"]) == 2   # the slowest rank's time

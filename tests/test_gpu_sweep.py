@@ -245,6 +245,56 @@ def test_jackknife_block_histograms(phast):
     ctx.close()
 
 
+@pytest.mark.parametrize("flush", [1, 4, 64])
+def test_shared_histogram_flush_is_exact(phast, orc, flush):
+    """The tile's 32-bit shared histogram moves a bin into the 64-bit sums whenever
+    an increment takes it to a multiple of the flush count.  With a small flush
+    count the flush runs constantly; the block sums must equal the run with the
+    default count, the per-walker histograms summed per block, and the oracle's."""
+    s = inputs.config0(walkers=9728)        # 608 tiles of 16 walkers: whole rounds of the grid
+    lnW = torch.from_numpy(smooth_lnW(s.n_bins, 3)).cuda()
+    n_jk, n_sweeps = 16, 60
+    runs = []
+    for count in (0, flush):
+        ctx = phast.Context(s, pair_precision=64)
+        ctx.set_tile(32, 16)
+        ctx.set_hist_flush(count)
+        hs, hw = ctx.hist_sum_zeros(n_jk), ctx.hist_walker_zeros()
+        ctx.sweep(n_sweeps, lnW, n_jk=n_jk, hist_sum=hs, hist_walker=hw)
+        torch.cuda.synchronize()
+        runs.append((hs.cpu().numpy().reshape(n_jk, s.n_bins), hw.cpu().numpy().reshape(s.walkers, s.n_bins)))
+        ctx.close()
+    (hs0, hw0), (hs1, hw1) = runs
+    assert np.array_equal(hs0, hs1) and np.array_equal(hw0, hw1)
+    per = s.walkers // n_jk
+    for b in range(n_jk):
+        assert np.array_equal(hs1[b], hw1[b * per:(b + 1) * per].astype(np.int64).sum(0))
+    picks = [0, 777, 4100, s.walkers - 1]
+    res = oracle_walkers(orc, s, smooth_lnW(s.n_bins, 3), n_sweeps * s.n_total, walkers=picks)
+    for w, r in zip(picks, res):
+        assert np.array_equal(hw1[w].astype(np.uint64), r[1]), w
+    assert hs1.sum() == s.walkers * n_sweeps * s.n_total
+
+
+def test_histogram_bounds_are_refused(phast):
+    s = inputs.config0(walkers=4)
+    ctx = phast.Context(s, pair_precision=64)
+    lnW = torch.zeros(s.n_bins, dtype=torch.float64, device="cuda")
+    hw = ctx.hist_walker_zeros()
+    n_max = (2 ** 32 - 1) // s.n_total            # the most sweeps whose counts fit a uint32
+    with pytest.raises(phast.PhastError, match="2\\^32"):
+        ctx.sweep(n_max + 1, lnW, hist_walker=hw)
+    for bad in (3, 2 ** 31 + 1, 2 ** 32 - 1):
+        with pytest.raises(phast.PhastError, match="power of two"):
+            ctx.set_hist_flush(bad)
+    ctx.set_hist_flush(2 ** 31)
+    ctx.sweep(1, lnW, hist_walker=hw)            # a call within the bound runs
+    torch.cuda.synchronize()
+    assert int(hw.sum()) == 4 * s.n_total
+    assert np.all(ctx.stats()["recompute_kept"] == 0)
+    ctx.close()
+
+
 def test_resume_and_checkpoint_bit_exact(phast):
     s = inputs.config1(16)
     lnW = torch.from_numpy(smooth_lnW(s.n_bins, 2)).cuda()
