@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sweeps-per-step", type=int, default=10)
     ap.add_argument("--walkers", type=int, default=16384)
+    ap.add_argument("--recompute-every", type=int, default=None,
+                    help="sweeps between FP64 full-energy recomputes (default: the workload's)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -268,6 +270,8 @@ def run_ours(args):
         pass
 
     s = inputs.config4(walkers=args.walkers)
+    if args.recompute_every is not None:
+        s.recompute_every = args.recompute_every
     s.seed_base = parallel.walker_seed_base(rank, args.walkers)
     K, N, S = s.n_bins, s.n_total, args.sweeps_per_step
     ctx = phast.Context(s, pair_precision=32)
@@ -350,6 +354,10 @@ def run_ours(args):
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "clocks": clocks,
         "drift_max": float(st1["drift_max"].max()),
+        "drift_per_walker": {"p50": float(np.percentile(st1["drift_max"], 50)),
+                             "p99": float(np.percentile(st1["drift_max"], 99))},
+        "recompute_every": s.recompute_every,
+        "recompute_outside": int(st1["recompute_outside"].sum()),
         "accept_rate": {name: (float(a) / float(n) if n else None) for name, a, n in
                         zip(MOVE_NAMES, st1["accepts"].sum(0) - st0["accepts"].sum(0),
                             st1["attempts"].sum(0) - st0["attempts"].sum(0))},

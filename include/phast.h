@@ -129,8 +129,10 @@ typedef struct {
     uint64_t pair_evals_inter;  /* the part of pair_evals between different chains */
     uint64_t recomputes;
     double drift_max;      /* largest |E_running - E_full| seen at a recompute */
-    uint64_t recompute_kept;    /* recomputes whose FP64 energy fell outside the bins: the running
-                                   energy and its bin were kept (the drift was not removed) */
+    uint64_t recompute_outside; /* recomputes whose FP64 energy fell outside the bins (an FP32
+                                   rounding let the walker step just past a range edge): the
+                                   running energy takes the FP64 value and the walker counts
+                                   in the nearest edge bin until a move brings it back */
     uint64_t pad;
 } phast_walker_stats;
 
@@ -208,8 +210,10 @@ enum { PHAST_FORM_BATCHED = 0, PHAST_FORM_PLAIN = 1 };
  * (times ((r + delta) / r)^2 for a bond-length move, the Jacobian of its
  * radial map), count the current bin after every attempt.  Proposals out of
  * range, beyond the sphere or with non-finite dE are rejected.  Every
- * recompute_every sweeps (by each walker's
- * own move index) the running energy is replaced by an FP64 full energy.
+ * recompute_every sweeps (by each walker's own move index) the running energy
+ * is replaced by an FP64 full energy, and the bin by its bin (the nearest edge
+ * bin when that energy lies just outside the range; phast_walker_stats counts
+ * those events).
  *  form: PHAST_FORM_BATCHED (shared-memory tiles, FP32 or FP64 pairs per
  *        mp.pair_precision) or PHAST_FORM_PLAIN (one walker per CTA, all FP64,
  *        global-memory histogram atomics; the comparison form).

@@ -571,14 +571,17 @@ int32_t orc_bin(const orc_muca* mu, double E) {
 /* histogram after every attempt, accepted or not.  Readings: one sweep is      */
 /* N_tot attempts; a proposal out of the bin range or with non-finite dE is     */
 /* rejected; every recompute_every sweeps the running energy is replaced by a   */
-/* full FP64 energy (if that lands in range) and the drift recorded.            */
+/* full FP64 energy and the drift recorded; the bin follows, the nearest edge  */
+/* bin for an energy just past a range edge.                                    */
 /* ------------------------------------------------------------------------- */
 int orc_sweep_walker(const orc_model* m, const orc_muca* mu, const double* lnW,
                      uint64_t seed, int64_t n_moves,
                      double* xyz, double* E, int32_t* bin, uint64_t* t,
                      uint64_t* hist, const int8_t* force, orc_record* rec, double* stats) {
     int N = orc_total(m);
-    if (orc_bin(mu, *E) != *bin || *bin < 0) return -1;
+    const int32_t b0 = orc_bin(mu, *E);
+    const int edge = (b0 < 0) && ((*E < mu->e_min && *bin == 0) || (*E >= mu->e_min && *bin == mu->n_bins - 1));
+    if (*bin < 0 || *bin >= mu->n_bins || (b0 != *bin && !edge)) return -1;
     double* xn = (double*)malloc(sizeof(double) * 3 * (size_t)N);
     uint64_t attempts[6] = {0, 0, 0, 0, 0, 0}, accepts[6] = {0, 0, 0, 0, 0, 0};
     int64_t pair_evals = 0, n_recompute = 0, mismatches = 0;
@@ -626,8 +629,11 @@ int orc_sweep_walker(const orc_model* m, const orc_muca* mu, const double* lnW,
             double Ef = orc_energy(m, xyz, NULL);
             double drift = fabs(*E - Ef);
             if (drift > drift_max) drift_max = drift;
-            int32_t bf = orc_bin(mu, Ef);
-            if (bf >= 0) { *E = Ef; *bin = bf; }
+            if (isfinite(Ef)) {
+                int32_t bf = orc_bin(mu, Ef);
+                *E = Ef;
+                *bin = bf >= 0 ? bf : (Ef < mu->e_min ? 0 : mu->n_bins - 1);
+            }
             n_recompute++;
         }
     }

@@ -120,14 +120,16 @@ __device__ __forceinline__ void recompute_energy(const SysDesc& sd, const double
         ls->drift_max = fmax(ls->drift_max, fabs(E - Ef));
         ls->recomputes++;
     }
-    const int bf = bin_of(sd, Ef);
-    if (bf >= 0) {
+    // the running energy always takes the FP64 value (the drift is removed); a
+    // value outside the bins (an FP32 rounding let the walker step just past a
+    // range edge) counts in the nearest edge bin until a move brings it back
+    if (isfinite(Ef)) {
+        const int bf = bin_of(sd, Ef);
         E = Ef;
-        bin = bf;
-        lnw_here = __ldg(lnW + bin);
         erel = (float)(E - sd.e_min);
-    } else if (g.lane == 0) {
-        ls->recompute_kept++;
+        bin = bf >= 0 ? bf : (Ef < sd.e_min ? 0 : sd.n_bins - 1);
+        lnw_here = __ldg(lnW + bin);
+        if (bf < 0 && g.lane == 0) ls->recompute_outside++;
     }
     g.sync();
     build_working<TPW, PT>(sd, x64, slot, g);
@@ -269,7 +271,7 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         st->pair_evals += ls->pair_evals;
         st->pair_evals_inter += ls->pair_evals_inter;
         st->recomputes += ls->recomputes;
-        st->recompute_kept += ls->recompute_kept;
+        st->recompute_outside += ls->recompute_outside;
         st->drift_max = fmax(st->drift_max, ls->drift_max);
     }
 }
@@ -541,9 +543,12 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
             const double Ef = block_full_energy64(sd, x64, red);
             if (threadIdx.x == 0) {
                 ls->drift_max = fmax(ls->drift_max, fabs(E - Ef));
-                const int bf = bin_of(sd, Ef);
-                if (bf >= 0) { E = Ef; bin = bf; }
-                else ls->recompute_kept++;
+                if (isfinite(Ef)) {   // as in the batched form: edge bin when just out of range
+                    const int bf = bin_of(sd, Ef);
+                    E = Ef;
+                    bin = bf >= 0 ? bf : (Ef < sd.e_min ? 0 : sd.n_bins - 1);
+                    if (bf < 0) ls->recompute_outside++;
+                }
                 ls->recomputes++;
             }
         }
@@ -557,7 +562,7 @@ __global__ void __launch_bounds__(kPlainThreads) sweep_plain_kernel(const SweepA
         st->pair_evals += ls->pair_evals;
         st->pair_evals_inter += ls->pair_evals_inter;
         st->recomputes += ls->recomputes;
-        st->recompute_kept += ls->recompute_kept;
+        st->recompute_outside += ls->recompute_outside;
         st->drift_max = fmax(st->drift_max, ls->drift_max);
     }
 }

@@ -68,7 +68,7 @@ MOVE_DTYPE = np.dtype([("type", "<i4"), ("chain", "<i4"), ("index", "<i4"), ("pa
                        ("axis", "<f8", 3), ("angle", "<f8"), ("disp", "<f8", 3)])
 STATS_DTYPE = np.dtype([("attempts", "<u8", N_MOVES), ("accepts", "<u8", N_MOVES), ("pair_evals", "<u8"),
                         ("pair_evals_inter", "<u8"), ("recomputes", "<u8"), ("drift_max", "<f8"),
-                        ("recompute_kept", "<u8"), ("pad", "<u8")])
+                        ("recompute_outside", "<u8"), ("pad", "<u8")])
 TRACE_DTYPE = np.dtype([("dE", "<f8"), ("bin_after", "<i4"), ("accepted", "<i4")])
 
 _lib = None

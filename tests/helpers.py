@@ -56,12 +56,35 @@ def fp32_dE_tolerance(dE_ref: float, scale: float) -> float:
     return 1e-4 * max(1.0, abs(dE_ref)) + 2e-5 * scale
 
 
+STRICT_LOG = []   # one record per checked trace: how the FP32 dE meets the strict 1e-4 relative bound
+
+
+def strict_dE_stats(dE_gpu, dE_ref) -> dict:
+    """How a trace of FP32 dE meets the strict bound |err| <= 1e-4 |dE| (no floor):
+    moves, failures of the strict bound, failures of the bound with a floor of
+    one energy unit, the largest and 99th-percentile ratio err / (1e-4 |dE|), and
+    the largest absolute error."""
+    ok = np.isfinite(dE_ref) & np.isfinite(dE_gpu)
+    err = np.abs(dE_gpu[ok] - dE_ref[ok])
+    ref = np.abs(dE_ref[ok])
+    with np.errstate(divide="ignore", invalid="ignore"):
+        ratio = np.where(ref > 0, err / (1e-4 * ref), np.where(err > 0, np.inf, 0.0))
+    return {"moves": int(ok.sum()), "strict_fail": int((ratio > 1.0).sum()),
+            "floor1_fail": int((err > 1e-4 * np.maximum(1.0, ref)).sum()),
+            "max_ratio": float(ratio.max()) if ratio.size else 0.0,
+            "p99_ratio": float(np.percentile(ratio, 99)) if ratio.size else 0.0,
+            "max_abs_err": float(err.max()) if err.size else 0.0}
+
+
 def check_fp32_trace_dE(orc, s, lnW, seed, dE_gpu, rec, force, label=""):
     """Every finite dE of a replayed FP32 trace within fp32_dE_tolerance; the
     scale is computed (by a prefix replay) only for moves over the 1e-4 floor."""
     m, mu = oracle_model(orc, s), oracle_muca(orc, s)
     ok = np.isfinite(rec["dE"])
     assert np.array_equal(ok, np.isfinite(dE_gpu)), label
+    st = strict_dE_stats(np.asarray(dE_gpu, float), np.asarray(rec["dE"], float))
+    STRICT_LOG.append({"system": s.name, "label": label, **st})
+    print(f"strict dE bound [{s.name} {label}]: {st}")
     err = np.zeros(ok.shape)
     err[ok] = np.abs(dE_gpu[ok] - rec["dE"][ok])
     base = 1e-4 * np.maximum(1.0, np.abs(np.where(ok, rec["dE"], 0.0)))

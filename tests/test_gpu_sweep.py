@@ -291,7 +291,7 @@ def test_histogram_bounds_are_refused(phast):
     ctx.sweep(1, lnW, hist_walker=hw)            # a call within the bound runs
     torch.cuda.synchronize()
     assert int(hw.sum()) == 4 * s.n_total
-    assert np.all(ctx.stats()["recompute_kept"] == 0)
+    assert np.all(ctx.stats()["recompute_outside"] == 0)
     ctx.close()
 
 
