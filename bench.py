@@ -55,6 +55,11 @@ def parse():
     ap.add_argument("--no-geom", action="store_true")
     ap.add_argument("--geom-only", action="store_true")
     ap.add_argument("--geom-tile", type=int, nargs=2, default=None, metavar=("TPW", "WPC"))
+    ap.add_argument("--eager", action="store_true",
+                    help="run the headline step's sweeps and Berg update as separate calls instead of a captured "
+                         "CUDA graph (always so with more than one rank: the histogram all-reduce sits between them)")
+    ap.add_argument("--no-uneven", action="store_true")
+    ap.add_argument("--uneven-only", action="store_true")
     ap.add_argument("--dry-run-cpu", action="store_true",
                     help="rank plumbing only, on CPU over gloo: walker keys, one histogram exchange per step, "
                          "max-over-ranks time (no GPU, no sweep)")
@@ -248,6 +253,105 @@ def measure_geometry(args, dev):
     return res
 
 
+UNEVEN_CHUNK = 1000        # sweeps per captured iteration of the four-type workload
+
+
+def _flops(pe, pex):
+    return (pe - pex) * FLOPS_OPEN + pex * FLOPS_PBC
+
+
+def measure_uneven(args, dev, peak_tf):
+    """Four uneven system types in one persistent launch (1024 walkers each: a
+    Fibonacci 13-mer, a Fibonacci 21-mer, two 34-mers in L = 40, eight 9-mers in
+    L = 30), FP32 pairs: the autotuned tile, one multicanonical iteration of
+    UNEVEN_CHUNK sweeps captured as a CUDA graph and replayed; then each type alone
+    (its own autotuned tile) and the plain FP64 form on the same four types."""
+    import numpy as np
+    import torch
+
+    from paper_1702_01770_gb300 import inputs, phast
+    systems = inputs.config2(walkers_each=1024)
+    ctx = phast.Context(systems, pair_precision=32)
+    lnW = ctx.lnW_zeros()
+    g = torch.zeros_like(lnW)
+    n_jk = 16
+    hs = ctx.hist_sum_zeros(n_jk)
+    flat = torch.zeros(len(systems), 4, dtype=torch.float64, device=dev)
+    default_tile = ctx.get_tile()
+    tile = ctx.autotune(lnW, sweeps=10)
+    graph = ctx.capture_iteration(UNEVEN_CHUNK, lnW, hs, g, n_jk=n_jk, flat_out=flat)
+    graph.launch()                               # warm-up iteration
+    torch.cuda.synchronize()
+    st0 = ctx.stats()
+    reps = 3
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        graph.launch()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    st1 = ctx.stats()
+    graph.close()
+    per_type = []
+    for k, x in enumerate(systems):
+        sl = slice(ctx.walker_off[k], ctx.walker_off[k] + x.walkers)
+        mv = int(st1["attempts"][sl].sum() - st0["attempts"][sl].sum()) // reps
+        pe = int(st1["pair_evals"][sl].sum() - st0["pair_evals"][sl].sum()) // reps
+        pex = int(st1["pair_evals_inter"][sl].sum() - st0["pair_evals_inter"][sl].sum()) // reps
+        per_type.append({"system": x.name, "walkers": x.walkers, "moves_per_chunk": mv, "pair_evals_per_chunk": pe,
+                         "pair_evals_inter_per_chunk": pex})
+    moves = sum(t["moves_per_chunk"] for t in per_type)
+    pe = sum(t["pair_evals_per_chunk"] for t in per_type)
+    fl = sum(_flops(t["pair_evals_per_chunk"], t["pair_evals_inter_per_chunk"]) for t in per_type)
+    ctx.close()
+    # each type alone: the share of the chip it gets when it has the chip to itself
+    for k, x in enumerate(systems):
+        c1 = phast.Context(x, pair_precision=32)
+        l1 = c1.lnW_zeros()
+        t1 = c1.autotune(l1, sweeps=10)
+        c1.sweep(20, l1)
+        torch.cuda.synchronize()
+        s0 = c1.stats()
+        a.record()
+        c1.sweep(200, l1)
+        b.record()
+        torch.cuda.synchronize()
+        s1 = c1.stats()
+        t_ms = a.elapsed_time(b)
+        m1 = int(s1["attempts"].sum() - s0["attempts"].sum())
+        p1 = int(s1["pair_evals"].sum() - s0["pair_evals"].sum())
+        x1 = int(s1["pair_evals_inter"].sum() - s0["pair_evals_inter"].sum())
+        per_type[k]["alone"] = {"tile": list(t1), "walker_moves_per_s": m1 / (t_ms / 1e3),
+                                "pair_evals_per_s": p1 / (t_ms / 1e3),
+                                "fp32_frac": _flops(p1, x1) / (t_ms / 1e3) / 1e12 / peak_tf}
+        c1.close()
+    res = {"workload": "four system types in one launch, 1024 walkers each: Fibonacci 13-mer, Fibonacci 21-mer, "
+                       "2 x 34-mer (L = 40), 8 x 9-mer (L = 30); FP32 pairs, FP64 totals",
+           "launch": f"captured CUDA graph per iteration of {UNEVEN_CHUNK} sweeps (clear, sweeps, Berg per type)",
+           "tile_autotuned": list(tile), "tile_default": list(default_tile), "ms_per_chunk": ms,
+           "walker_moves_per_s": moves / (ms / 1e3), "pair_evals_per_s": pe / (ms / 1e3),
+           "fp32_frac": fl / (ms / 1e3) / 1e12 / peak_tf, "per_type": per_type, "dtype": "f32"}
+    # the plain one-walker-per-CTA FP64 form on the same four types
+    cp = phast.Context(systems, pair_precision=64)
+    lp = cp.lnW_zeros()
+    cp.sweep(1, lp, form=phast.FORM_PLAIN)
+    torch.cuda.synchronize()
+    p0 = cp.stats()
+    a.record()
+    cp.sweep(5, lp, form=phast.FORM_PLAIN)
+    b.record()
+    torch.cuda.synchronize()
+    p1 = cp.stats()
+    pms = a.elapsed_time(b)
+    res["plain"] = {"walker_moves_per_s": float((p1["attempts"].sum() - p0["attempts"].sum()) / (pms / 1e3)),
+                    "pair_evals_per_s": float((p1["pair_evals"].sum() - p0["pair_evals"].sum()) / (pms / 1e3)),
+                    "sweeps": 5, "dtype": "f64"}
+    res["batched_over_plain"] = res["walker_moves_per_s"] / res["plain"]["walker_moves_per_s"]
+    cp.close()
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -263,11 +367,17 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps({"geometry": measure_geometry(args, dev)}), flush=True)
         return
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
+    max_mhz = float(peaks.get("sm_max_mhz") or 2070.0)
+    if args.uneven_only:   # the four-type workload alone (a profiling aid)
+        if rank == 0:
+            print(json.dumps({"uneven": measure_uneven(args, dev, n_sm * 256 * max_mhz * 1e6 / 1e12)}), flush=True)
+        return
 
     s = inputs.config4(walkers=args.walkers)
     if args.recompute_every is not None:
@@ -282,8 +392,22 @@ def run_ours(args):
     T = torch.linspace(0.3, 3.0, N_T, dtype=torch.float64, device=dev)
     ws = torch.empty(phast.lib().phast_micro_workspace_size(K, N_T, N_JK), dtype=torch.uint8, device=dev)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    use_graph = not args.eager and world == 1
+    graph, lnW_used = None, torch.empty_like(lnW)
+    if use_graph:   # one multicanonical iteration (clear, sweeps, Berg) as a captured CUDA graph
+        graph = ctx.capture_iteration(S, lnW, hs, g, n_jk=N_JK, flat_out=flat)
+        torch.cuda.synchronize()
 
     def step(i=None):
+        if use_graph:
+            lnW_used.copy_(lnW)            # the weights this iteration samples with (Berg rewrites lnW)
+            if i is not None:
+                ev[i][0].record()
+            graph.launch()
+            if i is not None:
+                ev[i][1].record()
+            return phast.phast_micro_analysis(lnW_used, s.e_min, s.bin_width, hist=hs.view(N_JK, K),
+                                              fd_half_width=5, n_monomers=N, T=T, workspace=ws)
         hs.zero_()
         if i is not None:
             ev[i][0].record()
@@ -328,7 +452,6 @@ def run_ours(args):
     value = total_moves / (ms / 1e3)
 
     # roofline of the sweep kernel: algorithmic FP32 flops / its event-timed duration
-    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
     peak_tf = n_sm * 128 * 2 * max_mhz * 1e6 / 1e12
     achieved_tf = flops / (sum(sweep_ms) / 1e3) / 1e12
@@ -337,7 +460,9 @@ def run_ours(args):
                 "peak_basis": f"derived: {n_sm} SMs x 128 FP32 lanes x 2 flop x {max_mhz:.0f} MHz (max SM clock)",
                 "kernel": "sweep_batched_kernel<32,float,0,1> (no FENE, sphere, bond or cap moves)",
                 "frac_at_median_clock": (achieved_tf / (n_sm * 256 * clocks["sm_mhz"] * 1e6 / 1e12))
-                if clocks.get("sm_mhz") else None}
+                if clocks.get("sm_mhz") else None,
+                "timed": ("CUDA events around each captured iteration (histogram clear, the sweep kernel, "
+                          "the Berg kernel)" if use_graph else "CUDA events around each sweep launch")}
 
     out = {
         "metric": METRIC, "value": value, "unit": "walker-moves/s", "n_gpus": world, "steps": args.steps,
@@ -347,7 +472,9 @@ def run_ours(args):
                    "step": "sweeps + analysis (16 jackknife blocks, 64 T) + Berg update",
                    "precision": "FP32 pair and local terms, FP64 geometry/totals/weights/histogram sums",
                    "l2": "inputs larger than L2 (walker state %.0f MB)" % (args.walkers * N * 24 / 1e6),
-                   "tile": list(ctx.get_tile())},
+                   "tile": list(ctx.get_tile()),
+                   "launch": ("captured CUDA graph per iteration (clear, sweeps, Berg), analysis after it"
+                              if use_graph else "separate calls")},
         "pair_evals_per_s": pe * world / (ms / 1e3),
         "sweep_kernel_ms_per_step": sum(sweep_ms) / args.steps,
         "roofline": roofline,
@@ -428,6 +555,9 @@ def run_ours(args):
     if not args.no_geom and rank == 0:
         out["geometry"] = measure_geometry(args, dev)
 
+    if not args.no_uneven and rank == 0:
+        out["uneven"] = measure_uneven(args, dev, peak_tf)
+
     # end to end through the C ABI with host buffers: state in from pinned host memory, results out
     if not args.no_e2e:
         st = ctx.get_state("cpu")
@@ -464,6 +594,8 @@ def run_ours(args):
                                          f"FP64 oracle, {dt:.1f} s", "pair_evals_per_s": pev}
     if rank == 0:
         print(json.dumps(out), flush=True)
+    if graph is not None:
+        graph.close()
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
