@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-geom", action="store_true")
     ap.add_argument("--geom-only", action="store_true")
     ap.add_argument("--geom-tile", type=int, nargs=2, default=None, metavar=("TPW", "WPC"))
+    ap.add_argument("--geom-walkers", type=int, default=GEOM_WALKERS)
     ap.add_argument("--eager", action="store_true",
                     help="run the headline step's sweeps and Berg update as separate calls instead of a captured "
                          "CUDA graph (always so with more than one rank: the histogram all-reduce sits between them)")
@@ -216,7 +217,7 @@ def measure_geometry(args, dev):
     import torch
 
     from paper_1702_01770_gb300 import inputs, phast
-    gsys = inputs.fene_sphere(walkers=GEOM_WALKERS)
+    gsys = inputs.fene_sphere(walkers=args.geom_walkers)
     gctx = phast.Context(gsys, pair_precision=32)
     glnW = torch.zeros(gsys.n_bins, dtype=torch.float64, device=dev)
     if args.geom_tile:
@@ -235,15 +236,16 @@ def measure_geometry(args, dev):
     g1 = gctx.stats()
     gms = a.elapsed_time(b)
     gmoves = int(g1["attempts"].sum() - g0["attempts"].sum())
-    assert gmoves == GEOM_WALKERS * gsys.n_total * GEOM_SWEEPS
+    assert gmoves == args.geom_walkers * gsys.n_total * GEOM_SWEEPS
     res = {
         "workload": "2 Fibonacci 13-mers in a steric sphere R = 8, FENE bonds (k_F = -20, R_F = 0.3), "
-                    f"all six move types, {GEOM_WALKERS} walkers, flat weights, {GEOM_SWEEPS} sweeps",
-        "kernel": f"sweep_batched_kernel<{gtile[0]},float,1>", "tile": list(gtile),
+                    f"all six move types, {args.geom_walkers} walkers, flat weights, {GEOM_SWEEPS} sweeps",
+        "kernel": ("sweep_lane_kernel<float,1> (one walker per thread)" if gtile[0] == 1
+                   else f"sweep_batched_kernel<{gtile[0]},float,1>"), "tile": list(gtile),
         "walker_moves_per_s": gmoves / (gms / 1e3),
         "pair_evals_per_s": float((g1["pair_evals"].sum() - g0["pair_evals"].sum()) / (gms / 1e3)),
         "accept_rate": float((g1["accepts"].sum() - g0["accepts"].sum()) / gmoves), "dtype": "f32",
-        "l2": "walker state %.0f MB, L2-resident" % (GEOM_WALKERS * gsys.n_total * 24 / 1e6)}
+        "l2": "walker state %.0f MB, L2-resident" % (args.geom_walkers * gsys.n_total * 24 / 1e6)}
     if not args.no_cpu_baseline:
         v, pev, n, dt = oracle_walker_moves_per_s(inputs.fene_sphere(walkers=1), 4.0, os.cpu_count() or 1)
         res["cpu_baseline"] = {"value": v, "unit": "walker-moves/s", "cores": os.cpu_count() or 1,

@@ -70,9 +70,16 @@ struct SweepArgs {
     double* scratch;
     int scratch_stride;                   // doubles per walker in scratch
     SlotLayout L;
+    LaneLayout LL;                        // per-warp layout of the one-walker-per-thread form
     int hist_bins;                        // shared histogram capacity (max n_bins)
     uint32_t hist_flush;                  // a shared bin reaching this count moves it into hist_sum
 };
+
+}  // namespace
+
+#include "lane.cuh"   // the one-walker-per-thread form (uses SweepArgs)
+
+namespace {
 
 __device__ __forceinline__ void copy_desc(SysDesc* dst, const SysDesc* src) {
     const int4* s = reinterpret_cast<const int4*>(src);
@@ -319,6 +326,53 @@ sweep_batched_kernel(const SweepArgs a) {
             unsigned long long* hg =
                 (a.hist_sum && mine != blk) ? a.hist_sum + a.hs_off[s_id] + (int64_t)mine * sd.n_bins : nullptr;
             run_walker<TPW, PT, GEOM>(sd, a, s_id, w_local, slot, hist, hs_tile, hg, g);
+        }
+        __syncthreads();
+        if (hs_tile) {
+            for (int k = threadIdx.x; k < sd.n_bins; k += blockDim.x)
+                if (hist[k]) atomicAdd(hs_tile + k, (unsigned long long)hist[k]);
+        }
+        __syncthreads();
+    }
+}
+
+// One walker per thread (small systems): the same persistent tiles, a tile being
+// the CTA's blockDim.x walkers, each warp's walkers in one lane-interleaved
+// shared-memory slot.
+constexpr int kLaneMaxThreads = 256;
+
+template <typename PT, bool GEOM>
+__global__ void __launch_bounds__(kLaneMaxThreads)
+sweep_lane_kernel(const SweepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_tile;
+    SysDesc& sd = *reinterpret_cast<SysDesc*>(smem);
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + sizeof(SysDesc));
+    unsigned char* warps = smem + sizeof(SysDesc) + align16(4 * a.hist_bins);
+    const LaneSlot<PT> slot(warps + (size_t)(threadIdx.x >> 5) * a.LL.bytes, a.LL, threadIdx.x & 31);
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(a.tile_counter, 1);
+        __syncthreads();
+        const int tile = s_tile;
+        if (tile >= a.n_tiles) break;
+        int pos = 0;
+        while (pos + 1 < a.n_sys && tile >= a.tile_start[pos + 1]) ++pos;
+        const int s_id = a.order[pos];
+        copy_desc(&sd, a.descs + s_id);
+        __syncthreads();
+        for (int k = threadIdx.x; k < sd.n_bins; k += blockDim.x) hist[k] = 0u;
+        const int k = tile - a.tile_start[pos], nt = a.tiles[pos];
+        const int W = sd.n_walkers;
+        const int w_a = (int)((int64_t)k * W / nt), w_b = (int)((int64_t)(k + 1) * W / nt);
+        const int w_local = w_a + (int)threadIdx.x;
+        const int blk = jk_block(w_a, W, a.n_jk);
+        __syncthreads();
+        unsigned long long* hs_tile = a.hist_sum ? a.hist_sum + a.hs_off[s_id] + (int64_t)blk * sd.n_bins : nullptr;
+        if (w_local < w_b) {
+            const int mine = jk_block(w_local, W, a.n_jk);
+            unsigned long long* hg =
+                (a.hist_sum && mine != blk) ? a.hist_sum + a.hs_off[s_id] + (int64_t)mine * sd.n_bins : nullptr;
+            run_walker_lane<PT, GEOM>(sd, a, s_id, w_local, slot, hist, hs_tile, hg);
         }
         __syncthreads();
         if (hs_tile) {
@@ -591,6 +645,9 @@ batched_fn pick_batched_g(int tpw, bool fp32, bool lean) {
 constexpr int kLeanMaxN = 48;
 
 batched_fn pick_batched(int tpw, bool fp32, bool geom, bool lean) {
+    if (tpw == 1)
+        return geom ? (fp32 ? sweep_lane_kernel<float, true> : sweep_lane_kernel<double, true>)
+                    : (fp32 ? sweep_lane_kernel<float, false> : sweep_lane_kernel<double, false>);
     return geom ? pick_batched_g<true>(tpw, fp32, lean) : pick_batched_g<false>(tpw, fp32, lean);
 }
 
@@ -599,6 +656,19 @@ size_t batched_smem(const phast_ctx* c, bool fp32, int wpc, SlotLayout* L) {
     *L = fp32 ? slot_layout<float>(c->max_N, c->max_nc, c->max_chain)
               : slot_layout<double>(c->max_N, c->max_nc, c->max_chain);
     return sizeof(SysDesc) + (size_t)align16(4 * c->max_bins) + (size_t)wpc * L->bytes;
+}
+
+// Shared memory of a one-walker-per-thread tile of wpc walkers (wpc / 32 warp slots).
+size_t lane_smem(const phast_ctx* c, bool fp32, int wpc, LaneLayout* L) {
+    *L = fp32 ? lane_layout<float>(c->max_N, c->max_nc, c->max_chain)
+              : lane_layout<double>(c->max_N, c->max_nc, c->max_chain);
+    return sizeof(SysDesc) + (size_t)align16(4 * c->max_bins) + (size_t)(wpc / 32) * L->bytes;
+}
+
+size_t tile_smem(const phast_ctx* c, bool fp32, int tpw, int wpc) {
+    SlotLayout S;
+    LaneLayout L;
+    return tpw == 1 ? lane_smem(c, fp32, wpc, &L) : batched_smem(c, fp32, wpc, &S);
 }
 
 double system_cost(const SysDesc& d) {
@@ -688,14 +758,17 @@ struct BatchedLaunch {
 int prepare_batched(phast_ctx* c, const SweepArgs& a0, int tpw, int wpc, bool fp32, BatchedLaunch* L) {
     L->a = a0;
     SlotLayout SL;
-    L->smem = batched_smem(c, fp32, wpc, &SL);
+    LaneLayout LLay;
+    L->smem = tpw == 1 ? lane_smem(c, fp32, wpc, &LLay) : batched_smem(c, fp32, wpc, &SL);
     L->a.L = SL;
+    L->a.LL = LLay;
     L->fn = pick_batched(tpw, fp32, uses_geometry(c), c->max_N < kLeanMaxN);
-    if (!L->fn) return phast_set_error(PHAST_EINVAL, "threads per walker %d not in {4, 8, 16, 32}", tpw);
+    if (!L->fn) return phast_set_error(PHAST_EINVAL, "threads per walker %d not in {1, 4, 8, 16, 32}", tpw);
     L->threads = tpw * wpc;
-    if (L->threads < 32 || L->threads > kMaxTileThreads || L->threads % 32)
+    const int max_threads = tpw == 1 ? kLaneMaxThreads : kMaxTileThreads;
+    if (L->threads < 32 || L->threads > max_threads || L->threads % 32)
         return phast_set_error(PHAST_EINVAL, "tile of %d x %d threads is not a whole number of warps <= %d", tpw, wpc,
-                               kMaxTileThreads);
+                               max_threads);
     int max_sm = 0;
     PHAST_CUDA_TRY(cudaDeviceGetAttribute(&max_sm, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
     if (L->smem + 64 > (size_t)max_sm)
@@ -704,7 +777,7 @@ int prepare_batched(phast_ctx* c, const SweepArgs& a0, int tpw, int wpc, bool fp
     int per_sm = 0, n_sm = 0;
     PHAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, L->fn, L->threads, L->smem));
     const batched_fn full = pick_batched(tpw, fp32, uses_geometry(c), false);
-    if (L->fn != full) {   // the 64-register build pays only if more CTAs then share an SM
+    if (tpw != 1 && L->fn != full) {   // the 64-register build pays only if more CTAs then share an SM
         int per_sm_full = 0;
         PHAST_CUDA_TRY(cudaFuncSetAttribute(full, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem));
         PHAST_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_full, full, L->threads, L->smem));
@@ -922,11 +995,12 @@ extern "C" int phast_ctx_set_tile(phast_ctx* c, int32_t tpw, int32_t wpc) {
     default_tile(c, &dt, &dw);
     if (tpw == 0) tpw = dt;
     if (wpc == 0) wpc = dw;
-    if (tpw != 4 && tpw != 8 && tpw != 16 && tpw != 32)
-        return phast_set_error(PHAST_EINVAL, "phast_ctx_set_tile: threads per walker %d not in {4, 8, 16, 32}", tpw);
-    if (wpc < 1 || tpw * wpc > kMaxTileThreads || (tpw * wpc) % 32)
+    if (tpw != 1 && tpw != 4 && tpw != 8 && tpw != 16 && tpw != 32)
+        return phast_set_error(PHAST_EINVAL, "phast_ctx_set_tile: threads per walker %d not in {1, 4, 8, 16, 32}", tpw);
+    const int max_threads = tpw == 1 ? kLaneMaxThreads : kMaxTileThreads;
+    if (wpc < 1 || tpw * wpc > max_threads || (tpw * wpc) % 32)
         return phast_set_error(PHAST_EINVAL, "phast_ctx_set_tile: %d walkers of %d threads is not a whole number of warps <= %d",
-                               wpc, tpw, kMaxTileThreads);
+                               wpc, tpw, max_threads);
     c->tpw = tpw;
     c->wpc = wpc;
     return PHAST_OK;
@@ -1001,11 +1075,11 @@ extern "C" int phast_ctx_autotune(phast_ctx* c, const double* lnW, int32_t sweep
     int best_t = c->tpw, best_w = c->wpc;
     float best = 1e30f;
     const int cands[][2] = {{32, 4}, {32, 8}, {32, 16}, {16, 4}, {16, 8}, {16, 16}, {16, 32}, {8, 8}, {8, 16},
-                            {8, 32}, {8, 64}, {4, 16}, {4, 32}, {4, 64}, {4, 128}};
+                            {8, 32}, {8, 64}, {4, 16}, {4, 32}, {4, 64}, {4, 128}, {1, 32}, {1, 64}, {1, 128},
+                            {1, 256}};
     for (const auto& cd : cands) {
         if (e != cudaSuccess) break;
-        SlotLayout L;
-        if (batched_smem(c, fp32, cd[1], &L) > 220 * 1024) continue;
+        if (tile_smem(c, fp32, cd[0], cd[1]) > 220 * 1024) continue;
         e = cudaMemcpyAsync(tmp.xyz, c->xyz, sizeof(double) * c->xyz_total, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(tmp.E, c->E, sizeof(double) * c->W, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(tmp.bin, c->bin, sizeof(int32_t) * c->W, cudaMemcpyDeviceToDevice, st);

@@ -75,11 +75,14 @@ def test_delta_energy_every_move_type(phast, orc, precision):
     assert seen == set(range(6))
 
 
+@pytest.mark.parametrize("tile", [None, (1, 32)])
 @pytest.mark.parametrize("precision", [64, 32])
-def test_sweep_lockstep_with_oracle(phast, orc, precision):
+def test_sweep_lockstep_with_oracle(phast, orc, precision, tile):
     s = inputs.fene_sphere(32)
     n_tr, n_sweeps = 4, 150
     ctx = phast.Context(s, pair_precision=precision)
+    if tile:
+        ctx.set_tile(*tile)
     k = np.arange(s.n_bins)
     lnW = -0.03 * k + 0.5 * np.sin(k / 13.0)
     trace = ctx.trace_buffer(n_sweeps, n_tr)
@@ -181,13 +184,15 @@ def test_bond_moves_sample_the_cartesian_measure(phast, precision):
     assert abs(x.mean() - x_mean) < 0.02, (x.mean(), x_mean)     # 0 without the Hastings factor
 
 
-@pytest.mark.parametrize("form", ["plain", "batched"])
+@pytest.mark.parametrize("form", ["plain", "batched", "lane"])
 def test_fp64_sweeps_follow_the_oracle_unforced(phast, orc, form):
     # no imposed decisions: the GPU and the oracle walk the same chains move for
     # move, so histograms, coordinates and per-type acceptance counts agree
     from test_gpu_sweep import oracle_walkers
     s = inputs.fene_sphere(8)
     ctx = phast.Context(s, pair_precision=64)
+    if form == "lane":
+        ctx.set_tile(1, 32)
     k = np.arange(s.n_bins)
     lnW = -0.02 * k + 0.6 * np.sin(k / 23.0)
     n_sweeps = 500
@@ -224,12 +229,15 @@ def _tight_sphere(walkers):
                                seq=inputs.fibonacci_sequence(13), sphere_R=2.6, xyz0=x)
 
 
+@pytest.mark.parametrize("tile", [None, (1, 64)])
 @pytest.mark.parametrize("precision", [32, 64])
-def test_tight_sphere_stays_inside(phast, orc, precision):
+def test_tight_sphere_stays_inside(phast, orc, precision, tile):
     # near the wall the FP32 sweep decides with the exact positions, which must
     # include the accepted moves still waiting for their exact replay
     s = _tight_sphere(4096)
     ctx = phast.Context(s, pair_precision=precision)
+    if tile:
+        ctx.set_tile(*tile)
     n_tr, n_sweeps = 6, 300
     k = np.arange(s.n_bins)
     lnW = -0.02 * k

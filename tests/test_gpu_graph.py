@@ -24,9 +24,10 @@ def _hs_offsets(ctx, n_jk):
     return out
 
 
+@pytest.mark.parametrize("tile", [None, (1, 32)])
 @pytest.mark.parametrize("workload", ["four types", "sphere"])
 @pytest.mark.parametrize("precision", [32, 64])
-def test_graph_iterations_equal_eager_calls(phast, precision, workload):
+def test_graph_iterations_equal_eager_calls(phast, precision, workload, tile):
     if workload == "four types":
         systems = inputs.config2(walkers_each=8)  # four uneven system types in one launch
     else:
@@ -34,6 +35,9 @@ def test_graph_iterations_equal_eager_calls(phast, precision, workload):
     n_jk, S, iters = 2, 15, 3
     a = phast.Context(systems, pair_precision=precision)
     b = phast.Context(systems, pair_precision=precision)
+    if tile:
+        a.set_tile(*tile)
+        b.set_tile(*tile)
     lnWa, lnWb = a.lnW_zeros(), b.lnW_zeros()
     ga, gb = torch.zeros_like(lnWa), torch.zeros_like(lnWb)
     hsa, hsb = a.hist_sum_zeros(n_jk), b.hist_sum_zeros(n_jk)

@@ -54,7 +54,8 @@ def smooth_lnW(K, seed=0):
     return -0.04 * k + 0.8 * np.sin(k / 17.0 + seed)
 
 
-@pytest.mark.parametrize("form,tile", [("plain", None), ("batched", (8, 8)), ("batched", (32, 2))])
+@pytest.mark.parametrize("form,tile", [("plain", None), ("batched", (8, 8)), ("batched", (32, 2)),
+                                       ("batched", (1, 32))])
 def test_fp64_decisions_and_histograms_bit_exact(phast, orc, form, tile):
     s = inputs.config0()
     ctx = phast.Context(s, pair_precision=64)
@@ -136,11 +137,14 @@ def _near_tie(E_o, dE_o, dE_g, s, lnW, u, b0, tol):
     return False
 
 
+@pytest.mark.parametrize("tile", [None, (1, 64)])
 @pytest.mark.parametrize("name", ["4x9", "xseed"])
-def test_fp32_lockstep_with_oracle(phast, orc, name):
+def test_fp32_lockstep_with_oracle(phast, orc, name, tile):
     s = inputs.config1(64) if name == "4x9" else paper_cross_seeding(64)
     n_tr, n_sweeps = 4, 300
     ctx = phast.Context(s, pair_precision=32)
+    if tile:
+        ctx.set_tile(*tile)
     lnW = smooth_lnW(s.n_bins, 1)
     trace = ctx.trace_buffer(n_sweeps, n_tr)
     ctx.sweep(n_sweeps, torch.from_numpy(lnW).cuda(), trace=trace, trace_walkers=n_tr)
@@ -199,11 +203,14 @@ def test_fp32_drift_recompute(phast, orc):
     ctx.close()
 
 
-def test_uneven_batch_plain_equals_batched_fp64(phast, orc):
+@pytest.mark.parametrize("tile", [None, (1, 32)])
+def test_uneven_batch_plain_equals_batched_fp64(phast, orc, tile):
     systems = inputs.config2(walkers_each=8)
     systems = [all_move_types(x) for x in systems]
     a = phast.Context(systems, pair_precision=64)
     b = phast.Context(systems, pair_precision=64)
+    if tile:
+        b.set_tile(*tile)
     lnW = torch.cat([torch.from_numpy(smooth_lnW(x.n_bins, i)) for i, x in enumerate(systems)]).cuda()
     ha, hb = a.hist_walker_zeros(), b.hist_walker_zeros()
     a.sweep(20, lnW, form=phast.FORM_PLAIN, hist_walker=ha)
@@ -226,10 +233,11 @@ def test_uneven_batch_plain_equals_batched_fp64(phast, orc):
     b.close()
 
 
-def test_jackknife_block_histograms(phast):
+@pytest.mark.parametrize("tile", [(8, 8), (1, 32)])
+def test_jackknife_block_histograms(phast, tile):
     s = inputs.config1(40)
     ctx = phast.Context(s, pair_precision=32)
-    ctx.set_tile(8, 8)
+    ctx.set_tile(*tile)
     lnW = torch.zeros(s.n_bins, dtype=torch.float64, device="cuda")
     n_jk = 6                                # blocks of 6 or 7 walkers, tiles of 8: ragged tiles
     hs = ctx.hist_sum_zeros(n_jk)
@@ -328,7 +336,7 @@ def test_tile_invariance_fp64(phast):
     s = paper_cross_seeding(24)
     lnW = torch.from_numpy(smooth_lnW(s.n_bins, 3)).cuda()
     out = []
-    for tile in [(4, 8), (8, 16), (16, 4), (32, 2)]:
+    for tile in [(4, 8), (8, 16), (16, 4), (32, 2), (1, 32), (1, 64)]:
         c = phast.Context(s, pair_precision=64)
         c.set_tile(*tile)
         h = c.hist_walker_zeros()
@@ -349,7 +357,7 @@ def test_autotune_keeps_state(phast):
     tile = c.autotune(lnW, sweeps=1)
     after = c.get_state("cpu")
     torch.cuda.synchronize()
-    assert tile[0] in (4, 8, 16, 32) and tile[0] * tile[1] % 32 == 0
+    assert tile[0] in (1, 4, 8, 16, 32) and tile[0] * tile[1] % 32 == 0
     assert torch.equal(before["xyz"], after["xyz"]) and torch.equal(before["t"], after["t"])
     c.sweep(1, lnW)
     c.close()
