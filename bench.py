@@ -532,10 +532,18 @@ def run_ours(args):
         gms = a.elapsed_time(b) / reps
         n = gs.n_total
         pairs = n * (n - 1) // 2 - (n - 1)
+        # roofline: each of the `pairs` Lennard-Jones pairs of a conformation gives its energy term
+        # (14 flops) and its gradient contribution (4 more for dphi/dr^2, 6 for the force on both
+        # ends: 24 flops); the kernel evaluates each pair from both of its ends
+        grad_tf = gx0.shape[0] * pairs * 24 / (gms / 1e3) / 1e12
         out["differentiation"] = {"workload": "65536 random self-avoiding walks of a Fibonacci 55-mer (d_min 0.8)",
                                   "ms_per_batch": gms, "conformations_per_s": gx0.shape[0] / (gms / 1e3),
                                   "pair_terms_per_s": gx0.shape[0] * pairs / (gms / 1e3),
-                                  "outputs": "E, dE/dx, dE/d(C_AA, C_BB, C_AB, kappa, kappa_C)", "dtype": "f32"}
+                                  "outputs": "E, dE/dx, dE/d(C_AA, C_BB, C_AB, kappa, kappa_C)", "dtype": "f32",
+                                  "roofline": {"bound": "alu", "achieved": grad_tf, "peak": peak_tf,
+                                               "unit": "TFLOP/s", "frac": grad_tf / peak_tf,
+                                               "kernel": "energy_grad32_chain_kernel",
+                                               "flops_per_pair": 24}}
         del gxyz
 
     # free energy and Maxwell construction of the last step's S(E), with the

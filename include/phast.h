@@ -274,6 +274,15 @@ int phast_energy_grad(const phast_system* sys, const phast_ff* ff, int32_t B, co
                       int32_t pair_precision, double* E_out, double* grad_xyz, double* grad_ff,
                       void* stream);
 
+/* The same with the five parameters (C_AA, C_BB, C_AB, kappa, kappa_C) read
+ * from params, a dev FP64 [5] array, in place of ff's values (C_AB serves AB
+ * and BA): a caller that keeps the parameters on the device (a training loop)
+ * needs no copy to the host.  ff supplies everything else.  PHAST_EINVAL for a
+ * NULL params or the arguments phast_energy_grad refuses. */
+int phast_energy_grad_params(const phast_system* sys, const phast_ff* ff, int32_t B, const double* xyz,
+                             int32_t pair_precision, const double* params, double* E_out,
+                             double* grad_xyz, double* grad_ff, void* stream);
+
 /* Canonical averages from multicanonical samples (Sec. 2.2 reweighting) and
  * their derivatives in a force-field parameter lambda.  Sample q (of n) has
  * energy E[q], D[q] = dE/dlambda (e.g. a column of grad_ff) and was drawn with

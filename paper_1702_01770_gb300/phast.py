@@ -30,7 +30,7 @@ SYMBOLS = ["phast_energy", "phast_delta_energy", "phast_ctx_create", "phast_ctx_
            "phast_version", "phast_ctx_capture_iteration", "phast_graph_launch",
            "phast_graph_destroy", "phast_energy_grad",
            "phast_reweight_sensitivity", "phast_maxwell", "phast_micro_binned_workspace_size",
-           "phast_micro_analysis_binned", "phast_ctx_set_hist_flush"]
+           "phast_micro_analysis_binned", "phast_ctx_set_hist_flush", "phast_energy_grad_params"]
 
 
 class PhastError(RuntimeError):
@@ -108,6 +108,7 @@ def lib():
                                                    vp]
         L.phast_maxwell.argtypes = [i32, dbl, dbl, vp, vp, i32, i32, i32, dbl, dbl, dbl, vp, vp, vp, vp]
         L.phast_energy_grad.argtypes = [P(_System), P(_FF), i32, vp, i32, vp, vp, vp, vp]
+        L.phast_energy_grad_params.argtypes = [P(_System), P(_FF), i32, vp, i32, vp, vp, vp, vp, vp]
         L.phast_reweight_sensitivity.argtypes = [i64, vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp]
         L.phast_ctx_capture_iteration.argtypes = [vp, i64, vp, i32, vp, vp, vp, P(vp), vp]
         L.phast_graph_launch.argtypes = [vp, vp]
@@ -206,17 +207,23 @@ def with_ff_params(system, params):
 
 
 def phast_energy_grad(system, xyz: torch.Tensor, pair_precision: int = 32, want_xyz: bool = True,
-                      want_ff: bool = True, stream=None):
+                      want_ff: bool = True, stream=None, params: torch.Tensor | None = None):
     """(E [B], dE/dxyz [B, N, 3] or None, dE/d(C_AA, C_BB, C_AB, kappa, kappa_C) [B, 5] or None),
-    FP64 on the device, of xyz [B, N, 3] FP64 on the device."""
+    FP64 on the device, of xyz [B, N, 3] FP64 on the device.  params: FP64 [5] on the device
+    (ff_params order) in place of the system's values (phast_energy_grad_params)."""
     st = _Structs([system])
     xyz = xyz.contiguous()
     B = xyz.shape[0] if xyz.numel() else 0
     E = torch.empty(B, dtype=torch.float64, device=xyz.device)
     gx = torch.empty_like(xyz) if want_xyz else None
     gf = torch.empty(B, 5, dtype=torch.float64, device=xyz.device) if want_ff else None
-    _check(lib().phast_energy_grad(st.sys, st.ff, B, _ptr(xyz), pair_precision, _ptr(E), _ptr(gx), _ptr(gf),
-                                   _stream(stream)))
+    if params is None:
+        _check(lib().phast_energy_grad(st.sys, st.ff, B, _ptr(xyz), pair_precision, _ptr(E), _ptr(gx), _ptr(gf),
+                                       _stream(stream)))
+    else:
+        assert params.dtype == torch.float64 and params.numel() == 5 and params.device == xyz.device
+        _check(lib().phast_energy_grad_params(st.sys, st.ff, B, _ptr(xyz), pair_precision, _ptr(params.contiguous()),
+                                              _ptr(E), _ptr(gx), _ptr(gf), _stream(stream)))
     return E, gx, gf
 
 
@@ -227,8 +234,10 @@ class EnergyFunction(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, xyz, params, system, pair_precision):
-        s = with_ff_params(system, params.detach().cpu().tolist())
-        E, _, _ = phast_energy_grad(s, xyz.detach().to(torch.float64), pair_precision, want_xyz=False, want_ff=False)
+        # the parameters stay where they are (no copy to the host, no synchronisation)
+        p = params.detach().to(device=xyz.device, dtype=torch.float64).contiguous()
+        E, _, _ = phast_energy_grad(system, xyz.detach().to(torch.float64), pair_precision, want_xyz=False,
+                                    want_ff=False, params=p)
         ctx.save_for_backward(xyz, params)
         ctx.system, ctx.pair_precision = system, pair_precision
         return E
@@ -236,8 +245,8 @@ class EnergyFunction(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gE):
         xyz, params = ctx.saved_tensors
-        s = with_ff_params(ctx.system, params.detach().cpu().tolist())
-        _, gx, gf = phast_energy_grad(s, xyz.detach().to(torch.float64), ctx.pair_precision)
+        p = params.detach().to(device=xyz.device, dtype=torch.float64).contiguous()
+        _, gx, gf = phast_energy_grad(ctx.system, xyz.detach().to(torch.float64), ctx.pair_precision, params=p)
         gE = gE.to(torch.float64)
         g_xyz = (gE.view(-1, 1, 1) * gx).to(xyz.dtype) if ctx.needs_input_grad[0] else None
         g_par = (gE.view(-1, 1) * gf).sum(0).to(params.device, params.dtype) if ctx.needs_input_grad[1] else None

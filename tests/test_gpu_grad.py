@@ -211,3 +211,20 @@ def test_muca_run_trimer_sensitivities(phast, orc):
     assert np.all(np.abs(est - ref) <= 5.0 * err + 1e-9), (est, ref, err)
     assert np.all(err < 0.1 * np.abs(ref) + 1e-6)         # the test has teeth
     ctx.close()
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("name,s,x", BATCHES[:3], ids=[b[0] for b in BATCHES[:3]])
+def test_device_parameters_equal_host_parameters(phast, name, s, x, precision):
+    """phast_energy_grad_params with the five parameters in device memory gives what
+    phast_energy_grad gives for a force field holding the same values."""
+    p = [1.3, 0.2, -0.7, -0.9, 0.4]                    # C_AA, C_BB, C_AB, kappa, kappa_C
+    xt = torch.from_numpy(x).cuda()
+    Ea, gxa, gfa = phast.phast_energy_grad(phast.with_ff_params(s, p), xt, precision)
+    Eb, gxb, gfb = phast.phast_energy_grad(s, xt, precision, params=torch.tensor(p, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    assert torch.equal(Ea, Eb) and torch.equal(gxa, gxb) and torch.equal(gfa, gfb)
+    with pytest.raises(phast.PhastError, match="NULL params"):
+        st = phast._Structs([s])
+        phast._check(phast.lib().phast_energy_grad_params(st.sys, st.ff, x.shape[0], xt.data_ptr(), precision, None,
+                                                          None, None, None, phast._stream(None)))
