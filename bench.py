@@ -186,7 +186,7 @@ def run_reference(args):
 # ----------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------
-SWEEP_SOURCES = ("common.cuh", "group.cuh", "sweep.cu")   # what the sweep kernel is compiled from
+SWEEP_SOURCES = ("common.cuh", "group.cuh", "lane.cuh", "sweep.cu")   # what the sweep kernels are compiled from
 
 
 def csrc_digest() -> str:
@@ -211,13 +211,15 @@ def traffic_per_launch(walkers: int):
     return j["dram_bytes_per_walker"] * walkers
 
 
-def measure_geometry(args, dev):
+def measure_geometry(args, dev, walkers=None):
     """The paper's own geometry: steric sphere, FENE bonds, bond-length and cap moves
-    (the batched kernel's build with them), two Fibonacci 13-mers, FP32 pair terms."""
+    (the builds with them), two Fibonacci 13-mers, FP32 pair terms, on the tile the
+    autotuner picks (one walker per thread or a group of lanes per walker)."""
     import torch
 
     from paper_1702_01770_gb300 import inputs, phast
-    gsys = inputs.fene_sphere(walkers=args.geom_walkers)
+    walkers = walkers or args.geom_walkers
+    gsys = inputs.fene_sphere(walkers=walkers)
     gctx = phast.Context(gsys, pair_precision=32)
     glnW = torch.zeros(gsys.n_bins, dtype=torch.float64, device=dev)
     if args.geom_tile:
@@ -236,17 +238,17 @@ def measure_geometry(args, dev):
     g1 = gctx.stats()
     gms = a.elapsed_time(b)
     gmoves = int(g1["attempts"].sum() - g0["attempts"].sum())
-    assert gmoves == args.geom_walkers * gsys.n_total * GEOM_SWEEPS
+    assert gmoves == walkers * gsys.n_total * GEOM_SWEEPS
     res = {
         "workload": "2 Fibonacci 13-mers in a steric sphere R = 8, FENE bonds (k_F = -20, R_F = 0.3), "
-                    f"all six move types, {args.geom_walkers} walkers, flat weights, {GEOM_SWEEPS} sweeps",
+                    f"all six move types, {walkers} walkers, flat weights, {GEOM_SWEEPS} sweeps",
         "kernel": ("sweep_lane_kernel<float,1> (one walker per thread)" if gtile[0] == 1
                    else f"sweep_batched_kernel<{gtile[0]},float,1>"), "tile": list(gtile),
         "walker_moves_per_s": gmoves / (gms / 1e3),
         "pair_evals_per_s": float((g1["pair_evals"].sum() - g0["pair_evals"].sum()) / (gms / 1e3)),
         "accept_rate": float((g1["accepts"].sum() - g0["accepts"].sum()) / gmoves), "dtype": "f32",
-        "l2": "walker state %.0f MB, L2-resident" % (args.geom_walkers * gsys.n_total * 24 / 1e6)}
-    if not args.no_cpu_baseline:
+        "l2": "walker state %.0f MB, L2-resident" % (walkers * gsys.n_total * 24 / 1e6)}
+    if not args.no_cpu_baseline and walkers == args.geom_walkers:
         v, pev, n, dt = oracle_walker_moves_per_s(inputs.fene_sphere(walkers=1), 4.0, os.cpu_count() or 1)
         res["cpu_baseline"] = {"value": v, "unit": "walker-moves/s", "cores": os.cpu_count() or 1,
                                "kind": "oracle", "sample": f"{n} walkers x 1 sweep, FP64 oracle, "
@@ -564,6 +566,8 @@ def run_ours(args):
 
     if not args.no_geom and rank == 0:
         out["geometry"] = measure_geometry(args, dev)
+        # one walker per thread fills the chip only with tens of thousands of walkers
+        out["geometry_65536"] = measure_geometry(args, dev, walkers=65536)
 
     if not args.no_uneven and rank == 0:
         out["uneven"] = measure_uneven(args, dev, peak_tf)
