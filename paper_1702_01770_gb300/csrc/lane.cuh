@@ -257,6 +257,9 @@ __device__ __forceinline__ double lane_pairs64(const SysDesc& d, const MoveSet& 
     return acc;
 }
 
+// Sweeps between re-centrings of the FP32 working copy on the chain centroids.
+constexpr int kLaneRebuildSweeps = 64;
+
 // One walker, one thread: n_sweeps sweeps of the multicanonical Metropolis
 // scheme (Sec. 2.2) -- the counterpart of run_walker for a group of one lane.
 template <typename PT, bool GEOM>
@@ -278,6 +281,7 @@ __device__ void run_walker_lane(const SysDesc& sd, const SweepArgs& a, int s_id,
     const bool tracing = a.trace && s_id == 0 && w_local < a.trace_walkers;
     const int64_t n_moves = a.n_sweeps * sd.N;
     const uint64_t period = (uint64_t)sd.recompute_every * (uint64_t)sd.N;
+    const uint64_t rebuild = (uint64_t)kLaneRebuildSweeps * (uint64_t)sd.N;
     lane_build<PT>(sd, x64, s);
     double lnw_here = __ldg(lnW + bin);
     float erel = (float)(E - sd.e_min);
@@ -420,6 +424,10 @@ __device__ void run_walker_lane(const SysDesc& sd, const SweepArgs& a, int s_id,
                 if (bf < 0) ++n_outside;
             }
             lane_build<PT>(sd, x64, s);   // origins re-centred, working copy rounded afresh
+        } else if (sizeof(PT) == 4 && (t % rebuild) == 0) {
+            // translations carry a chain away from its origin, and its FP32 coordinates
+            // lose digits: re-centre now and then even without an energy recompute
+            lane_build<PT>(sd, x64, s);
         }
     }
     a.E[gw] = E;

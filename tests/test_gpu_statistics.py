@@ -3,7 +3,8 @@ workload (four 9-mers in a periodic box, L = 20, torsion kappa = -0.5, the
 70/15/15 move mix; Sec. 2.2 Eq. 4-6, Sec. 4.1).
 
 The weights come from Berg iterations of the GPU in FP32.  With those weights
-fixed, the GPU (FP32 pair terms, 2048 walkers) and the oracle (FP64, 64 walkers
+fixed, the GPU (FP32 pair terms, 2048 walkers, with a group of lanes per walker or one
+walker per thread) and the oracle (FP64, 64 walkers
 on independent seeds) each run the same production phase from the workload's
 starting conformation (equilibration, then counting); each estimates S(E) =
 -lnW + ln H (Eq. 4), and the canonical specific heat c_V(T) with its peak, with
@@ -50,7 +51,8 @@ def _oracle_production(orc, s, lnW, walkers, seed0):
     return full, err, Hb.sum(0)
 
 
-def test_fp32_entropy_and_specific_heat_agree_with_the_oracle(orc):
+@pytest.mark.parametrize("tile", [None, (1, 64)])
+def test_fp32_entropy_and_specific_heat_agree_with_the_oracle(orc, tile):
     from paper_1702_01770_gb300 import phast
     s = inputs.config1(walkers=2048)
     K, w = s.n_bins, s.bin_width
@@ -65,6 +67,8 @@ def test_fp32_entropy_and_specific_heat_agree_with_the_oracle(orc):
     ctx.close()
     # production with the weights fixed, from the start, on fresh walker streams
     ctx = phast.Context(dataclasses.replace(s, seed_base=500_000), pair_precision=32)
+    if tile:   # one walker per thread
+        ctx.set_tile(*tile)
     ctx.sweep(EQ, lnW)
     hs.zero_()
     ctx.sweep(PROD, lnW, n_jk=N_BLOCKS, hist_sum=hs)
