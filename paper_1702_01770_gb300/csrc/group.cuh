@@ -107,14 +107,14 @@ __host__ __device__ inline SlotLayout slot_layout(int N, int nc, int mc) {
 
 // Per-warp shared-memory layout of the one-walker-per-thread sweep (bytes).
 struct LaneLayout {
-    int r_off, newr_off, w_off, org_off, bytes;
+    int r_off, w_off, org_off, bytes;
 };
 template <typename PT>
 __host__ __device__ inline LaneLayout lane_layout(int N, int nc, int mc) {
     LaneLayout L;
     int o = 0;
+    (void)mc;
     L.r_off = o;    o += 32 * (int)sizeof(P4<PT>) * N;
-    L.newr_off = o; o += 32 * (int)sizeof(P4<PT>) * mc;
     L.w_off = o;    o += 32 * 16 * nc;
     L.org_off = o;  o += 32 * 16 * nc;
     L.bytes = o;

@@ -19,8 +19,9 @@
 //   * walker arrays in shared memory are lane-interleaved (element e of lane l
 //     at e * 32 + l), so the lanes of a warp reach theirs without bank
 //     conflicts whatever indices they use; the FP64 master coordinates stay in
-//     global memory (L2-resident for these sizes), the trial FP64 positions in
-//     a per-walker global scratch.
+//     global memory (L2-resident for these sizes), the trial positions (FP64
+//     and their working-precision records) in a per-walker global scratch, so
+//     that shared memory holds only the working copy and more warps fit.
 #pragma once
 
 #include "group.cuh"
@@ -29,15 +30,15 @@
 template <typename PT>
 struct LaneSlot {
     P4<PT>* r;       // [N][32] working positions (FP32: relative to the chain origin; FP64: absolute)
-    P4<PT>* newr;    // [mc][32] trial positions of the moved monomers
+    P4<PT>* newr;    // [mc] trial positions of the moved monomers (the walker's global scratch)
     float4* w;       // [nc][32] shift of each chain's origin from chain 0's, wrapped into the box (FP32 mode)
     float4* org;     // [nc][32] chain origins (FP32 values, exact in FP64)
     int lane;
     __device__ __forceinline__ LaneSlot(unsigned char* warp_base, const LaneLayout& L, int lane_)
-        : r((P4<PT>*)(warp_base + L.r_off)), newr((P4<PT>*)(warp_base + L.newr_off)),
+        : r((P4<PT>*)(warp_base + L.r_off)), newr(nullptr),
           w((float4*)(warp_base + L.w_off)), org((float4*)(warp_base + L.org_off)), lane(lane_) {}
     __device__ __forceinline__ P4<PT>& R(int j) const { return r[j * 32 + lane]; }
-    __device__ __forceinline__ P4<PT>& NR(int q) const { return newr[q * 32 + lane]; }
+    __device__ __forceinline__ P4<PT>& NR(int q) const { return newr[q]; }
     __device__ __forceinline__ float4& W(int c) const { return w[c * 32 + lane]; }
     __device__ __forceinline__ float4& O(int c) const { return org[c * 32 + lane]; }
 };
@@ -263,11 +264,12 @@ constexpr int kLaneRebuildSweeps = 64;
 // One walker, one thread: n_sweeps sweeps of the multicanonical Metropolis
 // scheme (Sec. 2.2) -- the counterpart of run_walker for a group of one lane.
 template <typename PT, bool GEOM>
-__device__ void run_walker_lane(const SysDesc& sd, const SweepArgs& a, int s_id, int w_local, const LaneSlot<PT>& s,
+__device__ void run_walker_lane(const SysDesc& sd, const SweepArgs& a, int s_id, int w_local, LaneSlot<PT> s,
                                 uint32_t* hist, unsigned long long* hist_tile, unsigned long long* hist_g) {
     const int gw = sd.walker_off + w_local;
     double* x64 = a.xyz + sd.xyz_off + (int64_t)w_local * sd.N * 3;
-    double* new64 = a.scratch + (int64_t)gw * a.scratch_stride;   // the trial's exact positions
+    double* new64 = a.scratch + (int64_t)gw * a.scratch_stride;   // the trial's exact positions [mc][3]
+    s.newr = reinterpret_cast<P4<PT>*>(new64 + 4 * sd.max_chain);   // their records [mc] (16-byte aligned)
     const double* lnW = a.lnW + sd.lnw_off;
     double E = a.E[gw];
     int bin = a.bin[gw];

@@ -36,7 +36,8 @@ struct phast_ctx {
     uint64_t* seed;
     phast_walker_stats* stats;
     int32_t* tile_counter;
-    double* plain_scratch;   // [W][max_chain][3] new positions of the plain form
+    double* plain_scratch;   // [W][8 max_chain] trial positions: [max_chain][3] FP64 (plain and lane forms),
+                             // then [max_chain] working-precision records at 4 max_chain (lane form)
     int tpw, wpc;
     uint32_t hist_flush;     // count at which a shared histogram bin moves into hist_sum
     int order[PHAST_MAX_SYSTEMS];   // tile order: most expensive system types first
@@ -706,7 +707,7 @@ int fill_args(const phast_ctx* c, int64_t n_sweeps, const double* lnW, int n_jk,
     a->trace_walkers = trace_walkers;
     a->tile_counter = c->tile_counter;
     a->scratch = c->plain_scratch;
-    a->scratch_stride = 3 * c->max_chain;
+    a->scratch_stride = 8 * c->max_chain;   // keeps each walker's records 16-byte aligned
     a->hist_bins = c->max_bins;
     a->hist_flush = c->hist_flush;
     return PHAST_OK;
@@ -901,7 +902,7 @@ extern "C" int phast_ctx_create(phast_ctx** out, int32_t n_systems, const phast_
     if (e == cudaSuccess) e = cudaMalloc(&c->seed, sizeof(uint64_t) * W);
     if (e == cudaSuccess) e = cudaMalloc(&c->stats, bytes_stats);
     if (e == cudaSuccess) e = cudaMalloc(&c->tile_counter, sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&c->plain_scratch, sizeof(double) * 3 * (size_t)c->max_chain * W);
+    if (e == cudaSuccess) e = cudaMalloc(&c->plain_scratch, sizeof(double) * 8 * (size_t)c->max_chain * W);
     if (e != cudaSuccess) {
         phast_ctx_destroy(c);
         return phast_set_error(e == cudaErrorMemoryAllocation ? PHAST_ENOMEM : PHAST_ECUDA,
