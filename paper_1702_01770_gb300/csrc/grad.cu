@@ -92,8 +92,6 @@ __device__ V3<PT> torsion_grad(const Pos& pos, int o, int j, int which) {
 template <typename PT>
 __device__ __forceinline__ PT nearest_count(PT x, PT iL);
 template <>
-__device__ __forceinline__ float nearest_count<float>(float x, float iL) { return image_count(x, iL); }
-template <>
 __device__ __forceinline__ double nearest_count<double>(double x, double iL) { return rint(x * iL); }
 
 template <typename PT>
@@ -524,7 +522,6 @@ energy_grad32_chain_kernel(const SysDesc d, int B, const double* __restrict__ xy
         o.x = q.x; o.y = q.y; o.z = q.z; o.tag = __float_as_int(q.w);
         return o;
     };
-    const FF<float> f{d};
     DF E{0.0f, 0.0f}, gp[5] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     // local terms, each evaluated once with its gradient; terms whose monomers overlap
     // go in different passes (k mod 3 for bends, j mod 4 for dihedrals, l mod 2 for

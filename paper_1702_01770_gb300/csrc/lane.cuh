@@ -393,6 +393,8 @@ __device__ void run_walker_lane(const SysDesc& sd, const SweepArgs& a, int s_id,
         }
         if (hist_g) {
             atomicAdd(hist_g + bin, 1ull);
+        } else if (!a.hist_flush_on) {
+            atomicAdd(hist + bin, 1u);
         } else if (((atomicAdd(hist + bin, 1u) + 1u) & (a.hist_flush - 1u)) == 0u && hist_tile) {
             atomicSub(hist + bin, a.hist_flush);   // the flush of the 32-bit shared bin (see run_walker)
             atomicAdd(hist_tile + bin, (unsigned long long)a.hist_flush);

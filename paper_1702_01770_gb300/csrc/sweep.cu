@@ -74,6 +74,7 @@ struct SweepArgs {
     LaneLayout LL;                        // per-warp layout of the one-walker-per-thread form
     int hist_bins;                        // shared histogram capacity (max n_bins)
     uint32_t hist_flush;                  // a shared bin reaching this count moves it into hist_sum
+    int hist_flush_on;                    // a tile's counts can reach hist_flush in this launch
 };
 
 }  // namespace
@@ -147,12 +148,13 @@ __device__ __forceinline__ void recompute_energy(const SysDesc& sd, const double
 // keeps the per-move loop short in the instruction cache.
 template <int TPW, typename PT, bool GEOM>
 __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int w_local, Slot<PT>& slot,
-                           uint32_t* hist, unsigned long long* hist_tile, unsigned long long* hist_g,
+                           uint32_t* hist, unsigned long long* const* hist_tile, unsigned long long* hist_g,
                            const Group<TPW>& g) {
-    // hist: the tile's shared histogram, whose bins move into hist_tile (the global
-    // sums of the tile's jackknife block, or null) on reaching a.hist_flush; hist_g
-    // (non-null): this walker's jackknife block differs from the tile's, so its
-    // visits go straight to the global sums
+    // hist: the tile's shared histogram, whose bins move into *hist_tile (the global
+    // sums of the tile's jackknife block, or null; kept in shared memory, read only
+    // when a bin reaches a multiple of a.hist_flush); hist_g (non-null): this
+    // walker's jackknife block differs from the tile's, so its visits go straight to
+    // the global sums
     const int gw = sd.walker_off + w_local;
     double* x64 = a.xyz + sd.xyz_off + (int64_t)w_local * sd.N * 3;
     const double* lnW = a.lnW + sd.lnw_off;
@@ -223,13 +225,15 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
         if (g.lane == 0) {   // histogram and bookkeeping on one lane
             if (hist_g) {
                 atomicAdd(hist_g + bin, 1ull);
-            } else if (((atomicAdd(hist + bin, 1u) + 1u) & (a.hist_flush - 1u)) == 0u && hist_tile) {
+            } else if (!a.hist_flush_on) {   // the tile cannot count to the flush count in this launch
+                atomicAdd(hist + bin, 1u);
+            } else if (((atomicAdd(hist + bin, 1u) + 1u) & (a.hist_flush - 1u)) == 0u && *hist_tile) {
                 // this increment took the bin to a multiple of the flush count (a power
                 // of two): move that many into the 64-bit sums.  Each multiple is crossed
                 // by one increment, so the bin stays below the flush count plus the
                 // walkers of the tile.
                 atomicSub(hist + bin, a.hist_flush);
-                atomicAdd(hist_tile + bin, (unsigned long long)a.hist_flush);
+                atomicAdd(*hist_tile + bin, (unsigned long long)a.hist_flush);
             }
             if (hw) atomicAdd(hw + bin, 1u);
             ls->attempts[P.type]++;
@@ -295,6 +299,7 @@ __global__ void __launch_bounds__(kMaxTileThreads, MINB)
 sweep_batched_kernel(const SweepArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_tile;
+    __shared__ unsigned long long* s_hs_tile;   // the global sums of the tile's jackknife block
     SysDesc& sd = *reinterpret_cast<SysDesc*>(smem);
     uint32_t* hist = reinterpret_cast<uint32_t*>(smem + sizeof(SysDesc));
     unsigned char* slots = smem + sizeof(SysDesc) + align16(4 * a.hist_bins);
@@ -321,14 +326,16 @@ sweep_batched_kernel(const SweepArgs a) {
         const int w_local = w_a + slot_id;
         const int blk = jk_block(w_a, W, a.n_jk);
         __syncthreads();
-        unsigned long long* hs_tile = a.hist_sum ? a.hist_sum + a.hs_off[s_id] + (int64_t)blk * sd.n_bins : nullptr;
+        if (threadIdx.x == 0) s_hs_tile = a.hist_sum ? a.hist_sum + a.hs_off[s_id] + (int64_t)blk * sd.n_bins : nullptr;
+        __syncthreads();
         if (w_local < w_b) {
             const int mine = jk_block(w_local, W, a.n_jk);
             unsigned long long* hg =
                 (a.hist_sum && mine != blk) ? a.hist_sum + a.hs_off[s_id] + (int64_t)mine * sd.n_bins : nullptr;
-            run_walker<TPW, PT, GEOM>(sd, a, s_id, w_local, slot, hist, hs_tile, hg, g);
+            run_walker<TPW, PT, GEOM>(sd, a, s_id, w_local, slot, hist, &s_hs_tile, hg, g);
         }
         __syncthreads();
+        unsigned long long* hs_tile = s_hs_tile;
         if (hs_tile) {
             for (int k = threadIdx.x; k < sd.n_bins; k += blockDim.x)
                 if (hist[k]) atomicAdd(hs_tile + k, (unsigned long long)hist[k]);
@@ -710,6 +717,8 @@ int fill_args(const phast_ctx* c, int64_t n_sweeps, const double* lnW, int n_jk,
     a->scratch_stride = 8 * c->max_chain;   // keeps each walker's records 16-byte aligned
     a->hist_bins = c->max_bins;
     a->hist_flush = c->hist_flush;
+    // the walkers of a tile add at most wpc n_sweeps N counts to its shared histogram
+    a->hist_flush_on = (uint64_t)wpc * (uint64_t)n_sweeps * (uint64_t)c->max_N >= (uint64_t)c->hist_flush;
     return PHAST_OK;
 }
 
