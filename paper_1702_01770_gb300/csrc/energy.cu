@@ -72,8 +72,17 @@ delta_kernel(const SysDesc d, int B, const double* __restrict__ xyz, const phast
     const bool wall = ok && !container_ok<32, PT>(d, const_cast<double*>(x64), P, M, s, g, true, 0ull, 0ull, nullptr);
     if (wall) dE = INFINITY;   // beyond the container's wall
     if (ok && !wall) {
-        double part = (double)local_delta<32, PT>(d, P, M, s, g);
-        if constexpr (sizeof(PT) == 4) {
+        PT fene = (PT)0;
+        bool near = false;
+        double part = (double)local_delta<32, PT>(d, P, M, s, g, sizeof(PT) == 4 ? &fene : nullptr, &near);
+        if constexpr (sizeof(PT) == 4) {   // a FENE bond near its divergence: the exact positions give the change
+            if (__ballot_sync(g.mask, near)) {
+                const double dF = fene_delta_exact<32>(d, const_cast<double*>(x64), P, M, s, g, true, 0ull, 0ull,
+                                                       nullptr);
+                part += g.lane == 0 ? dF : 0.0;
+            } else {
+                part += (double)fene;
+            }
             const DF q = d.box_L > 0.0 ? pair_delta32<32, 3, true>(d, M, P.chain, s, g)
                                        : pair_delta32<32, 3, false>(d, M, P.chain, s, g);
             part += (double)q.hi + (double)q.lo;

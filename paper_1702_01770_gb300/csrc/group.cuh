@@ -63,6 +63,11 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     const float e = (a.hi - (s - bb)) + (b.hi - bb);
     return DF{s, e + (a.lo + b.lo)};
 }
+// An FP64 value as a double-float (hi its FP32 rounding, lo the rest).
+__device__ __forceinline__ DF df_of(double x) {
+    const float h = (float)x;
+    return DF{h, (float)(x - (double)h)};
+}
 // Tree sum of the group's DF values; every lane receives lane 0's total.
 template <int TPW>
 __device__ __forceinline__ DF group_sum_df(DF v, const Group<TPW>& g) {
@@ -627,9 +632,12 @@ __device__ __noinline__ bool container_ok(const SysDesc& d, double* x64, const P
             const int k = rec_slot(d, M, M.lo + q);
             const float4 A = mv[2 * k], B = mv[2 * k + 1];
             const float x = ox + A.y, y = oy + A.w, z = oz + B.y;
-            const float r2 = x * x + y * y + z * z;
-            out |= r2 > R2 + band;
-            unsure |= fabsf(r2 - R2) <= band;
+            // one difference decides both tests (exact for r2 near R2), so the two
+            // cover the line without a gap: a separately rounded R2 + band could
+            // leave r2 - R2 just above band counted neither out nor unsure
+            const float e = (x * x + y * y + z * z) - R2;
+            out |= e > band;
+            unsure |= fabsf(e) <= band;
         }
         if ((__ballot_sync(g.mask, unsure) >> g.base) & gm) {   // near the wall: the exact positions decide
             if (queued && *queued > 0) {
@@ -649,6 +657,45 @@ __device__ __noinline__ bool container_ok(const SysDesc& d, double* x64, const P
         }
     }
     return ((__ballot_sync(g.mask, out) >> g.base) & gm) == 0u;
+}
+
+// The FENE change of a move in FP64 on the exact positions, for FP32 mode
+// when one of its FENE terms lies in the band of fene_w (+inf for a bond
+// beyond its range, NaN for an exact geometry that is no move).  exact, seed,
+// t and queued as for container_ok: the queued moves are replayed first, so
+// that x64 holds the current coordinates.  The same value on every lane of the
+// group.  Out of line, as container_ok.
+template <int TPW>
+__device__ __noinline__ double fene_delta_exact(const SysDesc& d, double* x64, const Proposal& P, const MoveSet& M,
+                                                Slot<float>& s, const Group<TPW>& g, bool exact, uint64_t seed,
+                                                uint64_t t, int* queued) {
+    if (queued && *queued > 0) {
+        flush_queue<TPW, true>(d, x64, seed, s, g, *queued);
+        *queued = 0;
+    }
+    Proposal E = P;
+    if (!exact) {
+        propose_select(d, stream_block(seed, t, 0u), stream_block(seed, t, 1u), stream_block(seed, t, 2u), &E);
+        if (E.type == PHAST_PIVOT || E.type == PHAST_ROT || E.type == PHAST_CAP)
+            E.axis = exact_axis(seed, t, P.attempt);
+    }
+    const bool ok = prepare_exact<TPW, float>(d, x64, E, E.axis, s, g);
+    int vb0, nb, jt0, nt, fb0, nf;
+    local_window(d, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt, &fb0, &nf);
+    const int o = d.chain_off[P.chain];
+    double part = 0.0;
+    if (ok)
+        for (int k = g.lane; k < 2 * nf; k += TPW) {
+            const bool after = k & 1;
+            auto pos = [&](int j) -> double3 {
+                const double3 x = ld3(x64 + 3 * j);
+                return (after && j >= M.lo && j <= M.hi) ? exact_position(E, s.geo, x) : x;
+            };
+            const double v = fene_term(d, pos, o, fb0 + (k >> 1));
+            part += after ? v : -v;
+        }
+    const double dF = g.sum(part);
+    return ok ? dF : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 // Commit an accepted move in FP64 mode: the exact positions computed for the
@@ -819,10 +866,18 @@ __device__ __forceinline__ PT torsion_w(const Pos& pos, int o, int j) {
     return n12 * rsqrt_w(n11 * n22);
 }
 
+// Band of x^2 = ((r - r0) / R)^2 where an FP32 FENE term is not trusted: the
+// FP32 working copy carries ~1e-5 of error in x^2, against a divergence at
+// x^2 = 1 that FP64 resolves to ~1e-16, and each term's error grows as
+// 1 / (1 - x^2).  Inside the band the exact positions decide (and give the term).
+constexpr float kFeneExactLo = 0.99f, kFeneExactHi = 1.01f;
+
 // FENE term of bond l in the working precision:
 // k_fene R^2 C_F ln(1 - ((r - r0) / R)^2), +inf outside |r - r0| < R.
+// near (FP32 only): a term inside the band [kFeneExactLo, kFeneExactHi) of x^2
+// sets *near and counts 0, for the caller to replace by the exact FP64 term.
 template <typename PT, class Pos>
-__device__ __forceinline__ PT fene_w(const SysDesc& d, const Pos& pos, int o, int l) {
+__device__ __forceinline__ PT fene_w(const SysDesc& d, const Pos& pos, int o, int l, bool* near = nullptr) {
     const P4<PT> a = pos(o + l), b = pos(o + l + 1);
     const PT dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
     const PT r = sqrt(dx * dx + dy * dy + dz * dz);
@@ -832,6 +887,11 @@ __device__ __forceinline__ PT fene_w(const SysDesc& d, const Pos& pos, int o, in
     } else {
         const float x = (r - d.fene_r0_32) * d.fene_iR32;
         const float x2 = x * x;
+        if (near && x2 >= kFeneExactLo) {
+            if (!(x2 < kFeneExactHi)) return INFINITY;   // beyond the range by far more than the FP32 error
+            *near = true;
+            return 0.0f;
+        }
         if (!(x2 < 1.0f)) return INFINITY;
         return d.fene_kR2_32 * (d.C_F32[2 * d.seq[o + l] + d.seq[o + l + 1]] * log1pf(-x2));
     }
@@ -843,19 +903,22 @@ __device__ __forceinline__ PT lj_pair(PT dx, PT dy, PT dz, PT Lj, PT iLj, PT C);
 
 // A FENE bond term of monomers (l, l + 1) at positions a, b (fene), or minus
 // the Lennard-Jones term of that pair (the bonded pair of a bond move).
+// near: as for fene_w.
 template <typename PT>
-__device__ __noinline__ PT bond_item(const SysDesc& d, bool fene, P4<PT> a, P4<PT> b, int l) {
+__device__ __noinline__ PT bond_item(const SysDesc& d, bool fene, P4<PT> a, P4<PT> b, int l, bool* near = nullptr) {
     const FF<PT> f{d};
     if (fene) {
         auto pos2 = [&](int j) -> P4<PT> { return j == l ? a : b; };
-        return fene_w<PT>(d, pos2, l, 0);
+        return fene_w<PT>(d, pos2, l, 0, near);
     }
     return -f.kin() * lj_pair<PT>(a.x - b.x, a.y - b.y, a.z - b.z, (PT)0, (PT)0, f.C(2 * d.seq[l] + d.seq[l + 1]));
 }
 
+// fene (FP32): the FENE terms go to *fene rather than into the returned part,
+// and *near is set where one of them lies in the band of fene_w.
 template <int TPW, typename PT, bool GEOM = true>
 __device__ PT local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M, const Slot<PT>& s,
-                              const Group<TPW>& g) {
+                              const Group<TPW>& g, PT* fene = nullptr, bool* near = nullptr) {
     int vb0, nb, jt0, nt, fb0, nf;
     local_window(d, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt, &fb0, &nf);
     const int o = d.chain_off[P.chain];
@@ -885,9 +948,13 @@ __device__ PT local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M,
         if (k < nb) term = f.kbend() * bend_w<PT>(pos, o, vb0 + k);
         else if (k < nb + nt) term = -f.ktors() * torsion_w<PT>(pos, o, jt0 + (k - nb));
         else {   // a FENE bond or the bond move's pair: out of line (most workloads have neither)
-            const bool fene = k < nb + nt + nf;
-            const int l = o + (fene ? fb0 + (k - nb - nt) : P.index);   // the bond's first monomer
-            term = bond_item<PT>(d, fene, pos(l), pos(l + 1), l);
+            const bool is_fene = k < nb + nt + nf;
+            const int l = o + (is_fene ? fb0 + (k - nb - nt) : P.index);   // the bond's first monomer
+            term = bond_item<PT>(d, is_fene, pos(l), pos(l + 1), l, fene ? near : nullptr);
+            if (is_fene && fene) {
+                *fene += after ? term : -term;
+                continue;
+            }
         }
         part += after ? term : -term;
     }

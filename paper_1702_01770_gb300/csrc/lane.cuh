@@ -341,31 +341,38 @@ __device__ void run_walker_lane(const SysDesc& sd, const SweepArgs& a, int s_id,
             };
             int vb0, nb, jt0, nt, fb0, nf;
             local_window(sd, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt, &fb0, &nf);
-            if (!GEOM) nf = 0;
             const int nc1 = GEOM && P.type == PHAST_BOND;
             const FF<PT> f{sd};
             PT loc = (PT)0;
-            for (int k = 0; k < nb + nt + nf + nc1; ++k) {
+            for (int k = 0; k < nb + nt + nc1; ++k) {
 #pragma unroll
                 for (int after = 0; after < 2; ++after) {
                     auto p = [&](int j) -> P4<PT> { return pos(j, after); };
                     PT term;
                     if (k < nb) term = f.kbend() * bend_w<PT>(p, o, vb0 + k);
                     else if (k < nb + nt) term = -f.ktors() * torsion_w<PT>(p, o, jt0 + (k - nb));
-                    else {
-                        const bool fene = k < nb + nt + nf;
-                        const int l = o + (fene ? fb0 + (k - nb - nt) : P.index);
-                        term = bond_item<PT>(sd, fene, p(l), p(l + 1), l);
-                    }
+                    else term = bond_item<PT>(sd, false, p(o + P.index), p(o + P.index + 1), o + P.index);
                     loc += after ? term : -term;
                 }
             }
+            // FENE bonds in FP64 on the exact positions: FP32 records cannot resolve
+            // 1 - ((r - r0) / R)^2 near the divergence
+            double fene = 0.0;
+            if constexpr (GEOM)
+                for (int k = 0; k < nf; ++k) {
+                    auto before = [&](int j) -> double3 { return ld3(x64 + 3 * j); };
+                    auto after = [&](int j) -> double3 {
+                        return (j >= M.lo && j <= M.hi) ? ld3(new64 + 3 * (j - M.lo)) : ld3(x64 + 3 * j);
+                    };
+                    fene += fene_term(sd, after, o, fb0 + k) - fene_term(sd, before, o, fb0 + k);
+                }
             if constexpr (sizeof(PT) == 4) {
                 const float pr = sd.box_L > 0.0 ? lane_pairs32<true>(sd, M, P.chain, s)
                                                 : lane_pairs32<false>(sd, M, P.chain, s);
                 dE32 = df_add(DF{loc, 0.0f}, DF{pr, 0.0f});
+                if (GEOM && nf) dE32 = df_add(dE32, df_of(fene));
             } else {
-                dE64 = loc + lane_pairs64(sd, M, P.chain, s);
+                dE64 = loc + fene + lane_pairs64(sd, M, P.chain, s);
             }
         }
         const bool finite = eval && (sizeof(PT) == 4 ? (isfinite(dE32.hi) && isfinite(dE32.lo)) : isfinite(dE64));

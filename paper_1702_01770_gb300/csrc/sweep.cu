@@ -197,7 +197,18 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
             if (eval) {
                 part = sd.box_L > 0.0 ? pair_delta32<TPW, 3, true>(sd, M, P.chain, slot, g)
                                       : pair_delta32<TPW, 3, false>(sd, M, P.chain, slot, g);
-                part = df_add(part, DF{local_delta<TPW, PT, GEOM>(sd, P, M, slot, g), 0.0f});
+                float fene = 0.0f;
+                bool near = false;
+                part = df_add(part, DF{local_delta<TPW, PT, GEOM>(sd, P, M, slot, g, GEOM ? &fene : nullptr,
+                                                                  &near), 0.0f});
+                if constexpr (GEOM) {   // a FENE bond near its divergence: the exact positions give the change
+                    if (__ballot_sync(g.mask, near) & g.mask) {
+                        const double dF = fene_delta_exact<TPW>(sd, x64, P, M, slot, g, false, seed, t, &queued);
+                        if (g.lane == 0) part = df_add(part, df_of(dF));
+                    } else {
+                        part = df_add(part, DF{fene, 0.0f});
+                    }
+                }
             }
             dE32 = group_sum_df<TPW>(part, g);
         } else {

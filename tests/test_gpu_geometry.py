@@ -260,15 +260,9 @@ def test_tight_sphere_stays_inside(phast, orc, precision, tile):
         wk = orc.new_walker(m, mu, s.xyz0, int(seeds[w]))
         f = tr[w]["accepted"].astype(np.int8)
         _, stats, rec = orc.sweep_walker(m, mu, lnW, wk, n_sweeps * s.n_total, force=f, record=True)
-        inf_o, inf_g = np.isinf(rec["dE"]), np.isinf(tr[w]["dE"])
-        one = inf_o != inf_g
-        if precision == 64:
-            assert not np.any(one), w
-        else:   # an FP32 bond at the edge of its range: infinite on one side only, rejected by both
-            E_prev = np.concatenate([[orc.energy(m, s.xyz0)], rec["E_after"][:-1]])
-            fin = np.where(inf_o, tr[w]["dE"], rec["dE"])
-            assert np.all(E_prev[one] + fin[one] >= s.e_min + s.bin_width * s.n_bins), w
-            assert not np.any(tr[w]["accepted"][one]), w
+        # a bond at the edge of its FENE range, or a monomer at the wall, is decided on
+        # the exact positions in FP32 mode too: infinite on both sides or on neither
+        assert np.array_equal(np.isinf(rec["dE"]), np.isinf(tr[w]["dE"])), w
         assert np.array_equal(xyz[w], wk.xyz), w
     ctx.close()
 
@@ -297,3 +291,64 @@ def test_bond_move_edge_cases(phast, orc, precision):
     assert np.isfinite(dE[2]) and np.array_equal(xn[2], ref[2][1])
     assert abs(dE[2] - ref[2][0]) <= (1e-9 if precision == 64 else 1e-4) * max(1.0, abs(ref[2][0]))
     assert ref[3][0] == np.inf and dE[3] == np.inf
+
+
+@pytest.mark.parametrize("tile", [(16, 32), (1, 128)])
+def test_fene_divergence_is_decided_exactly(phast, tile):
+    # weights that favour high energies drive bonds to the edge of their FENE range,
+    # where an FP32 bond length cannot tell a finite term from the divergence: no
+    # accepted move may leave a state whose exact FP64 energy is infinite
+    s = inputs.fene_sphere(16384)
+    ctx = phast.Context(s, pair_precision=32)
+    ctx.set_tile(*tile)
+    k = np.arange(s.n_bins)
+    lnW = -0.02 * k + 0.5 * np.sin(k / 13.0)
+    ctx.sweep(400, torch.from_numpy(lnW).cuda())
+    st, stt = ctx.get_state("cpu"), ctx.stats()
+    torch.cuda.synchronize()
+    xyz = st["xyz"].numpy().reshape(s.walkers, s.n_total, 3)
+    E64 = phast.phast_energy(s, torch.from_numpy(xyz).cuda(), 64).cpu().numpy()
+    assert np.all(np.isfinite(E64)), int(np.sum(~np.isfinite(E64)))
+    drift = stt["drift_max"]
+    assert np.all(np.isfinite(drift)) and drift.max() < 0.05, drift.max()
+    # the last move of the run is followed by a recompute: the running energy is the FP64 one
+    assert np.allclose(st["E"].numpy(), E64, rtol=1e-12, atol=1e-9)
+    b = np.concatenate([np.linalg.norm(xyz[:, o + 1:o + 13] - xyz[:, o:o + 12], axis=2) for o in (0, 13)], axis=1)
+    x2 = ((b - s.fene_r0) / s.fene_R) ** 2
+    print(f"bonds with x^2 > 0.99: {int(np.sum(x2 > 0.99))}, largest x^2 {x2.max():.6f}")
+    assert x2.max() < 1.0 and np.sum(x2 > 0.95) > 0          # the bonds do reach the edge of their range
+    ctx.close()
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_wall_at_the_edge_of_the_fp32_band(phast, orc, precision):
+    # translations that leave a monomer a hair off the wall, around r^2 - R^2 =
+    # +-1e-5 R^2 where FP32 mode hands the decision to the exact positions (a few
+    # FP32 ulps of r^2 either side): the wall is infinite exactly where the
+    # oracle's FP64 test puts it
+    s = inputs.fene_sphere(1)
+    x = _states(orc, s, 1, 6)[0]
+    m = oracle_model(orc, s)
+    R2 = s.sphere_R ** 2
+    c = x[:13]
+    rng = np.random.Generator(np.random.Philox(12))
+    targets = R2 * np.concatenate([1e-5 + rng.uniform(-4e-7, 4e-7, 300), -1e-5 + rng.uniform(-4e-7, 4e-7, 100)])
+    mvs = []
+    for tg in targets:
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        lo, hi = 0.0, 20.0                      # max_k |c_k + d u|^2 - R^2 - tg changes sign in [lo, hi]
+        for _ in range(200):
+            d = 0.5 * (lo + hi)
+            f = np.max(np.sum((c + d * u) ** 2, axis=1)) - R2 - tg
+            lo, hi = (d, hi) if f < 0 else (lo, d)
+        mvs.append(orc.make_move(orc.TRANS, 0, 0, disp=tuple(hi * u)))
+    arr = np.zeros(len(mvs), phast.MOVE_DTYPE)
+    for i, mv in enumerate(mvs):
+        arr[i] = (mv.type, mv.chain, mv.index, 0, tuple(mv.axis), mv.angle, tuple(mv.disp))
+    xs = torch.from_numpy(np.broadcast_to(x, (len(mvs),) + x.shape).copy()).cuda()
+    dE = phast.phast_delta_energy(s, xs, arr, precision).cpu().numpy()
+    dEo = np.array([orc.delta_energy(m, x, mv)[0] for mv in mvs])
+    assert np.sum(np.isinf(dEo)) >= 250 and np.sum(np.isfinite(dEo)) >= 80
+    bad = np.nonzero(np.isinf(dE) != np.isinf(dEo))[0]
+    assert bad.size == 0, [(int(i), float(targets[i] / R2), float(dE[i]), float(dEo[i])) for i in bad[:5]]
