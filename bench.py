@@ -61,6 +61,7 @@ def parse():
                          "CUDA graph (always so with more than one rank: the histogram all-reduce sits between them)")
     ap.add_argument("--no-uneven", action="store_true")
     ap.add_argument("--uneven-only", action="store_true")
+    ap.add_argument("--no-small", action="store_true", help="skip the 13-mer and four-9-mer workloads")
     ap.add_argument("--dry-run-cpu", action="store_true",
                     help="rank plumbing only, on CPU over gloo: walker keys, one histogram exchange per step, "
                          "max-over-ranks time (no GPU, no sweep)")
@@ -125,7 +126,10 @@ class ClockSampler:
 # CPU oracle legs (the oracle is the reference arm and the CPU baseline)
 # ----------------------------------------------------------------------------
 def oracle_walker_moves_per_s(s, seconds: float, threads: int):
-    """Time the FP64 oracle on a bounded sample: `threads` threads, each walker one sweep."""
+    """Time the FP64 oracle on a bounded sample: `threads` threads, each walker k
+    sweeps (k = 1 unless one sweep is under 10 ms, so that small systems are not
+    timed on the thread pool's per-task overhead).  Returns walker-moves/s,
+    pair-evals/s, walkers, seconds and k."""
     from concurrent.futures import ThreadPoolExecutor
 
     import numpy as np
@@ -138,20 +142,26 @@ def oracle_walker_moves_per_s(s, seconds: float, threads: int):
     lnW = np.zeros(s.n_bins)
     N = s.n_total
 
-    def one(w):
+    def one(w, k=1):
         wk = oracle.new_walker(m, mu, s.xyz0, int(w))
-        _, st, _ = oracle.sweep_walker(m, mu, lnW, wk, N)
+        _, st, _ = oracle.sweep_walker(m, mu, lnW, wk, k * N)
         return st[oracle.ST_PAIR_EVALS]
 
+    one(0)                                            # first call: library and model set-up
     t0 = time.perf_counter()
     one(0)
     per = time.perf_counter() - t0                    # one walker-sweep on one core
-    n = max(1, int(seconds / per)) * threads          # about `seconds` of wall time on `threads` cores
+    k = max(1, int(0.01 / per))                       # sweeps per task
+    if k > 1:
+        t0 = time.perf_counter()
+        one(0, k)
+        per = (time.perf_counter() - t0) / k
+    n = max(1, int(seconds / (per * k))) * threads    # about `seconds` of wall time on `threads` cores
     t0 = time.perf_counter()
     with ThreadPoolExecutor(max_workers=threads) as ex:
-        pev = sum(ex.map(one, range(1, n + 1)))
+        pev = sum(ex.map(lambda w: one(w, k), range(1, n + 1)))
     dt = time.perf_counter() - t0
-    return n * N / dt, pev / dt, n, dt
+    return n * k * N / dt, pev / dt, n, dt, k
 
 
 def run_reference(args):
@@ -166,7 +176,7 @@ def run_reference(args):
         oracle_walker_moves_per_s(s, per_step, threads)
     vals, pes, tot = [], [], 0.0
     for _ in range(args.steps):
-        v, pe, n, dt = oracle_walker_moves_per_s(s, per_step, threads)
+        v, pe, n, dt, _ = oracle_walker_moves_per_s(s, per_step, threads)
         vals.append(v)
         pes.append(pe)
         tot += dt
@@ -249,12 +259,62 @@ def measure_geometry(args, dev, walkers=None):
         "accept_rate": float((g1["accepts"].sum() - g0["accepts"].sum()) / gmoves), "dtype": "f32",
         "l2": "walker state %.0f MB, L2-resident" % (walkers * gsys.n_total * 24 / 1e6)}
     if not args.no_cpu_baseline and walkers == args.geom_walkers:
-        v, pev, n, dt = oracle_walker_moves_per_s(inputs.fene_sphere(walkers=1), 4.0, os.cpu_count() or 1)
+        v, pev, n, dt, k = oracle_walker_moves_per_s(inputs.fene_sphere(walkers=1), 4.0, os.cpu_count() or 1)
         res["cpu_baseline"] = {"value": v, "unit": "walker-moves/s", "cores": os.cpu_count() or 1,
-                               "kind": "oracle", "sample": f"{n} walkers x 1 sweep, FP64 oracle, "
+                               "kind": "oracle", "sample": f"{n} walkers x {k} sweeps, FP64 oracle, "
                                                            f"{dt:.1f} s", "pair_evals_per_s": pev}
     gctx.close()
     return res
+
+
+SMALL_SWEEPS = {"fib13": 10000, "4x9": 2000}   # sweeps timed per small workload
+
+
+def measure_small(args, dev, peak_tf):
+    """The two small workloads of the measurement table, each on its autotuned tile:
+    the Fibonacci 13-mer (8 walkers, pivot moves, FP64 pairs, one Berg iteration's
+    10^4 sweeps) and four 9-mers in L = 20 (256 walkers, FP32 pairs, FP64 recompute
+    every 100 sweeps, 2000 of the workload's 10^5 sweeps), with the FP64 oracle
+    beside each on a bounded sample of the same system."""
+    import torch
+
+    from paper_1702_01770_gb300 import inputs, phast
+    out = {}
+    for s, prec, label in ((inputs.config0(), 64, "Fibonacci 13-mer ABBABBABABBAB, 8 walkers, pivot only, "
+                                                  "720 bins of 0.05, FP64 pairs"),
+                           (inputs.config1(), 32, "four 9-mers (seed-1 sequences), L = 20, 256 walkers, "
+                                                  "70/15/15 pivot/translation/rotation, FP32 pairs, FP64 totals")):
+        n_sw = SMALL_SWEEPS[s.name]
+        ctx = phast.Context(s, pair_precision=prec)
+        lnW = ctx.lnW_zeros()
+        tile = ctx.autotune(lnW, sweeps=10)
+        ctx.sweep(20, lnW)
+        torch.cuda.synchronize()
+        s0 = ctx.stats()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.sweep(n_sw, lnW)
+        b.record()
+        torch.cuda.synchronize()
+        s1 = ctx.stats()
+        ms = a.elapsed_time(b)
+        mv = int(s1["attempts"].sum() - s0["attempts"].sum())
+        assert mv == s.walkers * s.n_total * n_sw
+        pe = int(s1["pair_evals"].sum() - s0["pair_evals"].sum())
+        pex = int(s1["pair_evals_inter"].sum() - s0["pair_evals_inter"].sum())
+        r = {"workload": label, "sweeps": n_sw, "tile": list(tile), "ms": ms,
+             "walker_moves_per_s": mv / (ms / 1e3), "pair_evals_per_s": pe / (ms / 1e3),
+             "dtype": "f64" if prec == 64 else "f32"}
+        if prec == 32:
+            r["fp32_frac"] = _flops(pe, pex) / (ms / 1e3) / 1e12 / peak_tf
+        ctx.close()
+        if not args.no_cpu_baseline:
+            v, pev, n, dt, k = oracle_walker_moves_per_s(s, 2.0, os.cpu_count() or 1)
+            r["cpu_baseline"] = {"value": v, "unit": "walker-moves/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+                                 "sample": f"{n} walkers x {k} sweeps, FP64 oracle, {dt:.1f} s",
+                                 "pair_evals_per_s": pev}
+        out[s.name] = r
+    return out
 
 
 UNEVEN_CHUNK = 1000        # sweeps per captured iteration of the four-type workload
@@ -572,6 +632,9 @@ def run_ours(args):
     if not args.no_uneven and rank == 0:
         out["uneven"] = measure_uneven(args, dev, peak_tf)
 
+    if not args.no_small and rank == 0:
+        out["small"] = measure_small(args, dev, peak_tf)
+
     # end to end through the C ABI with host buffers: state in from pinned host memory, results out
     if not args.no_e2e:
         st = ctx.get_state("cpu")
@@ -602,7 +665,8 @@ def run_ours(args):
                       "d2h_bytes_per_step": d2h}
 
     if rank == 0 and not args.no_cpu_baseline:
-        v, pev, n, dt = oracle_walker_moves_per_s(inputs.config4(walkers=1), args.cpu_seconds, os.cpu_count() or 1)
+        v, pev, n, dt, _ = oracle_walker_moves_per_s(inputs.config4(walkers=1), args.cpu_seconds,
+                                                     os.cpu_count() or 1)
         out["cpu_baseline"] = {"value": v, "unit": "walker-moves/s", "cores": os.cpu_count() or 1, "kind": "oracle",
                                "sample": f"{n} walkers x 1 sweep (440 moves) of the 8x55-mer workload, lnW = 0, "
                                          f"FP64 oracle, {dt:.1f} s", "pair_evals_per_s": pev}
