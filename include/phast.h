@@ -190,12 +190,15 @@ int phast_ctx_get_state(const phast_ctx* ctx, double* xyz, double* E, int32_t* b
 int phast_ctx_set_state(phast_ctx* ctx, const double* xyz, const double* E, const int32_t* bin,
                         const uint64_t* t, const phast_walker_stats* stats, void* stream);
 
-/* Tile shape of the batched sweep: threads per walker (4, 8, 16 or 32) and
- * walkers per CTA; 0 picks the default.  phast_ctx_autotune runs each
- * candidate on a scratch copy of the state for `sweeps` sweeps, once untimed
- * and once timed, and keeps the fastest.  Systems of fewer than 48 monomers run
- * 16-lane FP32 tiles in a build held to 64 registers when that fits more CTAs
- * on an SM. */
+/* Tile shape of the batched sweep: threads per walker (1, 4, 8, 16 or 32) and
+ * walkers per CTA (a whole number of warps: threads per walker x walkers per
+ * CTA a multiple of 32, at most 512, or 256 with one walker per thread); 0
+ * picks the default.  One thread per walker runs each walker's whole move on
+ * its own thread (small systems); a group of lanes shares a walker's pair
+ * loop.  phast_ctx_autotune runs each candidate on a scratch copy of the state
+ * for `sweeps` sweeps, once untimed and once timed, and keeps the fastest.
+ * Systems of fewer than 48 monomers run 16-lane FP32 tiles in a build held to
+ * 64 registers when that fits more CTAs on an SM. */
 int phast_ctx_set_tile(phast_ctx* ctx, int32_t threads_per_walker, int32_t walkers_per_cta);
 int phast_ctx_get_tile(const phast_ctx* ctx, int32_t* threads_per_walker, int32_t* walkers_per_cta);
 int phast_ctx_autotune(phast_ctx* ctx, const double* lnW, int32_t sweeps, void* stream);
