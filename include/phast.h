@@ -148,15 +148,21 @@ typedef struct phast_ctx phast_ctx;
 /* ---- energy (Sec. 2.1, Eq. 2 and Eq. 3) --------------------------------- */
 
 /* Total energy of B configurations of one system.  xyz: dev [B][N][3] FP64;
- * pair_precision 32 or 64 selects the arithmetic of the Lennard-Jones pairs and
- * of the bending/torsion terms (FP32 positions are taken relative to their
- * chain's FP64 centroid); sums are FP64.  E_out: dev [B].  B = 0 is a no-op. */
+ * pair_precision 32 or 64 selects the arithmetic of the Lennard-Jones pairs
+ * (FP32 positions are taken relative to their chain's FP64 centroid); the
+ * bending, torsion and FENE terms and all sums are FP64 (a dihedral of
+ * collinear bonds is 0, a decision FP32 coordinates cannot take).  E_out: dev
+ * [B].  B = 0 is a no-op. */
 int phast_energy(const phast_system* sys, const phast_ff* ff, int32_t B, const double* xyz,
                  int32_t pair_precision, double* E_out, void* stream);
 
 /* Energy change of move b applied to configuration b (Sec. 3.2 move set):
  * bending/torsion terms that the move changes plus every Lennard-Jones pair
- * (moved, unmoved) before and after.  moves: dev [B]; dE_out: dev [B];
+ * (moved, unmoved) before and after.  With pair_precision 32 the local terms
+ * are FP32 too, except that a dihedral with bonds within ~0.06 degrees of
+ * collinear (where FP32 cannot resolve its normal, and the FP64 term of
+ * collinear bonds is 0) or a FENE bond near its range makes that kind of term's
+ * change FP64 on the exact positions.  moves: dev [B]; dE_out: dev [B];
  * xyz_new_out: dev [B][N][3] or NULL (receives the moved configurations).
  * A degenerate crankshaft (coincident neighbours) gives NaN. */
 int phast_delta_energy(const phast_system* sys, const phast_ff* ff, int32_t B, const double* xyz,

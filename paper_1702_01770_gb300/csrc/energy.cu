@@ -23,7 +23,7 @@ energy_kernel(const SysDesc d, int B, const double* __restrict__ xyz, double* __
     } else {
         Slot<PT> s(smem + (size_t)w * L.bytes, L);
         build_working<32, PT>(d, x64, s, g);
-        E = full_energy_working<32, PT>(d, s, g);
+        E = full_energy_working<32, PT>(d, x64, s, g);
         bool out = false;   // a monomer beyond the container's wall: infinite energy
         for (int j = g.lane; j < d.N; j += 32) out |= !inside64(d, ld3(x64 + 3 * j));
         if (__any_sync(g.mask, out)) E = INFINITY;
@@ -72,17 +72,21 @@ delta_kernel(const SysDesc d, int B, const double* __restrict__ xyz, const phast
     const bool wall = ok && !container_ok<32, PT>(d, const_cast<double*>(x64), P, M, s, g, true, 0ull, 0ull, nullptr);
     if (wall) dE = INFINITY;   // beyond the container's wall
     if (ok && !wall) {
-        PT fene = (PT)0;
-        bool near = false;
-        double part = (double)local_delta<32, PT>(d, P, M, s, g, sizeof(PT) == 4 ? &fene : nullptr, &near);
-        if constexpr (sizeof(PT) == 4) {   // a FENE bond near its divergence: the exact positions give the change
-            if (__ballot_sync(g.mask, near)) {
-                const double dF = fene_delta_exact<32>(d, const_cast<double*>(x64), P, M, s, g, true, 0ull, 0ull,
-                                                       nullptr);
-                part += g.lane == 0 ? dF : 0.0;
-            } else {
-                part += (double)fene;
+        PT fene = (PT)0, tors = (PT)0;
+        bool near = false, tnear = false;
+        double part = (double)local_delta<32, PT>(d, P, M, s, g, sizeof(PT) == 4 ? &fene : nullptr, &near,
+                                                  sizeof(PT) == 4 ? &tors : nullptr, &tnear);
+        if constexpr (sizeof(PT) == 4) {
+            // a FENE bond near its divergence or a dihedral near degenerate: the exact
+            // positions give that kind of term's change
+            const bool fx = __ballot_sync(g.mask, near), tx = __ballot_sync(g.mask, tnear);
+            if (fx || tx) {
+                const double dX = local_delta_exact<32, true>(d, const_cast<double*>(x64), P, M, s, g, true, 0ull,
+                                                              0ull, nullptr, fx, tx);
+                part += g.lane == 0 ? dX : 0.0;
             }
+            if (!fx) part += (double)fene;
+            if (!tx) part += (double)tors;
             const DF q = d.box_L > 0.0 ? pair_delta32<32, 3, true>(d, M, P.chain, s, g)
                                        : pair_delta32<32, 3, false>(d, M, P.chain, s, g);
             part += (double)q.hi + (double)q.lo;

@@ -659,18 +659,20 @@ __device__ __noinline__ bool container_ok(const SysDesc& d, double* x64, const P
     return ((__ballot_sync(g.mask, out) >> g.base) & gm) == 0u;
 }
 
-// The FENE change of a move in FP64 on the exact positions, for FP32 mode
-// when one of its FENE terms lies in the band of fene_w (+inf for a bond
-// beyond its range, NaN for an exact geometry that is no move).  exact, seed,
-// t and queued as for container_ok: the queued moves are replayed first, so
-// that x64 holds the current coordinates.  The same value on every lane of the
-// group.  Out of line, as container_ok.
-template <int TPW>
-__device__ __noinline__ double fene_delta_exact(const SysDesc& d, double* x64, const Proposal& P, const MoveSet& M,
-                                                Slot<float>& s, const Group<TPW>& g, bool exact, uint64_t seed,
-                                                uint64_t t, int* queued) {
+// Local terms of a move in FP64 on the exact positions, for FP32 mode: the
+// FENE change (fene; when one of its terms lies in the band of fene_w) and the
+// torsion change of the move's window (tors; when a dihedral lies in the band of
+// torsion_w), summed (+inf for a bond beyond its range, NaN for an exact
+// geometry that is no move).  exact, seed, t and queued as for container_ok:
+// the queued moves are replayed first, so that x64 holds the current
+// coordinates.  The same value on every lane of the group.  Out of line, as
+// container_ok.
+template <int TPW, bool GEOM>
+__device__ __noinline__ double local_delta_exact(const SysDesc& d, double* x64, const Proposal& P, const MoveSet& M,
+                                                 Slot<float>& s, const Group<TPW>& g, bool exact, uint64_t seed,
+                                                 uint64_t t, int* queued, bool fene, bool tors) {
     if (queued && *queued > 0) {
-        flush_queue<TPW, true>(d, x64, seed, s, g, *queued);
+        flush_queue<TPW, GEOM>(d, x64, seed, s, g, *queued);
         *queued = 0;
     }
     Proposal E = P;
@@ -683,19 +685,21 @@ __device__ __noinline__ double fene_delta_exact(const SysDesc& d, double* x64, c
     int vb0, nb, jt0, nt, fb0, nf;
     local_window(d, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt, &fb0, &nf);
     const int o = d.chain_off[P.chain];
+    const int nF = fene ? 2 * nf : 0, nT = tors ? 2 * nt : 0;
     double part = 0.0;
     if (ok)
-        for (int k = g.lane; k < 2 * nf; k += TPW) {
+        for (int k = g.lane; k < nF + nT; k += TPW) {
             const bool after = k & 1;
             auto pos = [&](int j) -> double3 {
                 const double3 x = ld3(x64 + 3 * j);
                 return (after && j >= M.lo && j <= M.hi) ? exact_position(E, s.geo, x) : x;
             };
-            const double v = fene_term(d, pos, o, fb0 + (k >> 1));
+            const double v = k < nF ? fene_term(d, pos, o, fb0 + (k >> 1))
+                                    : -d.k_tors * torsion_term(pos, o, jt0 + ((k - nF) >> 1));
             part += after ? v : -v;
         }
-    const double dF = g.sum(part);
-    return ok ? dF : __longlong_as_double(0x7ff8000000000000ll);
+    const double dX = g.sum(part);
+    return ok ? dX : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 // Commit an accepted move in FP64 mode: the exact positions computed for the
@@ -851,8 +855,33 @@ __device__ __forceinline__ PT bend_w(const Pos& pos, int o, int k) {
     return (PT)1 - ab * rsqrt_w(aa * bb);
 }
 
+// An FP32 dihedral whose normals FP32 cannot resolve.  The FP64 term is 0 for a
+// degenerate dihedral (n1^2 n2^2 < 1e-20, so one normal has n^2 < 1e-10: collinear
+// bonds, as in a chain that started straight and keeps straight stretches under
+// pivot moves), but FP32 coordinates carry rounding of half an ulp of their
+// magnitude (a few ulp for the FP32 trial positions of a rotation), which leaves
+// the normal of a collinear pair of unit bonds with a length of a few to some
+// tens of ulp and a meaningless direction, and an FP32 cos tau of a normal n
+// carries an error of about that noise over |n|.  wide (the builds with an exact
+// FP64 path): a normal with n^2 < 1e-6 (bonds within ~0.06 degrees of collinear)
+// marks the term; narrow (the build without it, where a marked term counts as
+// degenerate): n^2 below max((32 ulp)^2, 1e-10), the ulp that of the largest
+// coordinate of the four monomers.  A dihedral that is that close to degenerate
+// without being degenerate (a bend under ~6e-5 rad for a 55-mer) has a
+// probability of order 1e-9 under continuous moves of a chain that did not start
+// straight; the host runs contexts whose chains start straight in a build with
+// the exact path.
+__device__ __forceinline__ bool torsion_unresolved32(float n11, float n22, float mx, bool wide) {
+    const float u = __int_as_float(((__float_as_int(fmaxf(mx, 1.0f)) >> 23) - 23) << 23);   // ulp of mx
+    const float tau = fmaxf(1024.0f * u * u, wide ? 1e-6f : 1e-10f);
+    return fminf(n11, n22) < tau;
+}
+
+// cos tau_j in the working precision.  near (FP32 only): a dihedral FP32 cannot
+// resolve (torsion_unresolved32) sets *near and counts 0, for the caller to
+// replace by the exact FP64 term or to take as degenerate.
 template <typename PT, class Pos>
-__device__ __forceinline__ PT torsion_w(const Pos& pos, int o, int j) {
+__device__ __forceinline__ PT torsion_w(const Pos& pos, int o, int j, bool* near = nullptr, bool wide = true) {
     const P4<PT> x0 = pos(o + j), x1 = pos(o + j + 1), x2 = pos(o + j + 2), x3 = pos(o + j + 3);
     const PT b0x = x1.x - x0.x, b0y = x1.y - x0.y, b0z = x1.z - x0.z;
     const PT b1x = x2.x - x1.x, b1y = x2.y - x1.y, b1z = x2.z - x1.z;
@@ -861,6 +890,18 @@ __device__ __forceinline__ PT torsion_w(const Pos& pos, int o, int j) {
     const PT n2x = b1y * b2z - b1z * b2y, n2y = b1z * b2x - b1x * b2z, n2z = b1x * b2y - b1y * b2x;
     const PT n12 = n1x * n2x + n1y * n2y + n1z * n2z;
     const PT n11 = n1x * n1x + n1y * n1y + n1z * n1z, n22 = n2x * n2x + n2y * n2y + n2z * n2z;
+    if constexpr (sizeof(PT) == 4) {
+        if (near) {
+            float mx = fmaxf(fmaxf(fabsf(x0.x), fabsf(x0.y)), fabsf(x0.z));
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x1.x), fabsf(x1.y)), fabsf(x1.z)));
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x2.x), fabsf(x2.y)), fabsf(x2.z)));
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x3.x), fabsf(x3.y)), fabsf(x3.z)));
+            if (torsion_unresolved32(n11, n22, mx, wide)) {
+                *near = true;
+                return (PT)0;
+            }
+        }
+    }
     if (n11 * n22 < (PT)1e-20) return (PT)0;
     if (sizeof(PT) == 8) return n12 / (sqrt(n11) * sqrt(n22));
     return n12 * rsqrt_w(n11 * n22);
@@ -915,10 +956,13 @@ __device__ __noinline__ PT bond_item(const SysDesc& d, bool fene, P4<PT> a, P4<P
 }
 
 // fene (FP32): the FENE terms go to *fene rather than into the returned part,
-// and *near is set where one of them lies in the band of fene_w.
+// and *near is set where one of them lies in the band of fene_w.  tors (FP32):
+// likewise the torsion terms go to *tors, and *tnear is set where a dihedral
+// lies in the band of torsion_w.
 template <int TPW, typename PT, bool GEOM = true>
 __device__ PT local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M, const Slot<PT>& s,
-                              const Group<TPW>& g, PT* fene = nullptr, bool* near = nullptr) {
+                              const Group<TPW>& g, PT* fene = nullptr, bool* near = nullptr, PT* tors = nullptr,
+                              bool* tnear = nullptr) {
     int vb0, nb, jt0, nt, fb0, nf;
     local_window(d, P.type, P.chain, P.index, &vb0, &nb, &jt0, &nt, &fb0, &nf);
     const int o = d.chain_off[P.chain];
@@ -946,8 +990,14 @@ __device__ PT local_delta(const SysDesc& d, const Proposal& P, const MoveSet& M,
         const FF<PT> f{d};
         PT term;
         if (k < nb) term = f.kbend() * bend_w<PT>(pos, o, vb0 + k);
-        else if (k < nb + nt) term = -f.ktors() * torsion_w<PT>(pos, o, jt0 + (k - nb));
-        else {   // a FENE bond or the bond move's pair: out of line (most workloads have neither)
+        else if (k < nb + nt) {
+            if (sizeof(PT) == 4 && tors) {
+                const PT v = -f.ktors() * torsion_w<PT>(pos, o, jt0 + (k - nb), tnear, GEOM);
+                *tors += after ? v : -v;
+                continue;
+            }
+            term = -f.ktors() * torsion_w<PT>(pos, o, jt0 + (k - nb));
+        } else {   // a FENE bond or the bond move's pair: out of line (most workloads have neither)
             const bool is_fene = k < nb + nt + nf;
             const int l = o + (is_fene ? fb0 + (k - nb - nt) : P.index);   // the bond's first monomer
             term = bond_item<PT>(d, is_fene, pos(l), pos(l + 1), l, fene ? near : nullptr);
@@ -1256,15 +1306,15 @@ __device__ double full_energy64(const SysDesc& d, const double* x64, const Group
 // Full energy with the Lennard-Jones pairs in the working precision (from the
 // working copy) and the local terms in FP64 (from x64).
 template <int TPW, typename PT>
-__device__ double full_energy_working(const SysDesc& d, const Slot<PT>& s, const Group<TPW>& g) {
+__device__ double full_energy_working(const SysDesc& d, const double* x64, const Slot<PT>& s, const Group<TPW>& g) {
     double part = 0.0;
-    auto pos = [&](int j) -> P4<PT> { return s.r[j]; };
+    auto pos = [&](int j) -> double3 { return ld3(x64 + 3 * j); };
     for (int c = 0; c < d.n_chains; ++c) {
         int o = d.chain_off[c], n = d.chain_off[c + 1] - o;
-        for (int k = 1 + g.lane; k <= n - 2; k += TPW) part += (double)((PT)d.k_bend * bend_w<PT>(pos, o, k));
-        for (int j = g.lane; j <= n - 4; j += TPW) part -= (double)((PT)d.k_tors * torsion_w<PT>(pos, o, j));
+        for (int k = 1 + g.lane; k <= n - 2; k += TPW) part += d.k_bend * bend_term(pos, o, k);
+        for (int j = g.lane; j <= n - 4; j += TPW) part -= d.k_tors * torsion_term(pos, o, j);
         if (d.k_fene != 0.0)
-            for (int l = g.lane; l <= n - 2; l += TPW) part += (double)fene_w<PT>(d, pos, o, l);
+            for (int l = g.lane; l <= n - 2; l += TPW) part += fene_term(d, pos, o, l);
     }
     const PT L = (PT)d.box_L, iL = (PT)d.inv_L;
     for (int i = 0; i < d.N; ++i) {

@@ -344,20 +344,33 @@ __device__ void run_walker_lane(const SysDesc& sd, const SweepArgs& a, int s_id,
             const int nc1 = GEOM && P.type == PHAST_BOND;
             const FF<PT> f{sd};
             PT loc = (PT)0;
+            double fene = 0.0;   // the terms taken in FP64 on the exact positions
             for (int k = 0; k < nb + nt + nc1; ++k) {
 #pragma unroll
                 for (int after = 0; after < 2; ++after) {
                     auto p = [&](int j) -> P4<PT> { return pos(j, after); };
                     PT term;
-                    if (k < nb) term = f.kbend() * bend_w<PT>(p, o, vb0 + k);
-                    else if (k < nb + nt) term = -f.ktors() * torsion_w<PT>(p, o, jt0 + (k - nb));
-                    else term = bond_item<PT>(sd, false, p(o + P.index), p(o + P.index + 1), o + P.index);
+                    if (k < nb) {
+                        term = f.kbend() * bend_w<PT>(p, o, vb0 + k);
+                    } else if (k < nb + nt) {
+                        bool nr = false;   // FP32: a dihedral near degenerate is taken in FP64
+                        term = -f.ktors() * torsion_w<PT>(p, o, jt0 + (k - nb), sizeof(PT) == 4 ? &nr : nullptr);
+                        if (nr) {
+                            auto ex = [&](int j) -> double3 {
+                                return (after && j >= M.lo && j <= M.hi) ? ld3(new64 + 3 * (j - M.lo))
+                                                                         : ld3(x64 + 3 * j);
+                            };
+                            const double v = -sd.k_tors * torsion_term(ex, o, jt0 + (k - nb));
+                            fene += after ? v : -v;
+                        }
+                    } else {
+                        term = bond_item<PT>(sd, false, p(o + P.index), p(o + P.index + 1), o + P.index);
+                    }
                     loc += after ? term : -term;
                 }
             }
             // FENE bonds in FP64 on the exact positions: FP32 records cannot resolve
             // 1 - ((r - r0) / R)^2 near the divergence
-            double fene = 0.0;
             if constexpr (GEOM)
                 for (int k = 0; k < nf; ++k) {
                     auto before = [&](int j) -> double3 { return ld3(x64 + 3 * j); };
@@ -370,7 +383,7 @@ __device__ void run_walker_lane(const SysDesc& sd, const SweepArgs& a, int s_id,
                 const float pr = sd.box_L > 0.0 ? lane_pairs32<true>(sd, M, P.chain, s)
                                                 : lane_pairs32<false>(sd, M, P.chain, s);
                 dE32 = df_add(DF{loc, 0.0f}, DF{pr, 0.0f});
-                if (GEOM && nf) dE32 = df_add(dE32, df_of(fene));
+                if (fene != 0.0) dE32 = df_add(dE32, df_of(fene));
             } else {
                 dE64 = loc + fene + lane_pairs64(sd, M, P.chain, s);
             }

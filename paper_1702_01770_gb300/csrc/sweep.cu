@@ -41,6 +41,7 @@ struct phast_ctx {
     int tpw, wpc;
     uint32_t hist_flush;     // count at which a shared histogram bin moves into hist_sum
     int order[PHAST_MAX_SYSTEMS];   // tile order: most expensive system types first
+    bool near_straight;      // a type with torsion starts with a dihedral FP32 cannot resolve
 };
 
 namespace {
@@ -197,17 +198,29 @@ __device__ void run_walker(const SysDesc& sd, const SweepArgs& a, int s_id, int 
             if (eval) {
                 part = sd.box_L > 0.0 ? pair_delta32<TPW, 3, true>(sd, M, P.chain, slot, g)
                                       : pair_delta32<TPW, 3, false>(sd, M, P.chain, slot, g);
-                float fene = 0.0f;
-                bool near = false;
+                float fene = 0.0f, tors = 0.0f;
+                bool near = false, tnear = false;
                 part = df_add(part, DF{local_delta<TPW, PT, GEOM>(sd, P, M, slot, g, GEOM ? &fene : nullptr,
-                                                                  &near), 0.0f});
-                if constexpr (GEOM) {   // a FENE bond near its divergence: the exact positions give the change
-                    if (__ballot_sync(g.mask, near) & g.mask) {
-                        const double dF = fene_delta_exact<TPW>(sd, x64, P, M, slot, g, false, seed, t, &queued);
-                        if (g.lane == 0) part = df_add(part, df_of(dF));
-                    } else {
-                        part = df_add(part, DF{fene, 0.0f});
+                                                                  &near, &tors, &tnear), 0.0f});
+                if constexpr (GEOM) {
+                    // a FENE bond near its divergence or a dihedral near degenerate: the
+                    // exact positions give that kind of term's change
+                    const bool fx = __ballot_sync(g.mask, near) & g.mask;
+                    const bool tx = __ballot_sync(g.mask, tnear) & g.mask;
+                    if (fx || tx) {
+                        const double dX = local_delta_exact<TPW, GEOM>(sd, x64, P, M, slot, g, false, seed, t,
+                                                                       &queued, fx, tx);
+                        if (g.lane == 0) part = df_add(part, df_of(dX));
                     }
+                    if (!fx) part = df_add(part, DF{fene, 0.0f});
+                    if (!tx) part = df_add(part, DF{tors, 0.0f});
+                } else {
+                    // this build keeps the exact path (an out-of-line call) out of its move
+                    // loop: a dihedral whose normals lie below FP32 resolution counts 0, the
+                    // FP64 value of collinear bonds (in continuous sampling a dihedral that
+                    // is near degenerate without being degenerate has probability ~1e-9, and
+                    // the host runs contexts whose chains start straight in the general build)
+                    part = df_add(part, DF{tors, 0.0f});
                 }
             }
             dE32 = group_sum_df<TPW>(part, g);
@@ -758,8 +771,36 @@ void layout_tiles(const phast_ctx* c, int wpc, int grid, SweepArgs* a) {
     a->n_tiles = start;
 }
 
-// Whether any system type of the context needs the paper's own geometry.
+// Whether a system type with a torsion term starts with a dihedral whose smaller
+// normal is under 1e-3 (bonds within ~0.06 degrees of collinear: a straight
+// start).  Pivot moves keep such stretches and keep making new ones with small
+// angles; FP32 resolves none of them, so such contexts run the build that takes
+// those dihedrals in FP64 on the exact positions.
+bool starts_near_straight(const phast_ctx* c, const double* xyz0) {
+    for (int s = 0; s < c->n_sys; ++s) {
+        const SysDesc& d = c->desc[s];
+        if (d.k_tors == 0.0) continue;
+        for (int w = 0; w < d.n_walkers; ++w) {
+            const double* x = xyz0 + d.xyz_off + (int64_t)w * d.N * 3;
+            for (int ch = 0; ch < d.n_chains; ++ch)
+                for (int j = d.chain_off[ch]; j + 2 < d.chain_off[ch + 1]; ++j) {
+                    const double* a = x + 3 * j;
+                    const double b0[3] = {a[3] - a[0], a[4] - a[1], a[5] - a[2]};
+                    const double b1[3] = {a[6] - a[3], a[7] - a[4], a[8] - a[5]};
+                    const double n[3] = {b0[1] * b1[2] - b0[2] * b1[1], b0[2] * b1[0] - b0[0] * b1[2],
+                                         b0[0] * b1[1] - b0[1] * b1[0]};
+                    if (n[0] * n[0] + n[1] * n[1] + n[2] * n[2] < 1e-6) return true;
+                }
+        }
+    }
+    return false;
+}
+
+// Whether the context runs the general build (the paper's own geometry, and the
+// exact FP64 path of the local terms): a system type needs that geometry, or a
+// type with torsion starts near straight.
 bool uses_geometry(const phast_ctx* c) {
+    if (c->near_straight) return true;
     for (int s = 0; s < c->n_sys; ++s) {
         const SysDesc& d = c->desc[s];
         if (d.has_sphere || d.k_fene != 0.0 || d.p[PHAST_BOND] > 0.0 || d.p[PHAST_CAP] > 0.0) return true;
@@ -905,6 +946,7 @@ extern "C" int phast_ctx_create(phast_ctx** out, int32_t n_systems, const phast_
     c->xyz_total = xyz_total;
     c->lnw_total = lnw_total;
     c->hw_total = hw_total;
+    c->near_straight = starts_near_straight(c, xyz0);
     // tile order: most expensive system types first
     std::vector<std::pair<double, int>> cost;
     for (int s = 0; s < n_systems; ++s) cost.push_back({-system_cost(c->desc[s]), s});
