@@ -222,7 +222,14 @@ enum { PHAST_FORM_BATCHED = 0, PHAST_FORM_PLAIN = 1 };
  * recompute_every sweeps (by each walker's own move index) the running energy
  * is replaced by an FP64 full energy, and the bin by its bin (the nearest edge
  * bin when that energy lies just outside the range; phast_walker_stats counts
- * those events).
+ * those events).  With pair_precision 32 the local terms are FP32 except near
+ * their hard edges, which the exact FP64 positions decide: the container wall,
+ * a FENE bond near its range, and a dihedral of bonds within ~0.06 degrees of
+ * collinear (whose FP64 term is 0 when they are collinear).  The batched form
+ * has a lean build without the paper's geometry, in which such a dihedral
+ * counts as collinear; a context runs it only when no system type needs the
+ * geometry and no type with a torsion term starts with a bend under ~0.06
+ * degrees (a straight start).
  *  form: PHAST_FORM_BATCHED (shared-memory tiles, FP32 or FP64 pairs per
  *        mp.pair_precision) or PHAST_FORM_PLAIN (one walker per CTA, all FP64,
  *        global-memory histogram atomics; the comparison form).
