@@ -292,6 +292,13 @@ energy_grad32_kernel(const SysDesc d, int B, const double* __restrict__ xyz, dou
         o.x = q.x; o.y = q.y; o.z = q.z; o.tag = __float_as_int(q.w);
         return o;
     };
+    // the FP64 coordinates, for the dihedrals FP32 cannot resolve (torsion_w)
+    auto pos64 = [&](int j) -> double3 { return ld3(x64 + 3 * j); };
+    auto pos64p = [&](int j) -> P4<double> {
+        P4<double> q;
+        q.x = x64[3 * j]; q.y = x64[3 * j + 1]; q.z = x64[3 * j + 2]; q.tag = 0; q.pad = 0;
+        return q;
+    };
     const FF<float> f{d};
     const Coef<float> cf = coef<float>(d, pdev);
     DF E{0.0f, 0.0f}, gp[5] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
@@ -304,7 +311,9 @@ energy_grad32_kernel(const SysDesc d, int B, const double* __restrict__ xyz, dou
             E = df_add(E, DF{cf.kb * t, 0.0f});
         }
         for (int j = lane; j <= n - 4; j += 32) {
-            const float t = torsion_w<float>(pos, o, j);
+            bool nr = false;   // a dihedral FP32 cannot resolve: its FP64 value
+            float t = torsion_w<float>(pos, o, j, &nr);
+            if (nr) t = (float)torsion_term(pos64, o, j);
             gp[3] = df_add(gp[3], DF{-t, 0.0f});
             E = df_add(E, DF{-cf.kt * t, 0.0f});
         }
@@ -381,7 +390,15 @@ energy_grad32_kernel(const SysDesc d, int B, const double* __restrict__ xyz, dou
             }
             for (int jj = li - 3; jj <= li; ++jj) {      // dihedrals containing i: -kappa cos tau
                 if (jj < 0 || jj > n - 4) continue;
-                const V3<float> t = torsion_grad<float>(pos, o, jj, li - jj);
+                bool nr = false;
+                (void)torsion_w<float>(pos, o, jj, &nr);
+                V3<float> t;
+                if (nr) {   // FP64, as the value
+                    const V3<double> t64 = torsion_grad<double>(pos64p, o, jj, li - jj);
+                    t = V3<float>{(float)t64.x, (float)t64.y, (float)t64.z};
+                } else {
+                    t = torsion_grad<float>(pos, o, jj, li - jj);
+                }
                 gxs -= cf.kt * t.x;
                 gys -= cf.kt * t.y;
                 gzs -= cf.kt * t.z;
@@ -444,13 +461,33 @@ __device__ __forceinline__ float bend_vg(const float4& x0, const float4& x1, con
 }
 
 // Value and gradient of cos tau_j of monomers j..j+3 at once (FP32); zero for a
-// degenerate dihedral (|n1|^2 |n2|^2 < 1e-20), whose term is 0.
+// degenerate dihedral (|n1|^2 |n2|^2 < 1e-20), whose term is 0.  A dihedral FP32
+// cannot resolve (torsion_unresolved32) is taken in FP64 from x64, the FP64
+// coordinates of the chain (monomer j at x64 + 3 j).
+__device__ __noinline__ float torsion_vg64(const double* x64, int j, float3 g[4]) {
+    auto p = [&](int k) -> P4<double> {
+        P4<double> q;
+        q.x = x64[3 * k]; q.y = x64[3 * k + 1]; q.z = x64[3 * k + 2]; q.tag = 0; q.pad = 0;
+        return q;
+    };
+    for (int q = 0; q < 4; ++q) {
+        const V3<double> t = torsion_grad<double>(p, 0, j, q);
+        g[q] = make_float3((float)t.x, (float)t.y, (float)t.z);
+    }
+    return (float)torsion_term([&](int k) { return ld3(x64 + 3 * k); }, 0, j);
+}
+
 __device__ __forceinline__ float torsion_vg(const float4& x0, const float4& x1, const float4& x2, const float4& x3,
-                                            float3 g[4]) {
+                                            float3 g[4], const double* x64, int j) {
     const V3<float> u{x1.x - x0.x, x1.y - x0.y, x1.z - x0.z}, v{x2.x - x1.x, x2.y - x1.y, x2.z - x1.z},
         w{x3.x - x2.x, x3.y - x2.y, x3.z - x2.z};
     const V3<float> n1 = cross3(u, v), n2 = cross3(v, w);
     const float n11 = dot3(n1, n1), n22 = dot3(n2, n2);
+    float mx = fmaxf(fmaxf(fabsf(x0.x), fabsf(x0.y)), fabsf(x0.z));
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x1.x), fabsf(x1.y)), fabsf(x1.z)));
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x2.x), fabsf(x2.y)), fabsf(x2.z)));
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x3.x), fabsf(x3.y)), fabsf(x3.z)));
+    if (torsion_unresolved32(n11, n22, mx, true)) return torsion_vg64(x64, j, g);
     if (n11 * n22 < 1e-20f) {
         g[0] = g[1] = g[2] = g[3] = make_float3(0.f, 0.f, 0.f);
         return 0.0f;
@@ -542,7 +579,7 @@ energy_grad32_chain_kernel(const SysDesc d, int B, const double* __restrict__ xy
     for (int p = 0; p < 4; ++p) {
         for (int j = p + 4 * lane; j <= N - 4; j += 128) {
             float3 g[4];
-            const float t = torsion_vg(r[j], r[j + 1], r[j + 2], r[j + 3], g);
+            const float t = torsion_vg(r[j], r[j + 1], r[j + 2], r[j + 3], g, x64, j);
             gp[3] = df_add(gp[3], DF{-t, 0.0f});
             E = df_add(E, DF{-kt * t, 0.0f});
             if (grad_xyz)

@@ -228,3 +228,44 @@ def test_device_parameters_equal_host_parameters(phast, name, s, x, precision):
         st = phast._Structs([s])
         phast._check(phast.lib().phast_energy_grad_params(st.sys, st.ff, x.shape[0], xt.data_ptr(), precision, None,
                                                           None, None, None, phast._stream(None)))
+
+
+def _straight_stretches(n_chain, n_chains, seed, box_L=0.0):
+    """Chains that started straight along an irrational direction and took three
+    pivots of +-0.4 rad each (FP64): their straight stretches hold dihedrals of
+    collinear bonds (FP64 term 0) whose FP32 normals are rounding noise."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in range(n_chains):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        x = np.arange(n_chain)[:, None] * u[None, :] + np.array([0.0, 6.0 * c, 0.0]) + rng.normal(size=3) * 0.1
+        for k in rng.choice(np.arange(2, n_chain - 2), 3, replace=False):
+            a = rng.normal(size=3)
+            a /= np.linalg.norm(a)
+            t = rng.choice([-0.4, 0.4])
+            K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+            R = np.eye(3) + np.sin(t) * K + (1 - np.cos(t)) * K @ K
+            x[k + 1:] = (x[k + 1:] - x[k]) @ R.T + x[k]
+        out.append(x)
+    return np.concatenate(out)[None]
+
+
+@pytest.mark.parametrize("name", ["fib55", "2x34"])
+def test_fp32_straight_stretches(phast, orc, name):
+    """FP32 energies and gradients of conformations with straight stretches: the
+    dihedrals FP32 cannot resolve are taken in FP64, so the FP32 results keep the
+    FP32 tolerance against the oracle (without that they were off by several
+    energy units)."""
+    if name == "fib55":
+        s, x = inputs.config3(1)[0], _straight_stretches(55, 1, 61)
+    else:
+        s, x = inputs.config2(1)[2], _straight_stretches(34, 2, 62, box_L=40.0)
+    E, gx, gf = phast.phast_energy_grad(s, torch.from_numpy(x).cuda(), 32)
+    E, gx, gf = E.cpu().numpy(), gx.cpu().numpy(), gf.cpu().numpy()
+    Eo, gxo, gfo = _oracle(orc, s, x)
+    assert abs(E[0] - Eo[0]) <= 1e-4 * max(1.0, abs(Eo[0])), (E[0], Eo[0])
+    assert np.max(np.abs(gx[0] - gxo[0])) <= 1e-4 * max(1.0, np.max(np.abs(gxo[0])))
+    assert np.all(np.abs(gf[0] - gfo[0]) <= 1e-4 * np.maximum(1.0, np.abs(gfo[0])))
+    E32 = phast.phast_energy(s, torch.from_numpy(x).cuda(), pair_precision=32).cpu().numpy()
+    assert abs(E32[0] - Eo[0]) <= 1e-4 * max(1.0, abs(Eo[0])), (E32[0], Eo[0])
