@@ -42,3 +42,18 @@ def test_gpus_flag_starts_one_rank_per_gpu_dry_run():
     assert d["dry_run"] is True and d["n_gpus"] == 2 and d["exchanges_per_step"] == 1.0
     assert d["key_ranges"] == [[0, 63], [64, 127]]
     assert d["max_ms"] == max(d["rank_ms"]) and len(d["rank_ms"]) == 2   # the slowest rank's time
+
+
+def test_oracle_sample_of_a_small_system_runs_several_sweeps_per_task():
+    """The CPU baseline of a small system: each thread-pool task carries a walker
+    through k sweeps, enough for about 10 ms of work, so that the pool's per-task
+    overhead does not set the figure; the eight 55-mers keep one sweep a task."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1702_01770_gb300 import inputs
+    v, pev, n, dt, k = bench.oracle_walker_moves_per_s(inputs.config0(), 0.3, 2)
+    assert k > 1 and n >= 2 and dt > 0.0
+    assert v > 0.0 and pev > 0.0
+    s4 = inputs.config4(walkers=1)
+    v4, pev4, n4, dt4, k4 = bench.oracle_walker_moves_per_s(s4, 0.01, 1)
+    assert k4 == 1 and n4 >= 1 and pev4 / v4 > 100.0   # hundreds of pair evaluations per move
