@@ -228,8 +228,8 @@ enum { PHAST_FORM_BATCHED = 0, PHAST_FORM_PLAIN = 1 };
  * collinear (whose FP64 term is 0 when they are collinear).  The batched form
  * has a lean build without the paper's geometry, in which such a dihedral
  * counts as collinear; a context runs it only when no system type needs the
- * geometry and no type with a torsion term starts with a bend under ~0.06
- * degrees (a straight start).
+ * geometry and no type with a torsion term starts with a bend under ~1e-5 rad
+ * (a straight start).
  *  form: PHAST_FORM_BATCHED (shared-memory tiles, FP32 or FP64 pairs per
  *        mp.pair_precision) or PHAST_FORM_PLAIN (one walker per CTA, all FP64,
  *        global-memory histogram atomics; the comparison form).

@@ -771,11 +771,12 @@ void layout_tiles(const phast_ctx* c, int wpc, int grid, SweepArgs* a) {
     a->n_tiles = start;
 }
 
-// Whether a system type with a torsion term starts with a dihedral whose smaller
-// normal is under 1e-3 (bonds within ~0.06 degrees of collinear: a straight
-// start).  Pivot moves keep such stretches and keep making new ones with small
-// angles; FP32 resolves none of them, so such contexts run the build that takes
-// those dihedrals in FP64 on the exact positions.
+// Whether a system type with a torsion term starts with a bend whose normal is
+// under 1e-5 (bonds within ~1e-5 rad of collinear: a straight start, collinear
+// up to FP64 rounding; a random start has such a bend with probability ~1e-11 per
+// bend).  Pivot moves keep such stretches and keep making nearly collinear bonds
+// with small angles; FP32 resolves none of them, so such contexts run the build
+// that takes those dihedrals in FP64 on the exact positions.
 bool starts_near_straight(const phast_ctx* c, const double* xyz0) {
     for (int s = 0; s < c->n_sys; ++s) {
         const SysDesc& d = c->desc[s];
@@ -789,7 +790,7 @@ bool starts_near_straight(const phast_ctx* c, const double* xyz0) {
                     const double b1[3] = {a[6] - a[3], a[7] - a[4], a[8] - a[5]};
                     const double n[3] = {b0[1] * b1[2] - b0[2] * b1[1], b0[2] * b1[0] - b0[0] * b1[2],
                                          b0[0] * b1[1] - b0[1] * b1[0]};
-                    if (n[0] * n[0] + n[1] * n[1] + n[2] * n[2] < 1e-6) return true;
+                    if (n[0] * n[0] + n[1] * n[1] + n[2] * n[2] < 1e-10) return true;
                 }
         }
     }
