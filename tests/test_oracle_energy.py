@@ -173,3 +173,20 @@ def test_config_initial_energies_in_range(orc):
         m = orc.Model(s.chain_len, s.seq, box_L=s.box_L, k_tors=s.k_tors)
         E = orc.energy(m, s.xyz0)
         assert s.e_min <= E < s.e_max, (s.name, E)
+
+
+@pytest.mark.parametrize("eps,resolved", [(0.0, False), (1e-12, False), (1e-6, True), (1e-3, True)])
+def test_nearly_collinear_dihedral(orc, eps, resolved):
+    """The degenerate-dihedral rule of the torsion term: bonds b0, b1 at an angle eps
+    make n1 = b0 x b1 of length sin(eps).  With b1 = e_x, b2 = e_y and b0 tilted by eps
+    in the plane at azimuth phi about e_x, cos tau = -cos(phi) whatever eps; the term
+    counts while |n1|^2 |n2|^2 = sin^2(eps) >= 1e-20 and is 0 below (eps = 1e-12: 1e-24,
+    and exactly collinear bonds)."""
+    phi = np.pi / 3
+    b0 = np.array([np.cos(eps), np.sin(eps) * np.cos(phi), np.sin(eps) * np.sin(phi)])
+    x = np.array([-b0, [0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [1.0, 1.0, 0.0]])
+    kappa = -0.5
+    m = model_for(orc, "AAAA", k_tors=kappa)
+    _, t = orc.energy(m, x, terms=True)
+    expected = -kappa * (-np.cos(phi)) if resolved else 0.0
+    assert t[1] == pytest.approx(expected, abs=1e-8), (eps, t[1])
