@@ -862,11 +862,11 @@ __device__ __forceinline__ PT bend_w(const Pos& pos, int o, int k) {
 // magnitude (a few ulp for the FP32 trial positions of a rotation), which leaves
 // the normal of a collinear pair of unit bonds with a length of a few to some
 // tens of ulp and a meaningless direction, and an FP32 cos tau of a normal n
-// carries an error of about that noise over |n|.  wide (the builds with an exact
-// FP64 path): a normal with n^2 < 1e-6 (bonds within ~0.06 degrees of collinear)
-// marks the term; narrow (the build without it, where a marked term counts as
-// degenerate): n^2 below max((32 ulp)^2, 1e-10), the ulp that of the largest
-// coordinate of the four monomers.  A dihedral that is that close to degenerate
+// carries an error of about that noise over |n|.  A normal with n^2 below
+// max((32 ulp)^2, floor), the ulp that of the largest coordinate of the four
+// monomers, marks the term: wide (the builds with an exact FP64 path) takes the
+// floor 1e-6 (bonds within ~0.06 degrees of collinear), narrow (the build
+// without it, where a marked term counts as degenerate) 1e-10.  A dihedral that is that close to degenerate
 // without being degenerate (a bend under ~6e-5 rad for a 55-mer) has a
 // probability of order 1e-9 under continuous moves of a chain that did not start
 // straight; the host runs contexts whose chains start straight in a build with
